@@ -1,0 +1,184 @@
+// Column passes: FFT down the columns of packed spectra, multiply by the PSF spectra, inverse FFT.
+//
+// A tile holds C adjacent spectrum columns x all H rows in shared memory (global loads and stores
+// are C*8 contiguous bytes per row).  Column 0 carries the DC and Nyquist columns of the row
+// transform as real / imaginary part; with Z its column FFT, F0[k] = (Z[k] + conj Z[-k])/2 and
+// FM[k] = (Z[k] - conj Z[-k])/(2i), and a product with the PSF spectrum becomes
+//     Z[k] P[k] + conj(Z[-k]) Q[k],   P = (K0 + KM)/2,  Q = (K0 - KM)/2
+// (K0, KM the PSF spectrum on those two columns; conjugated for the transpose), which is again
+// the packed spectrum of two real columns.
+//
+// Modes
+//   COL_KHAT      : forward only; writes the PSF spectrum (P in column 0, Q in a side column),
+//                   scaled by 1/(H*M*sum K) and, for centred PSFs, by (-1)^(kr+kc) (origin shift).
+//   COL_1TOP      : one input plane -> nout planes, out_j = IFFT(FFT(in) . K_j)   (A_j f, Eq. projection)
+//   COL_1TOP_CONJ : as COL_1TOP with conj K_j (correlation, used for alpha_j = K_j (x) M_S)
+//   COL_PTO1      : nin planes -> one plane, out = IFFT(sum_j FFT(in_j) . conj K_j)
+//                   (sum_j A_j^T y_j, Eq. backprojection)
+#pragma once
+#include "fft.cuh"
+#include "state.cuh"
+
+namespace sgp {
+
+enum ColMode { COL_KHAT = 0, COL_1TOP = 1, COL_1TOP_CONJ = 2, COL_PTO1 = 3 };
+
+template <int H> struct ColGeo {
+  using P = Plan<H>;
+  static constexpr int T = P::T, E = P::E;
+  static constexpr int C = kColBlock / T;
+  static constexpr int ROWSP = col_rows_padded<H>();
+  static constexpr size_t SMEM = size_t(C) * ROWSP * sizeof(float2);
+};
+
+template <int H, int C>
+__device__ __forceinline__ void col_load(const ColLayout<C>& x, const float2* __restrict__ src, int M, int t, bool act) {
+  constexpr int T = Plan<H>::T, E = Plan<H>::E;
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int i = t + q * T;
+      x(i) = src[size_t(i) * M];
+    }
+  }
+}
+
+// product of the column spectrum with the PSF spectrum for the element (row i) owned by a thread
+template <int H, int C, bool CONJ>
+__device__ __forceinline__ float2 col_product(const ColLayout<C>& x, int i, int col, float2 X,
+                                              const float2* __restrict__ kh, const float2* __restrict__ kq, int M) {
+  float2 K = __ldg(&kh[size_t(i) * M + col]);
+  if (CONJ) K = cconj(K);
+  if (col != 0) return cmul(X, K);
+  float2 Q = __ldg(&kq[i]);
+  if (CONJ) Q = cconj(Q);
+  const float2 Xm = x((H - i) % H);
+  return cadd(cmul(X, K), cmul(cconj(Xm), Q));
+}
+
+template <int H, int MODE>
+__global__ void __launch_bounds__(kColBlock) k_col(const ColJob* __restrict__ jobs, const int2* __restrict__ items,
+                                                  int n_items) {
+  using G = ColGeo<H>;
+  constexpr int C = G::C, T = G::T, E = G::E;
+  extern __shared__ float2 smem[];
+  const int c = threadIdx.x % C, t = threadIdx.x / C;
+  const ColLayout<C> x{smem + c};
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int2 item = items[it];
+    const ColJob& jb = jobs[item.x];
+    if (jb.ctrl && jb.ctrl->done >= 1) continue;
+    const int M = jb.M;
+    const int col = item.y + c;
+    const bool act = col < M;
+    if (MODE == COL_KHAT) {
+      col_load<H, C>(x, jb.in + col, M, t, act);
+      __syncthreads();
+      fft_inplace<H, false>(x, t, act);
+      if (act) {
+        float2 outv[E], qv[E];
+        const float s = jb.scale;
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+          const int i = t + q * T;
+          const float2 X = x(i);
+          if (col == 0) {
+            const float2 Xm = cconj(x((H - i) % H));
+            float2 F0 = cscale(cadd(X, Xm), 0.5f);
+            float2 FM = cscale(csub(X, Xm), 0.5f);
+            FM = make_float2(FM.y, -FM.x);               // divide by i
+            float s0 = s, sM = s;
+            if (!jb.corner) {
+              if (i & 1) { s0 = -s0; sM = -sM; }
+              if (M & 1) sM = -sM;
+            }
+            F0 = cscale(F0, s0);
+            FM = cscale(FM, sM);
+            outv[q] = cscale(cadd(F0, FM), 0.5f);
+            qv[q] = cscale(csub(F0, FM), 0.5f);
+          } else {
+            const float sg = (!jb.corner && ((i + col) & 1)) ? -s : s;
+            outv[q] = cscale(X, sg);
+            qv[q] = make_float2(0.0f, 0.0f);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+          const int i = t + q * T;
+          jb.out[size_t(i) * M + col] = outv[q];
+          if (col == 0) jb.khatq[i] = qv[q];
+        }
+      }
+      __syncthreads();
+    } else if (MODE == COL_1TOP || MODE == COL_1TOP_CONJ) {
+      constexpr bool CJ = MODE == COL_1TOP_CONJ;
+      for (int j = 0; j < jb.nout; ++j) {
+        col_load<H, C>(x, jb.in + col, M, t, act);
+        __syncthreads();
+        fft_inplace<H, false>(x, t, act);
+        float2 v[E];
+        if (act) {
+          const float2* kh = jb.khat + size_t(j) * jb.plane_stride;
+          const float2* kq = jb.khatq + size_t(j) * H;
+#pragma unroll
+          for (int q = 0; q < E; ++q) {
+            const int i = t + q * T;
+            v[q] = col_product<H, C, CJ>(x, i, col, x(i), kh, kq, M);
+          }
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll
+          for (int q = 0; q < E; ++q) x(t + q * T) = v[q];
+        }
+        __syncthreads();
+        fft_inplace<H, true>(x, t, act);
+        if (act) {
+          float2* dst = jb.out + size_t(j) * jb.plane_stride + col;
+#pragma unroll
+          for (int q = 0; q < E; ++q) {
+            const int i = t + q * T;
+            dst[size_t(i) * M] = x(i);
+          }
+        }
+        __syncthreads();
+      }
+    } else {  // COL_PTO1
+      float2 acc[E];
+#pragma unroll
+      for (int q = 0; q < E; ++q) acc[q] = make_float2(0.0f, 0.0f);
+      for (int j = 0; j < jb.nin; ++j) {
+        col_load<H, C>(x, jb.in + size_t(j) * jb.plane_stride + col, M, t, act);
+        __syncthreads();
+        fft_inplace<H, false>(x, t, act);
+        if (act) {
+          const float2* kh = jb.khat + size_t(j) * jb.plane_stride;
+          const float2* kq = jb.khatq + size_t(j) * H;
+#pragma unroll
+          for (int q = 0; q < E; ++q) {
+            const int i = t + q * T;
+            acc[q] = cadd(acc[q], col_product<H, C, true>(x, i, col, x(i), kh, kq, M));
+          }
+        }
+        __syncthreads();
+      }
+      if (act) {
+#pragma unroll
+        for (int q = 0; q < E; ++q) x(t + q * T) = acc[q];
+      }
+      __syncthreads();
+      fft_inplace<H, true>(x, t, act);
+      if (act) {
+        float2* dst = jb.out + col;
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+          const int i = t + q * T;
+          dst[size_t(i) * M] = x(i);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace sgp

@@ -1,0 +1,261 @@
+// Shared-memory Stockham FFT building blocks for real 2-D images on sm_103a.
+//
+// The convolutions A f = K * f and A^T y = K (x) y of the deconvolution methods (Sect. 2.2-2.4,
+// Eq. projection / backprojection) are evaluated as
+//      row R2C  ->  column FFT . (PSF spectrum) . column IFFT  ->  row C2R
+// with every pass reading and writing HBM once.  This header provides the pieces:
+//   * in-register DFTs of radix 2, 3, 4, 6, 8, 12, 16, 24;
+//   * one autosorting Stockham stage over data held in shared memory (radix R, sub-transform
+//     length NS):  read x[j + m L/R], twiddle by w_{NS R}^{m (j mod NS)}, DFT_R, write to
+//     (j - j mod NS) R + j mod NS + m NS.  The output is in natural order after the last stage,
+//     so the spectrum multiply and the row post-processing need no reordering;
+//   * per-length plans (radix sequences; E values per thread, T = L/E threads per transform);
+//   * a twiddle table exp(-2 pi i q / L) for every supported length (filled once per device).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sgp {
+
+// ------------------------------------------------------------------------------ complex helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV> __device__ __forceinline__ float2 mul_mi(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// ------------------------------------------------------------------------------ twiddles
+// cos / sin (2 pi t / 48), t = 0..47: every in-register radix used here divides 48.
+__constant__ float2 c_w48[48] = {
+    {1.0f, 0.0f}, {9.91444861374e-1f, 1.3052619222e-1f}, {9.65925826289e-1f, 2.58819045103e-1f},
+    {9.23879532511e-1f, 3.82683432365e-1f}, {8.66025403784e-1f, 5.0e-1f}, {7.93353340291e-1f, 6.08761429009e-1f},
+    {7.07106781187e-1f, 7.07106781187e-1f}, {6.08761429009e-1f, 7.93353340291e-1f}, {5.0e-1f, 8.66025403784e-1f},
+    {3.82683432365e-1f, 9.23879532511e-1f}, {2.58819045103e-1f, 9.65925826289e-1f}, {1.3052619222e-1f, 9.91444861374e-1f},
+    {0.0f, 1.0f}, {-1.3052619222e-1f, 9.91444861374e-1f}, {-2.58819045103e-1f, 9.65925826289e-1f},
+    {-3.82683432365e-1f, 9.23879532511e-1f}, {-5.0e-1f, 8.66025403784e-1f}, {-6.08761429009e-1f, 7.93353340291e-1f},
+    {-7.07106781187e-1f, 7.07106781187e-1f}, {-7.93353340291e-1f, 6.08761429009e-1f}, {-8.66025403784e-1f, 5.0e-1f},
+    {-9.23879532511e-1f, 3.82683432365e-1f}, {-9.65925826289e-1f, 2.58819045103e-1f}, {-9.91444861374e-1f, 1.3052619222e-1f},
+    {-1.0f, 0.0f}, {-9.91444861374e-1f, -1.3052619222e-1f}, {-9.65925826289e-1f, -2.58819045103e-1f},
+    {-9.23879532511e-1f, -3.82683432365e-1f}, {-8.66025403784e-1f, -5.0e-1f}, {-7.93353340291e-1f, -6.08761429009e-1f},
+    {-7.07106781187e-1f, -7.07106781187e-1f}, {-6.08761429009e-1f, -7.93353340291e-1f}, {-5.0e-1f, -8.66025403784e-1f},
+    {-3.82683432365e-1f, -9.23879532511e-1f}, {-2.58819045103e-1f, -9.65925826289e-1f}, {-1.3052619222e-1f, -9.91444861374e-1f},
+    {0.0f, -1.0f}, {1.3052619222e-1f, -9.91444861374e-1f}, {2.58819045103e-1f, -9.65925826289e-1f},
+    {3.82683432365e-1f, -9.23879532511e-1f}, {5.0e-1f, -8.66025403784e-1f}, {6.08761429009e-1f, -7.93353340291e-1f},
+    {7.07106781187e-1f, -7.07106781187e-1f}, {7.93353340291e-1f, -6.08761429009e-1f}, {8.66025403784e-1f, -5.0e-1f},
+    {9.23879532511e-1f, -3.82683432365e-1f}, {9.65925826289e-1f, -2.58819045103e-1f}, {9.91444861374e-1f, -1.3052619222e-1f},
+};
+
+// v * w_R^e, w_R = exp(-/+ 2 pi i / R) (forward / inverse); e is a compile-time constant after unrolling
+template <int R, bool INV>
+__device__ __forceinline__ float2 twr(float2 v, int e) {
+  const int t = ((e % R) * (48 / R)) % 48;
+  if (t == 0) return v;
+  if (t == 24) return make_float2(-v.x, -v.y);
+  if (t == 12) return mul_mi<INV>(v);
+  if (t == 36) return mul_mi<!INV>(v);
+  const float2 w = c_w48[t];
+  return INV ? cmul(v, w) : cmulc(v, w);
+}
+
+// supported transform lengths and the offsets of their tables exp(-2 pi i q / L), q < L
+constexpr int kTwiddleTotal = 7148;
+__host__ __device__ constexpr int tw_offset(int L) {
+  return L == 8 ? 0 : L == 12 ? 8 : L == 16 ? 20 : L == 24 ? 36 : L == 32 ? 60 : L == 48 ? 92 :
+         L == 64 ? 140 : L == 96 ? 204 : L == 128 ? 300 : L == 192 ? 428 : L == 256 ? 620 :
+         L == 384 ? 876 : L == 512 ? 1260 : L == 768 ? 1772 : L == 1024 ? 2540 :
+         L == 1536 ? 3564 : L == 2048 ? 5100 : -1;
+}
+// One copy per translation unit (internal linkage, no relocatable device code); every unit that
+// launches FFT kernels defines an initialiser (SGP_DEFINE_TWIDDLE_INIT) that copies the table in.
+namespace {
+__device__ float2 g_twiddle[kTwiddleTotal];
+}
+#define SGP_DEFINE_TWIDDLE_INIT(NAME)                                                                 \
+  cudaError_t NAME(const float2* host_table) {                                                       \
+    return cudaMemcpyToSymbol(::sgp::g_twiddle, host_table, sizeof(float2) * ::sgp::kTwiddleTotal);  \
+  }
+
+template <int L, bool INV>
+__device__ __forceinline__ float2 twl(int q) {  // exp(-/+ 2 pi i q / L), 0 <= q < L
+  const float2 w = __ldg(&g_twiddle[tw_offset(L) + q]);
+  return INV ? cconj(w) : w;
+}
+
+// ------------------------------------------------------------------------------ register DFTs
+// V[q] = sum_m v[m] w_R^{m q}
+template <int R, bool INV> struct DFT;
+
+template <bool INV> struct DFT<2, INV> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float2 a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+  }
+};
+template <bool INV> struct DFT<4, INV> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    const float2 t2 = cadd(v[1], v[3]), t3 = mul_mi<INV>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+  }
+};
+template <bool INV> struct DFT<3, INV> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float h = 0.866025403784438647f;  // sqrt(3)/2
+    const float2 s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    const float2 m = make_float2(v[0].x - 0.5f * s.x, v[0].y - 0.5f * s.y);
+    const float2 ihd = make_float2(-h * d.y, h * d.x);  // i h d
+    v[0] = cadd(v[0], s);
+    // forward: V1 = m - i h d, V2 = m + i h d; the inverse swaps the signs
+    if (INV) { v[1] = cadd(m, ihd); v[2] = csub(m, ihd); }
+    else     { v[1] = csub(m, ihd); v[2] = cadd(m, ihd); }
+  }
+};
+// composite R = R1 * R2: input index m = R2 m1 + m2, output index q = q1 + R1 q2
+template <int R1, int R2, bool INV> struct DFTComp {
+  __device__ __forceinline__ static void run(float2* v) {
+    constexpr int R = R1 * R2;
+    float2 a[R2][R1];
+#pragma unroll
+    for (int m2 = 0; m2 < R2; ++m2) {
+#pragma unroll
+      for (int m1 = 0; m1 < R1; ++m1) a[m2][m1] = v[R2 * m1 + m2];
+      DFT<R1, INV>::run(a[m2]);
+#pragma unroll
+      for (int q1 = 0; q1 < R1; ++q1) a[m2][q1] = twr<R, INV>(a[m2][q1], m2 * q1);
+    }
+#pragma unroll
+    for (int q1 = 0; q1 < R1; ++q1) {
+      float2 b[R2];
+#pragma unroll
+      for (int m2 = 0; m2 < R2; ++m2) b[m2] = a[m2][q1];
+      DFT<R2, INV>::run(b);
+#pragma unroll
+      for (int q2 = 0; q2 < R2; ++q2) v[q1 + R1 * q2] = b[q2];
+    }
+  }
+};
+template <bool INV> struct DFT<6, INV> : DFTComp<2, 3, INV> {};
+template <bool INV> struct DFT<8, INV> : DFTComp<2, 4, INV> {};
+template <bool INV> struct DFT<12, INV> : DFTComp<4, 3, INV> {};
+template <bool INV> struct DFT<16, INV> : DFTComp<4, 4, INV> {};
+template <bool INV> struct DFT<24, INV> : DFTComp<8, 3, INV> {};
+
+// ------------------------------------------------------------------------------ plans
+template <int... Rs> struct RL {};
+template <class A, class B> struct RevImpl;
+template <int... Out> struct RevImpl<RL<>, RL<Out...>> { using type = RL<Out...>; };
+template <int R, int... Rest, int... Out> struct RevImpl<RL<R, Rest...>, RL<Out...>> {
+  using type = typename RevImpl<RL<Rest...>, RL<R, Out...>>::type;
+};
+template <class A> struct Rev { using type = typename RevImpl<A, RL<>>::type; };
+
+// E: complex values held per thread in every stage (each radix divides E); T = L / E threads.
+// The inverse runs the radices in reverse order.
+template <int L> struct Plan;
+#define SGP_PLAN(L_, E_, ...)                         \
+  template <> struct Plan<L_> {                       \
+    static constexpr int L = L_, E = E_, T = L_ / E_; \
+    using Fwd = RL<__VA_ARGS__>;                      \
+    using Inv = typename Rev<Fwd>::type;              \
+  };
+SGP_PLAN(8, 8, 8)
+SGP_PLAN(12, 12, 12)
+SGP_PLAN(16, 16, 16)
+SGP_PLAN(24, 24, 8, 3)
+SGP_PLAN(32, 16, 16, 2)
+SGP_PLAN(48, 12, 4, 12)
+SGP_PLAN(64, 16, 16, 4)
+SGP_PLAN(96, 24, 8, 12)
+SGP_PLAN(128, 16, 16, 8)
+SGP_PLAN(192, 24, 8, 8, 3)
+SGP_PLAN(256, 16, 16, 16)
+SGP_PLAN(384, 24, 8, 8, 6)
+SGP_PLAN(512, 16, 16, 16, 2)
+SGP_PLAN(768, 24, 8, 8, 12)
+SGP_PLAN(1024, 16, 16, 16, 4)
+SGP_PLAN(1536, 24, 8, 8, 24)
+SGP_PLAN(2048, 16, 16, 16, 8)
+#undef SGP_PLAN
+
+// ------------------------------------------------------------------------------ layouts
+// Row layout: element i of a row at base[i + (i >> 4)] (one pad slot per 16 elements keeps the
+// stride-R writes of the first stage free of bank conflicts).
+template <int L> struct RowLayout {
+  static constexpr int pitch = L + (L >> 4);
+  float2* base;
+  __device__ __forceinline__ float2& operator()(int i) const { return base[i + (i >> 4)]; }
+};
+// Column layout: element i of column c of a C-column tile at s[(i + (i >> 4)) * C + c]
+// (base is already offset by c).
+template <int C> struct ColLayout {
+  float2* base;
+  __device__ __forceinline__ float2& operator()(int i) const { return base[(i + (i >> 4)) * C]; }
+};
+template <int L> __host__ __device__ constexpr int col_rows_padded() { return L + (L >> 4); }
+
+// ------------------------------------------------------------------------------ Stockham stage
+// One radix-R stage of a length-L transform run by T threads (t in [0, T)).  Every thread of the
+// block calls it (it synchronises); threads with act == false only synchronise.
+template <int L, int R, int NS, int T, bool INV, class Lay>
+__device__ __forceinline__ void stockham_stage(const Lay& x, int t, bool act) {
+  constexpr int NB = L / R;
+  constexpr int PER = NB / T;
+  static_assert(PER * T == NB, "plan: each radix must divide the per-thread count");
+  float2 v[PER][R];
+  if (act) {
+#pragma unroll
+    for (int b = 0; b < PER; ++b) {
+      const int j = t + b * T;
+#pragma unroll
+      for (int m = 0; m < R; ++m) v[b][m] = x(j + m * NB);
+    }
+  }
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int b = 0; b < PER; ++b) {
+      const int j = t + b * T;
+      const int k = j % NS;
+      if (NS > 1) {
+#pragma unroll
+        for (int m = 1; m < R; ++m) v[b][m] = cmul(v[b][m], twl<L, INV>(m * k * (L / (NS * R))));
+      }
+      DFT<R, INV>::run(v[b]);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int m = 0; m < R; ++m) x(base + m * NS) = v[b][m];
+    }
+  }
+  __syncthreads();
+}
+
+template <int L, int T, bool INV, int NS, class Lay>
+__device__ __forceinline__ void run_stages(const Lay&, int, bool, RL<>) {}
+template <int L, int T, bool INV, int NS, class Lay, int R, int... Rest>
+__device__ __forceinline__ void run_stages(const Lay& x, int t, bool act, RL<R, Rest...>) {
+  stockham_stage<L, R, NS, T, INV>(x, t, act);
+  run_stages<L, T, INV, NS * R>(x, t, act, RL<Rest...>{});
+}
+
+// In-place complex FFT of length L (unnormalised), natural order in and out.
+template <int L, bool INV, class Lay>
+__device__ __forceinline__ void fft_inplace(const Lay& x, int t, bool act) {
+  using P = Plan<L>;
+  if (INV) run_stages<L, P::T, true, 1>(x, t, act, typename P::Inv{});
+  else     run_stages<L, P::T, false, 1>(x, t, act, typename P::Fwd{});
+}
+
+}  // namespace sgp

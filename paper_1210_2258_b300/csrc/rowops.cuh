@@ -1,0 +1,676 @@
+// Row passes: packed real FFTs along image rows with the method's pointwise work fused in.
+//
+// A row of W reals is handled as M = W/2 complex values z[n] = x[2n] + i x[2n+1]; one complex
+// FFT of length M plus a pairwise (k, M-k) post-processing gives the half spectrum X[0..M]; X[0]
+// and X[M] are real and are stored together in slot 0 (re = X[0], im = X[M]), so a spectrum row is
+// exactly M complex values (16-byte aligned, the same bytes as the real row).
+//
+// Pointwise formulas (Sect. 1, 2.1-2.4):
+//   ratio      r = g / (A f + b)                     (0 where g = 0 or outside S)
+//   KL term    g ln(g/u) + u - g = g phi((u-g)/g),   phi(t) = t - log(1+t), u = A f + b
+//   Armijo     J(f + lam d) - J(f) = sum lam Ad - g log(1 + lam Ad / u)
+//              = sum (u - g) q + g phi(q),  q = lam Ad / u         (no cancellation)
+//   scaling    D = w clip(f, L1, L2), w = 1/p (periodic) or M_R/alpha (boundary), Eq. (Dk),(Dkbound)
+//   gradient   grad = alpha_sum - sum_j A_j^T r_j on R (0 outside R), Eq. (KLgrad),(gradientboundary)
+//   step       y = P_+(f - alpha D grad), d = y - f, Eq. (diry); flux mode y = max(0, x - mu D)
+#pragma once
+#include "fft.cuh"
+#include "state.cuh"
+
+namespace sgp {
+
+template <int W> struct RowGeo {
+  static constexpr int M = W / 2;
+  using P = Plan<M>;
+  static constexpr int T = P::T, E = P::E;
+  static constexpr int ROWS = kRowBlock / T;
+  static constexpr int PITCH = RowLayout<M>::pitch;
+  static constexpr size_t SMEM = size_t(ROWS) * PITCH * sizeof(float2);
+};
+
+// ------------------------------------------------------------------------------ pointwise math
+// phi(t) = t - log1p(t); for |t| < 1/8 the alternating series t^2 sum_{n>=2} (-t)^(n-2)/n
+// (truncated after n = 12, relative error < 2e-9) avoids the cancellation of the direct form.
+__device__ __forceinline__ float phi_t(float t) {
+  if (fabsf(t) < 0.125f) {
+    float p = 1.0f / 12.0f;
+    p = fmaf(t, p, -1.0f / 11.0f);
+    p = fmaf(t, p, 1.0f / 10.0f);
+    p = fmaf(t, p, -1.0f / 9.0f);
+    p = fmaf(t, p, 1.0f / 8.0f);
+    p = fmaf(t, p, -1.0f / 7.0f);
+    p = fmaf(t, p, 1.0f / 6.0f);
+    p = fmaf(t, p, -1.0f / 5.0f);
+    p = fmaf(t, p, 1.0f / 4.0f);
+    p = fmaf(t, p, -1.0f / 3.0f);
+    p = fmaf(t, p, 0.5f);
+    return t * t * p;
+  }
+  return t - log1pf(t);
+}
+__device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
+
+// KL pixel term; g < 0 marks a pixel outside S (contributes nothing)
+__device__ __forceinline__ float kl_term(float g, float u0) {
+  if (g < 0.0f) return 0.0f;
+  if (g == 0.0f) return u0;
+  if (u0 <= 0.0f) return f_inf();
+  return g * phi_t((u0 - g) / g);
+}
+// Armijo pixel term J(f + lam d) - J(f) with dl = lam * A d, u0 = A f + b
+__device__ __forceinline__ float armijo_term(float g, float u0, float dl) {
+  if (g < 0.0f) return 0.0f;
+  if (g == 0.0f) return dl;
+  if (u0 + dl <= 0.0f || u0 <= 0.0f) return f_inf();
+  const float q = dl / u0;
+  return fmaf(u0 - g, q, g * phi_t(q));
+}
+__device__ __forceinline__ float ratio_term(float g, float u0) {
+  return (g > 0.0f && u0 > 0.0f) ? g / u0 : 0.0f;
+}
+
+// ------------------------------------------------------------------------------ reductions
+// Per-thread compensated FP32 accumulation over the thread's few pixels, FP64 from the warp
+// level up (FP32 throughout for the plain-FP32 variant).
+struct KSum {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+template <bool FP64> struct Acc { using T = float; };
+template <> struct Acc<true> { using T = double; };
+
+template <class V> __device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum NS per-thread values over the block; thread 0 writes them (as doubles) to out[0..NS).
+template <int NS, bool FP64>
+__device__ __forceinline__ void block_sum_store(const KSum (&loc)[NS], double* out) {
+  using V = typename Acc<FP64>::T;
+  __shared__ V red[NS][kRowBlock / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    V v = warp_sum<V>(V(loc[s].s) - V(loc[s].c));
+    if (lane == 0) red[s][wid] = v;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      V v = lane < (int)(blockDim.x >> 5) ? red[s][lane] : V(0);
+      v = warp_sum<V>(v);
+      if (lane == 0) out[s] = double(v);
+    }
+  }
+  __syncthreads();
+}
+
+// min over strictly positive values and max, stored to out[0], out[1]
+__device__ __forceinline__ void block_minmax_store(float mn, float mx, double* out) {
+  __shared__ float rmn[kRowBlock / 32], rmx[kRowBlock / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (lane == 0) { rmn[wid] = mn; rmx[wid] = mx; }
+  __syncthreads();
+  if (wid == 0) {
+    mn = lane < (int)(blockDim.x >> 5) ? rmn[lane] : f_inf();
+    mx = lane < (int)(blockDim.x >> 5) ? rmx[lane] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) { out[0] = mn; out[1] = mx; }
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------------------ row FFT pieces
+template <int W>
+__device__ __forceinline__ void row_load(const RowLayout<W / 2>& x, const float2* __restrict__ src, int t, bool act) {
+  using G = RowGeo<W>;
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < G::E; ++q) x(t + q * G::T) = src[t + q * G::T];
+  }
+}
+template <int W>
+__device__ __forceinline__ void row_store(const RowLayout<W / 2>& x, float2* __restrict__ dst, int t, bool act) {
+  using G = RowGeo<W>;
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < G::E; ++q) dst[t + q * G::T] = x(t + q * G::T);
+  }
+}
+
+// packed half spectrum X -> Z with IFFT_M(Z) = M (x[2n] + i x[2n+1])
+template <int W>
+__device__ __forceinline__ void c2r_pre(const RowLayout<W / 2>& x, int t, bool act) {
+  constexpr int M = W / 2, T = RowGeo<W>::T;
+  if (!act) return;
+  for (int k = t; k <= M / 2; k += T) {
+    if (k == 0) {
+      const float2 a = x(0);
+      x(0) = make_float2(0.5f * (a.x + a.y), 0.5f * (a.x - a.y));
+    } else {
+      const float2 a = x(k), b = x(M - k);
+      const float2 w = twl<W, true>(k);                       // exp(+2 pi i k / W)
+      const float2 e1 = make_float2(a.x + b.x, a.y - b.y);    // a + conj b
+      const float2 o1 = make_float2(a.x - b.x, a.y + b.y);    // a - conj b
+      const float2 wo = cmul(w, o1);
+      const float2 zk = make_float2(0.5f * (e1.x - wo.y), 0.5f * (e1.y + wo.x));   // (e1 + i w o1)/2
+      const float2 e2 = make_float2(b.x + a.x, b.y - a.y);    // b + conj a
+      const float2 o2 = make_float2(b.x - a.x, b.y + a.y);    // b - conj a
+      const float2 wo2 = cmul(cconj(w), o2);
+      const float2 zm = make_float2(0.5f * (e2.x + wo2.y), 0.5f * (e2.y - wo2.x));  // (e2 - i conj(w) o2)/2
+      x(k) = zk;
+      x(M - k) = zm;
+    }
+  }
+}
+
+// Z = FFT_M(z) -> packed half spectrum X
+template <int W>
+__device__ __forceinline__ void r2c_post(const RowLayout<W / 2>& x, int t, bool act) {
+  constexpr int M = W / 2, T = RowGeo<W>::T;
+  if (!act) return;
+  for (int k = t; k <= M / 2; k += T) {
+    if (k == 0) {
+      const float2 a = x(0);
+      x(0) = make_float2(a.x + a.y, a.x - a.y);
+    } else {
+      const float2 a = x(k), b = x(M - k);
+      const float2 w = twl<W, false>(k);                      // exp(-2 pi i k / W)
+      const float2 e1 = make_float2(a.x + b.x, a.y - b.y);
+      const float2 o1 = make_float2(a.x - b.x, a.y + b.y);
+      const float2 wo = cmul(w, o1);
+      const float2 xk = make_float2(0.5f * (e1.x + wo.y), 0.5f * (e1.y - wo.x));   // (e1 - i w o1)/2
+      const float2 e2 = make_float2(b.x + a.x, b.y - a.y);
+      const float2 o2 = make_float2(b.x - a.x, b.y + a.y);
+      const float2 wo2 = cmul(cconj(w), o2);
+      const float2 xm = make_float2(0.5f * (e2.x - wo2.y), 0.5f * (e2.y + wo2.x));  // (e2 + i conj(w) o2)/2
+      x(k) = xk;
+      x(M - k) = xm;
+    }
+  }
+}
+
+// spectrum row (global) -> real values (times M) in shared memory; ends synchronised
+template <int W>
+__device__ __forceinline__ void row_spec_to_real(const RowLayout<W / 2>& x, const float2* src, int t, bool act) {
+  row_load<W>(x, src, t, act);
+  __syncthreads();
+  c2r_pre<W>(x, t, act);
+  __syncthreads();
+  fft_inplace<W / 2, true>(x, t, act);
+}
+// real values in shared memory -> spectrum row (global); starts with a barrier
+template <int W>
+__device__ __forceinline__ void row_real_to_spec(const RowLayout<W / 2>& x, float2* dst, int t, bool act) {
+  __syncthreads();
+  fft_inplace<W / 2, false>(x, t, act);
+  r2c_post<W>(x, t, act);
+  __syncthreads();
+  row_store<W>(x, dst, t, act);
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------------------ generic passes
+// out[v] = R2C(max(in[v], 0) if clamp else in[v]) for nviews planes of H x W
+template <int W>
+__global__ void __launch_bounds__(kRowBlock) k_row_r2c(const float* __restrict__ in, size_t in_vs,
+                                                      float2* __restrict__ out, size_t out_vs,
+                                                      int H, int nviews, int clamp) {
+  using G = RowGeo<W>;
+  extern __shared__ float2 smem[];
+  const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
+  const RowLayout<G::M> x{smem + r * G::PITCH};
+  const int per_view = (H + G::ROWS - 1) / G::ROWS;
+  for (int it = blockIdx.x; it < nviews * per_view; it += gridDim.x) {
+    const int v = it / per_view;
+    const int row = (it % per_view) * G::ROWS + r;
+    const bool act = row < H;
+    const float2* src = reinterpret_cast<const float2*>(in + v * in_vs + size_t(row) * W);
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < G::E; ++q) {
+        float2 z = src[t + q * G::T];
+        if (clamp) { z.x = fmaxf(z.x, 0.0f); z.y = fmaxf(z.y, 0.0f); }
+        x(t + q * G::T) = z;
+      }
+    }
+    row_real_to_spec<W>(x, out + v * out_vs + size_t(row) * G::M, t, act);
+  }
+}
+
+// out[v] = scale * C2R(in[v])
+template <int W>
+__global__ void __launch_bounds__(kRowBlock) k_row_c2r(const float2* __restrict__ in, size_t in_vs,
+                                                      float* __restrict__ out, size_t out_vs,
+                                                      int H, int nviews, float scale) {
+  using G = RowGeo<W>;
+  extern __shared__ float2 smem[];
+  const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
+  const RowLayout<G::M> x{smem + r * G::PITCH};
+  const int per_view = (H + G::ROWS - 1) / G::ROWS;
+  for (int it = blockIdx.x; it < nviews * per_view; it += gridDim.x) {
+    const int v = it / per_view;
+    const int row = (it % per_view) * G::ROWS + r;
+    const bool act = row < H;
+    row_spec_to_real<W>(x, in + v * in_vs + size_t(row) * G::M, t, act);
+    float2* dst = reinterpret_cast<float2*>(out + v * out_vs + size_t(row) * W);
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < G::E; ++q) dst[t + q * G::T] = cscale(x(t + q * G::T), scale);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------ hot passes
+__device__ __forceinline__ float2 ld2(const float* p, size_t i) { return reinterpret_cast<const float2*>(p)[i]; }
+__device__ __forceinline__ void st2(float* p, size_t i, float2 v) { reinterpret_cast<float2*>(p)[i] = v; }
+__device__ __forceinline__ float clipf(float f, float L1, float L2) { return fminf(L2, fmaxf(L1, f)); }
+__device__ __forceinline__ float2 w_pair(const ImgDesc& d, size_t i) {
+  return d.w ? ld2(d.w, i) : make_float2(d.w_scalar, d.w_scalar);
+}
+__device__ __forceinline__ float2 b_pair(const ImgDesc& d, int j, size_t i) {
+  return d.b ? ld2(d.b + size_t(j) * d.P, i) : make_float2(d.bs[j], d.bs[j]);
+}
+// y = P(f - alpha D grad), D = w clip(f): non-negativity (mu = 0) or flux (mu from the search)
+__device__ __forceinline__ float proj_step(float f, float gr, float w, float alpha, float mu, float L1, float L2) {
+  const float D = w * clipf(f, L1, L2);
+  return fmaxf(f - D * fmaf(alpha, gr, mu), 0.0f);
+}
+__device__ __forceinline__ float2* spec_plane(const ImgDesc& d, int plane) {
+  return reinterpret_cast<float2*>(d.spec) + (size_t(plane) * d.P) / 2;
+}
+__device__ __forceinline__ double* part_of(const ImgDesc& d, int it) {
+  return d.part + size_t(it - d.row_item0) * kPartStride;
+}
+
+// SGP K1: apply the pending update f <- f + lambda d and A_j f <- A_j f + lambda A_j d (Alg. 1,
+// step 6), then r_j = g_j / (A_j f + b_j) -> R2C into planes 1..p, with the KL (and rho) partials.
+template <int W, bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_sgp_update_ratio(const ImgDesc* __restrict__ imgs,
+                                                               const int2* __restrict__ items, int n_items) {
+  using G = RowGeo<W>;
+  extern __shared__ float2 smem[];
+  const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
+  const RowLayout<G::M> x{smem + r * G::PITCH};
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int2 item = items[it];
+    const ImgDesc& d = imgs[item.x];
+    const CtrlState* c = d.ctrl;
+    const int done = c->done;
+    if (done >= 2) continue;
+    const int k = c->k, fresh = c->fresh, ke = k + (fresh ? 0 : 1);
+    const int row = item.y + r;
+    const bool act = row < d.H;
+    const size_t off = size_t(row) * G::M;
+    KSum acc[2];
+    float* fcur = d.f[ke & 1];
+    const float lam = float(c->lambda);
+    if (!fresh && act) {
+      const float* fo = d.f[k & 1];
+      const float* go = d.grad[k & 1];
+      const float alpha = float(c->alpha), mu = float(c->mu);
+      const float L1 = float(c->L1), L2 = float(c->L2);
+#pragma unroll 4
+      for (int q = 0; q < G::E; ++q) {
+        const size_t i = off + t + q * G::T;
+        const float2 f = ld2(fo, i), gr = ld2(go, i), w = w_pair(d, i);
+        float2 fn;
+        fn.x = fmaf(lam, proj_step(f.x, gr.x, w.x, alpha, mu, L1, L2) - f.x, f.x);
+        fn.y = fmaf(lam, proj_step(f.y, gr.y, w.y, alpha, mu, L1, L2) - f.y, f.y);
+        st2(fcur, i, fn);
+      }
+    }
+    if (done == 0 && act && d.ftrue && c->stop_kind == STOP_MIN_ERROR) {
+#pragma unroll 4
+      for (int q = 0; q < G::E; ++q) {
+        const size_t i = off + t + q * G::T;
+        const float2 f = ld2(fcur, i), ft = ld2(d.ftrue, i);
+        acc[1].add((f.x - ft.x) * (f.x - ft.x) + (f.y - ft.y) * (f.y - ft.y));
+      }
+    }
+    for (int j = 0; j < d.p; ++j) {
+      float* uj = d.u + size_t(j) * d.P;
+      const float* adj = d.Ad + size_t(j) * d.P;
+      const float* gj = d.g + size_t(j) * d.P;
+      if (act) {
+#pragma unroll 4
+        for (int q = 0; q < G::E; ++q) {
+          const size_t i = off + t + q * G::T;
+          float2 u = ld2(uj, i);
+          if (!fresh) {
+            const float2 a = ld2(adj, i);
+            u.x = fmaf(lam, a.x, u.x);
+            u.y = fmaf(lam, a.y, u.y);
+            st2(uj, i, u);
+          }
+          if (done == 0) {
+            const float2 g = ld2(gj, i), b = b_pair(d, j, i);
+            const float u0x = u.x + b.x, u0y = u.y + b.y;
+            acc[0].add(kl_term(g.x, u0x));
+            acc[0].add(kl_term(g.y, u0y));
+            x(t + q * G::T) = make_float2(ratio_term(g.x, u0x), ratio_term(g.y, u0y));
+          }
+        }
+      }
+      if (done == 0) row_real_to_spec<W>(x, spec_plane(d, j + 1) + off, t, act);
+    }
+    if (done == 0) block_sum_store<2, FP64>(acc, part_of(d, it) + SLOT_KL);
+  }
+}
+
+// SGP K3: C2R of plane 0 (= sum_j A_j^T r_j) -> gradient, and the four scaled-BB partial sums.
+template <int W, bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
+                                                          const int2* __restrict__ items, int n_items) {
+  using G = RowGeo<W>;
+  extern __shared__ float2 smem[];
+  const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
+  const RowLayout<G::M> x{smem + r * G::PITCH};
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int2 item = items[it];
+    const ImgDesc& d = imgs[item.x];
+    const CtrlState* c = d.ctrl;
+    if (c->done >= 1) continue;
+    const int ke = c->k + (c->fresh ? 0 : 1);
+    const int row = item.y + r;
+    const bool act = row < d.H;
+    const size_t off = size_t(row) * G::M;
+    row_spec_to_real<W>(x, spec_plane(d, 0) + off, t, act);
+    KSum acc[4];
+    if (act) {
+      const float* f = d.f[ke & 1];
+      const float* fp = d.f[(ke + 1) & 1];
+      const float* gp = d.grad[(ke + 1) & 1];
+      float* gn = d.grad[ke & 1];
+      const float L1 = float(c->L1), L2 = float(c->L2);
+      const bool bb = ke >= 1;
+#pragma unroll 4
+      for (int q = 0; q < G::E; ++q) {
+        const size_t i = off + t + q * G::T;
+        const float2 v = x(t + q * G::T), w = w_pair(d, i);
+        const float a1x = d.w ? (w.x > 0.0f ? 1.0f / w.x : 0.0f) : d.a1_scalar;
+        const float a1y = d.w ? (w.y > 0.0f ? 1.0f / w.y : 0.0f) : d.a1_scalar;
+        float2 gr;
+        gr.x = w.x > 0.0f ? a1x - v.x : 0.0f;
+        gr.y = w.y > 0.0f ? a1y - v.y : 0.0f;
+        st2(gn, i, gr);
+        if (bb) {
+          const float2 fc = ld2(f, i), fo = ld2(fp, i), go = ld2(gp, i);
+          const float sx = fc.x - fo.x, sy = fc.y - fo.y, zx = gr.x - go.x, zy = gr.y - go.y;
+          const float Dx = w.x * clipf(fc.x, L1, L2), Dy = w.y * clipf(fc.y, L1, L2);
+          if (Dx > 0.0f) {
+            const float sd = sx / Dx, zd = zx * Dx;
+            acc[0].add(sd * sd); acc[1].add(sd * zx); acc[2].add(sx * zd); acc[3].add(zd * zd);
+          }
+          if (Dy > 0.0f) {
+            const float sd = sy / Dy, zd = zy * Dy;
+            acc[0].add(sd * sd); acc[1].add(sd * zy); acc[2].add(sy * zd); acc[3].add(zd * zd);
+          }
+        }
+      }
+    }
+    block_sum_store<4, FP64>(acc, part_of(d, it) + SLOT_BB);
+  }
+}
+
+// SGP K4: y = P(f - alpha D grad) (Alg. 1 step 2) -> R2C into plane 0, with the grad'd partials.
+template <int W, bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_sgp_y(const ImgDesc* __restrict__ imgs,
+                                                    const int2* __restrict__ items, int n_items) {
+  using G = RowGeo<W>;
+  extern __shared__ float2 smem[];
+  const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
+  const RowLayout<G::M> x{smem + r * G::PITCH};
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int2 item = items[it];
+    const ImgDesc& d = imgs[item.x];
+    const CtrlState* c = d.ctrl;
+    if (c->done >= 1) continue;
+    const int k = c->k;
+    const int row = item.y + r;
+    const bool act = row < d.H;
+    const size_t off = size_t(row) * G::M;
+    KSum acc[1];
+    if (act) {
+      const float* f = d.f[k & 1];
+      const float* gr = d.grad[k & 1];
+      const float alpha = float(c->alpha), mu = float(c->mu), L1 = float(c->L1), L2 = float(c->L2);
+#pragma unroll 4
+      for (int q = 0; q < G::E; ++q) {
+        const size_t i = off + t + q * G::T;
+        const float2 fv = ld2(f, i), gv = ld2(gr, i), w = w_pair(d, i);
+        const float yx = proj_step(fv.x, gv.x, w.x, alpha, mu, L1, L2);
+        const float yy = proj_step(fv.y, gv.y, w.y, alpha, mu, L1, L2);
+        acc[0].add(gv.x * (yx - fv.x));
+        acc[0].add(gv.y * (yy - fv.y));
+        x(t + q * G::T) = make_float2(yx, yy);
+      }
+    }
+    row_real_to_spec<W>(x, spec_plane(d, 0) + off, t, act);
+    block_sum_store<1, FP64>(acc, part_of(d, it) + SLOT_GTD);
+  }
+}
+
+// SGP K6: per view, C2R of plane j+1 (= A_j y) -> A_j d = A_j y - A_j f (linearity, no FFT per
+// backtrack) and the Armijo partial sums Delta J(theta^i), i = 0..3 (Alg. 1 step 5).
+template <int W, bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_sgp_ad_armijo(const ImgDesc* __restrict__ imgs,
+                                                            const int2* __restrict__ items, int n_items) {
+  using G = RowGeo<W>;
+  extern __shared__ float2 smem[];
+  const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
+  const RowLayout<G::M> x{smem + r * G::PITCH};
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int2 item = items[it];
+    const ImgDesc& d = imgs[item.x];
+    const CtrlState* c = d.ctrl;
+    if (c->done >= 1) continue;
+    const int row = item.y + r;
+    const bool act = row < d.H;
+    const size_t off = size_t(row) * G::M;
+    const float th = float(c->theta);
+    const float lam[4] = {1.0f, th, th * th, th * th * th};
+    KSum acc[4];
+    for (int j = 0; j < d.p; ++j) {
+      row_spec_to_real<W>(x, spec_plane(d, j + 1) + off, t, act);
+      if (act) {
+        const float* uj = d.u + size_t(j) * d.P;
+        float* adj = d.Ad + size_t(j) * d.P;
+        const float* gj = d.g + size_t(j) * d.P;
+#pragma unroll 2
+        for (int q = 0; q < G::E; ++q) {
+          const size_t i = off + t + q * G::T;
+          const float2 ay = x(t + q * G::T), u = ld2(uj, i), g = ld2(gj, i), b = b_pair(d, j, i);
+          const float2 ad = make_float2(ay.x - u.x, ay.y - u.y);
+          st2(adj, i, ad);
+          const float u0x = u.x + b.x, u0y = u.y + b.y;
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            acc[l].add(armijo_term(g.x, u0x, lam[l] * ad.x));
+            acc[l].add(armijo_term(g.y, u0y, lam[l] * ad.y));
+          }
+        }
+      }
+      __syncthreads();
+    }
+    block_sum_store<4, FP64>(acc, part_of(d, it) + SLOT_ARM);
+  }
+}
+
+// SGP K7 (only when no lambda in {1, .., theta^3} was accepted): Delta J(theta^i), i = 4..30.
+template <int W, bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_sgp_armijo_extra(const ImgDesc* __restrict__ imgs,
+                                                               const int2* __restrict__ items, int n_items) {
+  using G = RowGeo<W>;
+  const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int2 item = items[it];
+    const ImgDesc& d = imgs[item.x];
+    const CtrlState* c = d.ctrl;
+    if (c->done >= 1 || !c->need_more) continue;
+    const int row = item.y + r;
+    const bool act = row < d.H;
+    const size_t off = size_t(row) * G::M;
+    const float th = float(c->theta);
+    KSum acc[kArmExtra];
+    if (act) {
+      for (int j = 0; j < d.p; ++j) {
+        const float* uj = d.u + size_t(j) * d.P;
+        const float* adj = d.Ad + size_t(j) * d.P;
+        const float* gj = d.g + size_t(j) * d.P;
+        for (int q = 0; q < G::E; ++q) {
+          const size_t i = off + t + q * G::T;
+          const float2 u = ld2(uj, i), ad = ld2(adj, i), g = ld2(gj, i), b = b_pair(d, j, i);
+          const float u0x = u.x + b.x, u0y = u.y + b.y;
+          float lam = th * th * th * th;
+#pragma unroll
+          for (int l = 0; l < kArmExtra; ++l) {
+            acc[l].add(armijo_term(g.x, u0x, lam * ad.x));
+            acc[l].add(armijo_term(g.y, u0y, lam * ad.y));
+            lam *= th;
+          }
+        }
+      }
+    }
+    block_sum_store<kArmExtra, FP64>(acc, part_of(d, it) + SLOT_ARMX);
+  }
+}
+
+// RL K1: if plane 0 holds v = sum_j A_j^T r_j, f <- w f v (Eq. RL / multipleRL / boundaryRL);
+// then R2C of the current iterate into plane 0 (and the rho partial).
+template <int W, bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_rl_update(const ImgDesc* __restrict__ imgs,
+                                                        const int2* __restrict__ items, int n_items) {
+  using G = RowGeo<W>;
+  extern __shared__ float2 smem[];
+  const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
+  const RowLayout<G::M> x{smem + r * G::PITCH};
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int2 item = items[it];
+    const ImgDesc& d = imgs[item.x];
+    const CtrlState* c = d.ctrl;
+    if (c->done >= 2) continue;
+    const int k = c->k, hv = c->have_v, ke = k + hv;
+    const int row = item.y + r;
+    const bool act = row < d.H;
+    const size_t off = size_t(row) * G::M;
+    float2* sp = spec_plane(d, 0) + off;
+    if (hv) row_spec_to_real<W>(x, sp, t, act);
+    KSum acc[1];
+    if (act) {
+      const float* fo = d.f[k & 1];
+      float* fn = d.f[ke & 1];
+      const bool rho = d.ftrue && c->stop_kind == STOP_MIN_ERROR;
+#pragma unroll 4
+      for (int q = 0; q < G::E; ++q) {
+        const size_t i = off + t + q * G::T;
+        float2 f = ld2(fo, i);
+        if (hv) {
+          const float2 v = x(t + q * G::T), w = w_pair(d, i);
+          f.x = w.x * f.x * v.x;
+          f.y = w.y * f.y * v.y;
+          st2(fn, i, f);
+        }
+        if (rho) {
+          const float2 ft = ld2(d.ftrue, i);
+          acc[0].add((f.x - ft.x) * (f.x - ft.x) + (f.y - ft.y) * (f.y - ft.y));
+        }
+        x(t + q * G::T) = f;
+      }
+    }
+    row_real_to_spec<W>(x, sp, t, act);
+    block_sum_store<1, FP64>(acc, part_of(d, it) + SLOT_RHO);
+  }
+}
+
+// RL K3 (also a set-up pass): per view, C2R of plane j+1 (= A_j f) -> KL partials and
+// r_j = g_j/(A_j f + b_j) -> R2C back into plane j+1; optionally stores A_j f into u.
+template <int W, bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_rl_ratio(const ImgDesc* __restrict__ imgs,
+                                                       const int2* __restrict__ items, int n_items, int write_u) {
+  using G = RowGeo<W>;
+  extern __shared__ float2 smem[];
+  const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
+  const RowLayout<G::M> x{smem + r * G::PITCH};
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int2 item = items[it];
+    const ImgDesc& d = imgs[item.x];
+    if (d.ctrl->done >= 2) continue;
+    const int row = item.y + r;
+    const bool act = row < d.H;
+    const size_t off = size_t(row) * G::M;
+    KSum acc[1];
+    for (int j = 0; j < d.p; ++j) {
+      float2* sp = spec_plane(d, j + 1) + off;
+      row_spec_to_real<W>(x, sp, t, act);
+      if (act) {
+        float* uj = d.u + size_t(j) * d.P;
+        const float* gj = d.g + size_t(j) * d.P;
+#pragma unroll 4
+        for (int q = 0; q < G::E; ++q) {
+          const size_t i = off + t + q * G::T;
+          const float2 u = x(t + q * G::T), g = ld2(gj, i), b = b_pair(d, j, i);
+          if (write_u) st2(uj, i, u);
+          const float u0x = u.x + b.x, u0y = u.y + b.y;
+          acc[0].add(kl_term(g.x, u0x));
+          acc[0].add(kl_term(g.y, u0y));
+          x(t + q * G::T) = make_float2(ratio_term(g.x, u0x), ratio_term(g.y, u0y));
+        }
+      }
+      row_real_to_spec<W>(x, sp, t, act);
+    }
+    block_sum_store<1, FP64>(acc, part_of(d, it) + SLOT_KL);
+  }
+}
+
+// Set-up: y = w f v from plane 0 (one RL step from f^(0), Sect. 3.2); min over positive y and max y.
+template <int W>
+__global__ void __launch_bounds__(kRowBlock) k_rl_step_minmax(const ImgDesc* __restrict__ imgs,
+                                                             const int2* __restrict__ items, int n_items) {
+  using G = RowGeo<W>;
+  extern __shared__ float2 smem[];
+  const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
+  const RowLayout<G::M> x{smem + r * G::PITCH};
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int2 item = items[it];
+    const ImgDesc& d = imgs[item.x];
+    const int row = item.y + r;
+    const bool act = row < d.H;
+    const size_t off = size_t(row) * G::M;
+    row_spec_to_real<W>(x, spec_plane(d, 0) + off, t, act);
+    float mn = f_inf(), mx = 0.0f;
+    if (act) {
+      const float* f = d.f[d.ctrl->k & 1];
+      for (int q = 0; q < G::E; ++q) {
+        const size_t i = off + t + q * G::T;
+        const float2 v = x(t + q * G::T), fv = ld2(f, i), w = w_pair(d, i);
+        const float y0 = w.x * fv.x * v.x, y1 = w.y * fv.y * v.y;
+        if (y0 > 0.0f) mn = fminf(mn, y0);
+        if (y1 > 0.0f) mn = fminf(mn, y1);
+        mx = fmaxf(mx, fmaxf(y0, y1));
+      }
+    }
+    block_minmax_store(mn, mx, part_of(d, it) + SLOT_MIN);
+  }
+}
+
+}  // namespace sgp

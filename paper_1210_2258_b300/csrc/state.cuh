@@ -1,0 +1,99 @@
+// Device-resident problem state shared by the kernels and the host runtime.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace sgp {
+
+constexpr int kMaxViews = 8;        // p <= 8 views per problem
+constexpr int kMaxHist = 16;        // >= M_alpha
+constexpr int kPartStride = 48;     // doubles of partial sums per row item
+constexpr int kTraceStride = 8;     // doubles per trace record
+constexpr int kRowBlock = 256;      // threads of every row-pass block
+constexpr int kColBlock = 512;      // threads of every column-pass block
+constexpr int kCtrlBlock = 256;     // threads of the controller blocks
+
+// partial-sum slots (per row item)
+enum Slot {
+  SLOT_KL = 0,        // sum of KL terms (J_0)
+  SLOT_RHO = 1,       // sum (f - f_true)^2
+  SLOT_BB = 2,        // 4 slots: s'D^-2 s, s'D^-1 z, s'D z, z'D^2 z
+  SLOT_GTD = 6,       // grad' d
+  SLOT_FLUX = 7,      // sum f
+  SLOT_ARM = 8,       // 4 slots: Delta J(theta^i), i = 0..3
+  SLOT_ARMX = 12,     // 27 slots: Delta J(theta^i), i = 4..30
+  SLOT_MIN = 40,      // min over positive pixels (set-up)
+  SLOT_MAX = 41,      // max (set-up)
+  SLOT_PROJ = 42,     // flux projection search sums (up to 6)
+};
+constexpr int kArmExtra = 27;
+
+enum StopKind { STOP_FIXED = 0, STOP_CONVERGENCE = 1, STOP_DISCREPANCY = 2, STOP_MIN_ERROR = 3 };
+
+// Controller state of one problem (in the workspace; read by every hot kernel).
+struct CtrlState {
+  int k;            // index of the current iterate f^(k)
+  int fresh;        // SGP: 1 when f[k&1] is current, 0 when f^(k+1) = f^(k) + lambda d is pending
+  int done;         // 0 running; 1 stop decided, final SGP update pending; 2 stopped
+  int status;       // device-side status (sgp_status code), 0 = OK
+  int need_more;    // Armijo: no lambda in {1..theta^3} accepted yet
+  int have_v;       // RL: spectrum plane 0 holds sum_j A_j^T r_j of the current iterate
+  int branch;       // 0: alpha_0, 1: BB1, 2: windowed BB2
+  int backtracks;
+  int result_prev;  // min-error stop: the result is the previous iterate f[(k-1)&1]
+  int hist_n;
+  int trace_n, trace_cap;
+  int stop_kind, max_iter;
+  int M_alpha, warmup, max_backtracks, fp64;
+  int constraint;   // 0 non-negativity, 1 + flux
+  int proj_pass;    // flux projection search pass
+  double J;         // J_0 at the current iterate
+  double J_pred;    // J_0 at the accepted trial point
+  double alpha, alpha_prev, tau, lambda, gTd, dJ, mu, rho_prev, rho;
+  double L1, L2;
+  double hist[kMaxHist];
+  double beta, theta, alpha0, tau1, alpha_min, alpha_max;
+  double tol, eta, inv_pS, ftrue_norm2, flux_c;
+  double mu_lo, mu_hi, phi_lo, phi_hi;
+  double scratch[8];
+};
+
+// One problem (p views of an H x W object) as the kernels see it.  Arrays are FP32 row-major with
+// P = H*W elements per plane; spectra are H x W/2 complex (the real DC and Nyquist columns of the
+// row transform share column 0 as real and imaginary part), i.e. also P floats per plane.
+struct ImgDesc {
+  int H, W, p, boundary;
+  int row_item0, n_row_items;   // this problem's items in the row-item list
+  float w_scalar;               // periodic: 1/p (RL factor, SGP scaling factor)
+  float a1_scalar;              // periodic: p (= sum_j A_j^T 1)
+  float bs[kMaxViews];          // constant backgrounds (used when b == nullptr)
+  size_t P;
+  float* f[2];                  // iterate ping-pong
+  float* grad[2];               // gradient ping-pong
+  float* u;                     // p planes: A_j f (without b)
+  float* Ad;                    // p planes: A_j d
+  float* g;                     // p planes: data; -1 marks pixels outside S (boundary mode)
+  const float* b;               // p planes or nullptr
+  const float* w;               // boundary: M_R / alpha (0 outside R); nullptr when periodic
+  float* spec;                  // (p+1) planes of packed spectra: plane 0, then views 1..p
+  const float* ftrue;           // min-error stop only
+  CtrlState* ctrl;
+  double* part;                 // n_row_items x kPartStride
+  double* trace;                // trace_cap x kTraceStride
+};
+
+// A column-pass job: one problem's spectrum planes and PSF spectra.
+struct ColJob {
+  const float2* in;     // nin planes (plane_stride apart)
+  float2* out;          // nout planes
+  const float2* khat;   // p planes H x M (column 0 holds P = (K0 + KM)/2)
+  float2* khatq;        // p columns of H: Q = (K0 - KM)/2 (written by the spectrum set-up pass)
+  int H, M, nin, nout;
+  size_t plane_stride;  // float2 elements between planes (= H*M)
+  const CtrlState* ctrl;  // skip when ctrl->done >= 1 (nullptr: always run)
+  float scale;          // spectrum set-up: 1/(H*M*sum K)
+  int corner;           // spectrum set-up: PSF origin already at (0,0)
+};
+
+}  // namespace sgp
