@@ -86,6 +86,9 @@ __device__ float2 g_twiddle[kTwiddleTotal];
 
 template <int L, bool INV>
 __device__ __forceinline__ float2 twl(int q) {  // exp(-/+ 2 pi i q / L), 0 <= q < L
+  // the empty asm keeps the load after the preceding barrier: read-only loads may otherwise be
+  // hoisted across every stage of a transform, costing many live registers
+  asm volatile("" : "+r"(q));
   const float2 w = __ldg(&g_twiddle[tw_offset(L) + q]);
   return INV ? cconj(w) : w;
 }
@@ -210,7 +213,13 @@ template <int L> __host__ __device__ constexpr int col_rows_padded() { return L 
 // One radix-R stage of a length-L transform run by T threads (t in [0, T)).  Every thread of the
 // block calls it (it synchronises); threads with act == false only synchronise.
 template <int L, int R, int NS, int T, bool INV, class Lay>
-__device__ __forceinline__ void stockham_stage(const Lay& x, int t, bool act) {
+__device__ __forceinline__ void stockham_stage(const Lay& x0, int t, bool act) {
+  // Opaque copies of the thread index and base pointer: without them the compiler hoists the
+  // shared-memory addresses of every stage (and of every loop iteration around the transform)
+  // to the top of the kernel and keeps them all live.
+  asm volatile("" : "+r"(t));
+  Lay x = x0;
+  asm volatile("" : "+l"(x.base));
   constexpr int NB = L / R;
   constexpr int PER = NB / T;
   static_assert(PER * T == NB, "plan: each radix must divide the per-thread count");

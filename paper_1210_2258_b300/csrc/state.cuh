@@ -64,7 +64,8 @@ struct CtrlState {
 // row transform share column 0 as real and imaginary part), i.e. also P floats per plane.
 struct ImgDesc {
   int H, W, p, boundary;
-  int row_item0, n_row_items;   // this problem's items in the row-item list
+  int row_item0, n_row_items;   // this problem's items in the row-item list (image, row0)
+  int rv_item0, n_rv_items;     // ... and in the row-view list (image, row0 | view << 16)
   float w_scalar;               // periodic: 1/p (RL factor, SGP scaling factor)
   float a1_scalar;              // periodic: p (= sum_j A_j^T 1)
   float bs[kMaxViews];          // constant backgrounds (used when b == nullptr)
@@ -79,7 +80,8 @@ struct ImgDesc {
   float* spec;                  // (p+1) planes of packed spectra: plane 0, then views 1..p
   const float* ftrue;           // min-error stop only
   CtrlState* ctrl;
-  double* part;                 // n_row_items x kPartStride
+  double* part;                 // n_row_items x kPartStride (row-list passes)
+  double* partv;                // n_rv_items x kPartStride (row-view-list passes)
   double* trace;                // trace_cap x kTraceStride
 };
 
