@@ -239,7 +239,9 @@ __global__ void __launch_bounds__(kRowBlock) k_row_r2c(const float* __restrict__
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
   const RowLayout<G::M> x{smem + r * G::PITCH};
   const int per_view = (H + G::ROWS - 1) / G::ROWS;
-  for (int it = blockIdx.x; it < nviews * per_view; it += gridDim.x) {
+  {
+    const int it = blockIdx.x;
+    if (it >= nviews * per_view) return;
     const int v = it / per_view;
     const int row = (it % per_view) * G::ROWS + r;
     const bool act = row < H;
@@ -266,7 +268,9 @@ __global__ void __launch_bounds__(kRowBlock) k_row_c2r(const float2* __restrict_
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
   const RowLayout<G::M> x{smem + r * G::PITCH};
   const int per_view = (H + G::ROWS - 1) / G::ROWS;
-  for (int it = blockIdx.x; it < nviews * per_view; it += gridDim.x) {
+  {
+    const int it = blockIdx.x;
+    if (it >= nviews * per_view) return;
     const int v = it / per_view;
     const int row = (it % per_view) * G::ROWS + r;
     const bool act = row < H;
@@ -301,6 +305,12 @@ __device__ __forceinline__ float2* spec_plane(const ImgDesc& d, int plane) {
 __device__ __forceinline__ double* part_of(const ImgDesc& d, int it) {
   return d.part + size_t(it - d.row_item0) * kPartStride;
 }
+__device__ __forceinline__ double* partv_of(const ImgDesc& d, int it) {
+  return d.partv + size_t(it - d.rv_item0) * kPartStride;
+}
+// view-list items carry the view index in the high bits of .y
+__device__ __forceinline__ int item_row(int2 item) { return item.y & 0xffff; }
+__device__ __forceinline__ int item_view(int2 item) { return item.y >> 16; }
 
 // SGP K1: apply the pending update f <- f + lambda d and A_j f <- A_j f + lambda A_j d (Alg. 1,
 // step 6), then r_j = g_j / (A_j f + b_j) -> R2C into planes 1..p, with the KL (and rho) partials.
@@ -311,20 +321,23 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_update_ratio(const ImgDesc* _
   extern __shared__ float2 smem[];
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
   const RowLayout<G::M> x{smem + r * G::PITCH};
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int2 item = items[it];
-    const ImgDesc& d = imgs[item.x];
-    const CtrlState* c = d.ctrl;
-    const int done = c->done;
-    if (done >= 2) continue;
-    const int k = c->k, fresh = c->fresh, ke = k + (fresh ? 0 : 1);
-    const int row = item.y + r;
-    const bool act = row < d.H;
-    const size_t off = size_t(row) * G::M;
-    KSum acc[2];
+  const int it = blockIdx.x;
+  if (it >= n_items) return;
+  const int2 item = items[it];
+  const ImgDesc& d = imgs[item.x];
+  const CtrlState* c = d.ctrl;
+  const int done = c->done;
+  if (done >= 2) return;
+  const int j = item_view(item);
+  const int k = c->k, fresh = c->fresh, ke = k + (fresh ? 0 : 1);
+  const int row = item_row(item) + r;
+  const bool act = row < d.H;
+  const size_t off = size_t(row) * G::M;
+  KSum acc[2];
+  const float lam = float(c->lambda);
+  if (j == 0 && act) {
     float* fcur = d.f[ke & 1];
-    const float lam = float(c->lambda);
-    if (!fresh && act) {
+    if (!fresh) {
       const float* fo = d.f[k & 1];
       const float* go = d.grad[k & 1];
       const float alpha = float(c->alpha), mu = float(c->mu);
@@ -339,41 +352,40 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_update_ratio(const ImgDesc* _
         st2(fcur, i, fn);
       }
     }
-    if (done == 0 && act && d.ftrue && c->stop_kind == STOP_MIN_ERROR) {
-#pragma unroll 4
+    if (done == 0 && d.ftrue && c->stop_kind == STOP_MIN_ERROR) {
       for (int q = 0; q < G::E; ++q) {
         const size_t i = off + t + q * G::T;
         const float2 f = ld2(fcur, i), ft = ld2(d.ftrue, i);
         acc[1].add((f.x - ft.x) * (f.x - ft.x) + (f.y - ft.y) * (f.y - ft.y));
       }
     }
-    for (int j = 0; j < d.p; ++j) {
-      float* uj = d.u + size_t(j) * d.P;
-      const float* adj = d.Ad + size_t(j) * d.P;
-      const float* gj = d.g + size_t(j) * d.P;
-      if (act) {
+  }
+  float* uj = d.u + size_t(j) * d.P;
+  const float* adj = d.Ad + size_t(j) * d.P;
+  const float* gj = d.g + size_t(j) * d.P;
+  if (act) {
 #pragma unroll 4
-        for (int q = 0; q < G::E; ++q) {
-          const size_t i = off + t + q * G::T;
-          float2 u = ld2(uj, i);
-          if (!fresh) {
-            const float2 a = ld2(adj, i);
-            u.x = fmaf(lam, a.x, u.x);
-            u.y = fmaf(lam, a.y, u.y);
-            st2(uj, i, u);
-          }
-          if (done == 0) {
-            const float2 g = ld2(gj, i), b = b_pair(d, j, i);
-            const float u0x = u.x + b.x, u0y = u.y + b.y;
-            acc[0].add(kl_term(g.x, u0x));
-            acc[0].add(kl_term(g.y, u0y));
-            x(t + q * G::T) = make_float2(ratio_term(g.x, u0x), ratio_term(g.y, u0y));
-          }
-        }
+    for (int q = 0; q < G::E; ++q) {
+      const size_t i = off + t + q * G::T;
+      float2 u = ld2(uj, i);
+      if (!fresh) {
+        const float2 a = ld2(adj, i);
+        u.x = fmaf(lam, a.x, u.x);
+        u.y = fmaf(lam, a.y, u.y);
+        st2(uj, i, u);
       }
-      if (done == 0) row_real_to_spec<W>(x, spec_plane(d, j + 1) + off, t, act);
+      if (done == 0) {
+        const float2 g = ld2(gj, i), b = b_pair(d, j, i);
+        const float u0x = u.x + b.x, u0y = u.y + b.y;
+        acc[0].add(kl_term(g.x, u0x));
+        acc[0].add(kl_term(g.y, u0y));
+        x(t + q * G::T) = make_float2(ratio_term(g.x, u0x), ratio_term(g.y, u0y));
+      }
     }
-    if (done == 0) block_sum_store<2, FP64>(acc, part_of(d, it) + SLOT_KL);
+  }
+  if (done == 0) {
+    row_real_to_spec<W>(x, spec_plane(d, j + 1) + off, t, act);
+    block_sum_store<2, FP64>(acc, partv_of(d, it) + SLOT_KL);
   }
 }
 
@@ -385,13 +397,15 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_grad_bb(const ImgDesc* __rest
   extern __shared__ float2 smem[];
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
   const RowLayout<G::M> x{smem + r * G::PITCH};
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+  {
+    const int it = blockIdx.x;
+    if (it >= n_items) return;
     const int2 item = items[it];
     const ImgDesc& d = imgs[item.x];
     const CtrlState* c = d.ctrl;
-    if (c->done >= 1) continue;
+    if (c->done >= 1) return;
     const int ke = c->k + (c->fresh ? 0 : 1);
-    const int row = item.y + r;
+    const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
     row_spec_to_real<W>(x, spec_plane(d, 0) + off, t, act);
@@ -440,13 +454,15 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_y(const ImgDesc* __restrict__
   extern __shared__ float2 smem[];
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
   const RowLayout<G::M> x{smem + r * G::PITCH};
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+  {
+    const int it = blockIdx.x;
+    if (it >= n_items) return;
     const int2 item = items[it];
     const ImgDesc& d = imgs[item.x];
     const CtrlState* c = d.ctrl;
-    if (c->done >= 1) continue;
+    if (c->done >= 1) return;
     const int k = c->k;
-    const int row = item.y + r;
+    const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
     KSum acc[1];
@@ -479,41 +495,39 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_ad_armijo(const ImgDesc* __re
   extern __shared__ float2 smem[];
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
   const RowLayout<G::M> x{smem + r * G::PITCH};
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int2 item = items[it];
-    const ImgDesc& d = imgs[item.x];
-    const CtrlState* c = d.ctrl;
-    if (c->done >= 1) continue;
-    const int row = item.y + r;
-    const bool act = row < d.H;
-    const size_t off = size_t(row) * G::M;
-    const float th = float(c->theta);
-    const float lam[4] = {1.0f, th, th * th, th * th * th};
-    KSum acc[4];
-    for (int j = 0; j < d.p; ++j) {
-      row_spec_to_real<W>(x, spec_plane(d, j + 1) + off, t, act);
-      if (act) {
-        const float* uj = d.u + size_t(j) * d.P;
-        float* adj = d.Ad + size_t(j) * d.P;
-        const float* gj = d.g + size_t(j) * d.P;
+  const int it = blockIdx.x;
+  if (it >= n_items) return;
+  const int2 item = items[it];
+  const ImgDesc& d = imgs[item.x];
+  const CtrlState* c = d.ctrl;
+  if (c->done >= 1) return;
+  const int j = item_view(item);
+  const int row = item_row(item) + r;
+  const bool act = row < d.H;
+  const size_t off = size_t(row) * G::M;
+  const float th = float(c->theta);
+  const float lam[4] = {1.0f, th, th * th, th * th * th};
+  KSum acc[4];
+  row_spec_to_real<W>(x, spec_plane(d, j + 1) + off, t, act);
+  if (act) {
+    const float* uj = d.u + size_t(j) * d.P;
+    float* adj = d.Ad + size_t(j) * d.P;
+    const float* gj = d.g + size_t(j) * d.P;
 #pragma unroll 2
-        for (int q = 0; q < G::E; ++q) {
-          const size_t i = off + t + q * G::T;
-          const float2 ay = x(t + q * G::T), u = ld2(uj, i), g = ld2(gj, i), b = b_pair(d, j, i);
-          const float2 ad = make_float2(ay.x - u.x, ay.y - u.y);
-          st2(adj, i, ad);
-          const float u0x = u.x + b.x, u0y = u.y + b.y;
+    for (int q = 0; q < G::E; ++q) {
+      const size_t i = off + t + q * G::T;
+      const float2 ay = x(t + q * G::T), u = ld2(uj, i), g = ld2(gj, i), b = b_pair(d, j, i);
+      const float2 ad = make_float2(ay.x - u.x, ay.y - u.y);
+      st2(adj, i, ad);
+      const float u0x = u.x + b.x, u0y = u.y + b.y;
 #pragma unroll
-          for (int l = 0; l < 4; ++l) {
-            acc[l].add(armijo_term(g.x, u0x, lam[l] * ad.x));
-            acc[l].add(armijo_term(g.y, u0y, lam[l] * ad.y));
-          }
-        }
+      for (int l = 0; l < 4; ++l) {
+        acc[l].add(armijo_term(g.x, u0x, lam[l] * ad.x));
+        acc[l].add(armijo_term(g.y, u0y, lam[l] * ad.y));
       }
-      __syncthreads();
     }
-    block_sum_store<4, FP64>(acc, part_of(d, it) + SLOT_ARM);
   }
+  block_sum_store<4, FP64>(acc, partv_of(d, it) + SLOT_ARM);
 }
 
 // SGP K7 (only when no lambda in {1, .., theta^3} was accepted): Delta J(theta^i), i = 4..30.
@@ -522,12 +536,14 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_armijo_extra(const ImgDesc* _
                                                                const int2* __restrict__ items, int n_items) {
   using G = RowGeo<W>;
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+  {
+    const int it = blockIdx.x;
+    if (it >= n_items) return;
     const int2 item = items[it];
     const ImgDesc& d = imgs[item.x];
     const CtrlState* c = d.ctrl;
-    if (c->done >= 1 || !c->need_more) continue;
-    const int row = item.y + r;
+    if (c->done >= 1 || !c->need_more) return;
+    const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
     const float th = float(c->theta);
@@ -564,13 +580,15 @@ __global__ void __launch_bounds__(kRowBlock) k_rl_update(const ImgDesc* __restri
   extern __shared__ float2 smem[];
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
   const RowLayout<G::M> x{smem + r * G::PITCH};
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+  {
+    const int it = blockIdx.x;
+    if (it >= n_items) return;
     const int2 item = items[it];
     const ImgDesc& d = imgs[item.x];
     const CtrlState* c = d.ctrl;
-    if (c->done >= 2) continue;
+    if (c->done >= 2) return;
     const int k = c->k, hv = c->have_v, ke = k + hv;
-    const int row = item.y + r;
+    const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
     float2* sp = spec_plane(d, 0) + off;
@@ -611,35 +629,34 @@ __global__ void __launch_bounds__(kRowBlock) k_rl_ratio(const ImgDesc* __restric
   extern __shared__ float2 smem[];
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
   const RowLayout<G::M> x{smem + r * G::PITCH};
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int2 item = items[it];
-    const ImgDesc& d = imgs[item.x];
-    if (d.ctrl->done >= 2) continue;
-    const int row = item.y + r;
-    const bool act = row < d.H;
-    const size_t off = size_t(row) * G::M;
-    KSum acc[1];
-    for (int j = 0; j < d.p; ++j) {
-      float2* sp = spec_plane(d, j + 1) + off;
-      row_spec_to_real<W>(x, sp, t, act);
-      if (act) {
-        float* uj = d.u + size_t(j) * d.P;
-        const float* gj = d.g + size_t(j) * d.P;
+  const int it = blockIdx.x;
+  if (it >= n_items) return;
+  const int2 item = items[it];
+  const ImgDesc& d = imgs[item.x];
+  if (d.ctrl->done >= 2) return;
+  const int j = item_view(item);
+  const int row = item_row(item) + r;
+  const bool act = row < d.H;
+  const size_t off = size_t(row) * G::M;
+  KSum acc[1];
+  float2* sp = spec_plane(d, j + 1) + off;
+  row_spec_to_real<W>(x, sp, t, act);
+  if (act) {
+    float* uj = d.u + size_t(j) * d.P;
+    const float* gj = d.g + size_t(j) * d.P;
 #pragma unroll 4
-        for (int q = 0; q < G::E; ++q) {
-          const size_t i = off + t + q * G::T;
-          const float2 u = x(t + q * G::T), g = ld2(gj, i), b = b_pair(d, j, i);
-          if (write_u) st2(uj, i, u);
-          const float u0x = u.x + b.x, u0y = u.y + b.y;
-          acc[0].add(kl_term(g.x, u0x));
-          acc[0].add(kl_term(g.y, u0y));
-          x(t + q * G::T) = make_float2(ratio_term(g.x, u0x), ratio_term(g.y, u0y));
-        }
-      }
-      row_real_to_spec<W>(x, sp, t, act);
+    for (int q = 0; q < G::E; ++q) {
+      const size_t i = off + t + q * G::T;
+      const float2 u = x(t + q * G::T), g = ld2(gj, i), b = b_pair(d, j, i);
+      if (write_u) st2(uj, i, u);
+      const float u0x = u.x + b.x, u0y = u.y + b.y;
+      acc[0].add(kl_term(g.x, u0x));
+      acc[0].add(kl_term(g.y, u0y));
+      x(t + q * G::T) = make_float2(ratio_term(g.x, u0x), ratio_term(g.y, u0y));
     }
-    block_sum_store<1, FP64>(acc, part_of(d, it) + SLOT_KL);
   }
+  row_real_to_spec<W>(x, sp, t, act);
+  block_sum_store<1, FP64>(acc, partv_of(d, it) + SLOT_KL);
 }
 
 // Set-up: y = w f v from plane 0 (one RL step from f^(0), Sect. 3.2); min over positive y and max y.
@@ -650,10 +667,12 @@ __global__ void __launch_bounds__(kRowBlock) k_rl_step_minmax(const ImgDesc* __r
   extern __shared__ float2 smem[];
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
   const RowLayout<G::M> x{smem + r * G::PITCH};
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+  {
+    const int it = blockIdx.x;
+    if (it >= n_items) return;
     const int2 item = items[it];
     const ImgDesc& d = imgs[item.x];
-    const int row = item.y + r;
+    const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
     row_spec_to_real<W>(x, spec_plane(d, 0) + off, t, act);
