@@ -38,7 +38,7 @@ __device__ __forceinline__ void col_load(const ColLayout<C>& x, const float2* __
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const int i = t + q * T;
-      x(i) = src[size_t(i) * M];
+      x(i) = src[i * M];
     }
   }
 }
@@ -47,7 +47,7 @@ __device__ __forceinline__ void col_load(const ColLayout<C>& x, const float2* __
 template <int H, int C, bool CONJ>
 __device__ __forceinline__ float2 col_product(const ColLayout<C>& x, int i, int col, float2 X,
                                               const float2* __restrict__ kh, const float2* __restrict__ kq, int M) {
-  float2 K = __ldg(&kh[size_t(i) * M + col]);
+  float2 K = __ldg(&kh[i * M + col]);
   if (CONJ) K = cconj(K);
   if (col != 0) return cmul(X, K);
   float2 Q = __ldg(&kq[i]);
@@ -56,7 +56,10 @@ __device__ __forceinline__ float2 col_product(const ColLayout<C>& x, int i, int 
   return cadd(cmul(X, K), cmul(cconj(Xm), Q));
 }
 
-template <int H, int MODE>
+// MODE as above; NV = number of views summed by COL_PTO1 (0: any number, runtime loop).
+// One block per item (job, col0 | view << 16): runtime loops around the transforms make the
+// register allocator keep every stage's addresses live, so views are separate items where possible.
+template <int H, int MODE, int NV = 0>
 __global__ void __launch_bounds__(kColBlock) k_col(const ColJob* __restrict__ jobs, const int2* __restrict__ items,
                                                   int n_items) {
   using G = ColGeo<H>;
@@ -64,12 +67,14 @@ __global__ void __launch_bounds__(kColBlock) k_col(const ColJob* __restrict__ jo
   extern __shared__ float2 smem[];
   const int c = threadIdx.x % C, t = threadIdx.x / C;
   const ColLayout<C> x{smem + c};
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+  {
+    const int it = blockIdx.x;
+    if (it >= n_items) return;
     const int2 item = items[it];
     const ColJob& jb = jobs[item.x];
-    if (jb.ctrl && jb.ctrl->done >= 1) continue;
+    if (jb.ctrl && jb.ctrl->done >= 1) return;
     const int M = jb.M;
-    const int col = item.y + c;
+    const int col = (item.y & 0xffff) + c;
     const bool act = col < M;
     if (MODE == COL_KHAT) {
       col_load<H, C>(x, jb.in + col, M, t, act);
@@ -105,14 +110,15 @@ __global__ void __launch_bounds__(kColBlock) k_col(const ColJob* __restrict__ jo
 #pragma unroll
         for (int q = 0; q < E; ++q) {
           const int i = t + q * T;
-          jb.out[size_t(i) * M + col] = outv[q];
+          jb.out[i * M + col] = outv[q];
           if (col == 0) jb.khatq[i] = qv[q];
         }
       }
       __syncthreads();
     } else if (MODE == COL_1TOP || MODE == COL_1TOP_CONJ) {
       constexpr bool CJ = MODE == COL_1TOP_CONJ;
-      for (int j = 0; j < jb.nout; ++j) {
+      {
+        const int j = item.y >> 16;
         col_load<H, C>(x, jb.in + col, M, t, act);
         __syncthreads();
         fft_inplace<H, false>(x, t, act);
@@ -138,7 +144,7 @@ __global__ void __launch_bounds__(kColBlock) k_col(const ColJob* __restrict__ jo
 #pragma unroll
           for (int q = 0; q < E; ++q) {
             const int i = t + q * T;
-            dst[size_t(i) * M] = x(i);
+            dst[i * M] = x(i);
           }
         }
         __syncthreads();
@@ -147,7 +153,9 @@ __global__ void __launch_bounds__(kColBlock) k_col(const ColJob* __restrict__ jo
       float2 acc[E];
 #pragma unroll
       for (int q = 0; q < E; ++q) acc[q] = make_float2(0.0f, 0.0f);
-      for (int j = 0; j < jb.nin; ++j) {
+      const int nin = NV > 0 ? NV : jb.nin;
+#pragma unroll
+      for (int j = 0; j < nin; ++j) {
         col_load<H, C>(x, jb.in + size_t(j) * jb.plane_stride + col, M, t, act);
         __syncthreads();
         fft_inplace<H, false>(x, t, act);
@@ -173,7 +181,7 @@ __global__ void __launch_bounds__(kColBlock) k_col(const ColJob* __restrict__ jo
 #pragma unroll
         for (int q = 0; q < E; ++q) {
           const int i = t + q * T;
-          dst[size_t(i) * M] = x(i);
+          dst[i * M] = x(i);
         }
       }
       __syncthreads();
