@@ -1,0 +1,384 @@
+// Device-side controllers (one block per problem): they turn the partial sums of the row passes
+// into the scalar decisions of the methods, so an iteration never waits on the host.
+//   k_ctrl_alpha   step 1 of Alg. 1: scaled BB values (Eq. BB1, BB2), the safeguards, the
+//                  alternation of Eq. (alphadef) with the M_alpha window and tau, warm-up rule
+//   k_ctrl_lambda  step 5 of Alg. 1: first lambda in {1, theta, theta^2, theta^3} with
+//                  J(f + lambda d) <= J(f) + beta lambda grad'd; stop rules of Sect. 3.3
+//   k_ctrl_lambda_extra  lambda = theta^4 .. theta^30 when needed
+//   k_ctrl_rl      Richardson-Lucy bookkeeping (J, trace, stop rules)
+//   k_ctrl_setup   J_0 and the adaptive bounds L1, L2 of Sect. 3.2
+#pragma once
+#include <math.h>
+#include "rowops.cuh"
+#include "state.cuh"
+
+namespace sgp {
+
+// Sum NS slots over this problem's items (row list or row-view list); result on every thread.
+template <int NS, bool FP64>
+__device__ void ctrl_sum(const ImgDesc& d, int slot, double (&res)[NS], bool view_list) {
+  using V = typename Acc<FP64>::T;
+  __shared__ V red[NS][kCtrlBlock / 32];
+  V loc[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) loc[s] = V(0);
+  const int n = view_list ? d.n_rv_items : d.n_row_items;
+  const double* base = view_list ? d.partv : d.part;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double* p = base + size_t(i) * kPartStride + slot;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) loc[s] += V(p[s]);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const V v = warp_sum<V>(loc[s]);
+    if (lane == 0) red[s][wid] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    V v = V(0);
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) v += red[s][w];   // fixed order: deterministic
+    res[s] = double(v);
+  }
+  __syncthreads();
+}
+
+__device__ inline void ctrl_minmax(const ImgDesc& d, double& mn, double& mx) {
+  __shared__ double rmn[kCtrlBlock / 32], rmx[kCtrlBlock / 32];
+  double a = INFINITY, b = 0.0;
+  for (int i = threadIdx.x; i < d.n_row_items; i += blockDim.x) {
+    const double* p = d.part + size_t(i) * kPartStride;
+    a = fmin(a, p[SLOT_MIN]);
+    b = fmax(b, p[SLOT_MAX]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { rmn[wid] = a; rmx[wid] = b; }
+  __syncthreads();
+  mn = INFINITY; mx = 0.0;
+  for (int w = 0; w < int(blockDim.x >> 5); ++w) { mn = fmin(mn, rmn[w]); mx = fmax(mx, rmx[w]); }
+  __syncthreads();
+}
+
+__device__ inline void trace_push(const ImgDesc& d, CtrlState* c, double k, double J, double alpha,
+                                  double lam, int bt, int branch, double gTd) {
+  if (c->trace_n < c->trace_cap) {
+    double* r = d.trace + size_t(c->trace_n) * kTraceStride;
+    r[0] = k; r[1] = J; r[2] = 2.0 * J * c->inv_pS; r[3] = alpha; r[4] = lam;
+    r[5] = bt; r[6] = branch; r[7] = gTd;
+  }
+  c->trace_n += 1;
+}
+
+// Step 1 of Alg. 1 for k >= 1 (V = double, or float for the plain-FP32 variant).
+template <class V>
+__device__ inline double bb_alpha(CtrlState* c, V n1, V d1, V n2, V d2, int k) {
+  const V amin = V(c->alpha_min), amax = V(c->alpha_max), aprev = V(c->alpha);
+  V a1, a2;
+  if (d1 <= V(0)) a1 = fmin(V(10) * aprev, amax);
+  else a1 = fmin(amax, fmax(amin, n1 / d1));
+  if (n2 <= V(0)) a2 = fmin(V(10) * aprev, amax);
+  else a2 = fmin(amax, fmax(amin, n2 / d2));
+  // window of the last M_alpha values of alpha^(2), Eq. (alphadef)
+  if (c->hist_n < c->M_alpha) c->hist[c->hist_n++] = double(a2);
+  else {
+    for (int i = 1; i < c->M_alpha; ++i) c->hist[i - 1] = c->hist[i];
+    c->hist[c->M_alpha - 1] = double(a2);
+  }
+  V wmin = V(c->hist[0]);
+  for (int i = 1; i < c->hist_n; ++i) wmin = fmin(wmin, V(c->hist[i]));
+  V alpha;
+  if (k <= c->warmup) { alpha = wmin; c->branch = 2; }
+  else if (a2 / a1 <= V(c->tau)) { alpha = wmin; c->tau *= 0.9; c->branch = 2; }
+  else { alpha = a1; c->tau *= 1.1; c->branch = 1; }
+  return double(alpha);
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(kCtrlBlock) k_ctrl_alpha(const ImgDesc* __restrict__ imgs) {
+  const ImgDesc& d = imgs[blockIdx.x];
+  CtrlState* c = d.ctrl;
+  if (c->done >= 2) return;
+  double kl[2], bb[4];
+  ctrl_sum<2, FP64>(d, SLOT_KL, kl, true);
+  ctrl_sum<4, FP64>(d, SLOT_BB, bb, false);
+  if (threadIdx.x != 0) return;
+  if (!c->fresh) { c->k += 1; c->fresh = 1; }
+  if (c->done == 1) { c->done = 2; c->J = c->J_pred; return; }
+  if (!isfinite(kl[0])) { c->status = 8; c->done = 2; return; }
+  c->J = kl[0];
+  if (c->stop_kind == STOP_MIN_ERROR && c->ftrue_norm2 > 0.0) {
+    const double rho = sqrt(kl[1] / c->ftrue_norm2);
+    c->rho = rho;
+    if (c->k >= 1 && rho > c->rho_prev) { c->done = 2; c->result_prev = 1; return; }
+    c->rho_prev = rho;
+  }
+  double alpha;
+  if (c->k == 0) {
+    alpha = c->alpha0;
+    c->branch = 0;
+  } else if (FP64) {
+    alpha = bb_alpha<double>(c, bb[0], bb[1], bb[2], bb[3], c->k);
+  } else {
+    alpha = bb_alpha<float>(c, float(bb[0]), float(bb[1]), float(bb[2]), float(bb[3]), c->k);
+  }
+  c->alpha = alpha;
+}
+
+__device__ inline void sgp_accept(const ImgDesc& d, CtrlState* c, int nb, double lam, double dJ) {
+  c->lambda = lam;
+  c->backtracks = nb;
+  c->dJ = dJ;
+  c->J_pred = c->J + dJ;
+  c->fresh = 0;                       // f^(k+1) = f^(k) + lambda d is applied by the next K1
+  c->need_more = 0;
+  const int kn = c->k + 1;
+  trace_push(d, c, kn, c->J_pred, c->alpha, lam, nb, c->branch, c->gTd);
+  bool stop = kn >= c->max_iter;
+  if (c->stop_kind == STOP_CONVERGENCE && fabs(c->J_pred - c->J) <= c->tol * c->J) stop = true;
+  if (c->stop_kind == STOP_DISCREPANCY && 2.0 * c->J_pred * c->inv_pS <= c->eta) stop = true;
+  if (stop) c->done = 1;
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(kCtrlBlock) k_ctrl_lambda(const ImgDesc* __restrict__ imgs) {
+  const ImgDesc& d = imgs[blockIdx.x];
+  CtrlState* c = d.ctrl;
+  if (c->done >= 1) return;
+  double s[1], arm[4];
+  ctrl_sum<1, FP64>(d, SLOT_GTD, s, false);
+  ctrl_sum<4, FP64>(d, SLOT_ARM, arm, true);
+  if (threadIdx.x != 0) return;
+  const double gTd = s[0];
+  c->gTd = gTd;
+  if (!isfinite(gTd)) { c->status = 8; c->done = 2; return; }
+  double lam = 1.0;
+  for (int i = 0; i < 4 && i <= c->max_backtracks; ++i) {
+    const bool ok = FP64 ? (arm[i] <= c->beta * lam * gTd)
+                         : (float(arm[i]) <= float(c->beta) * float(lam) * float(gTd));
+    if (ok) { sgp_accept(d, c, i, lam, arm[i]); return; }
+    lam *= c->theta;
+  }
+  c->need_more = 1;
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(kCtrlBlock) k_ctrl_lambda_extra(const ImgDesc* __restrict__ imgs) {
+  const ImgDesc& d = imgs[blockIdx.x];
+  CtrlState* c = d.ctrl;
+  if (c->done >= 1 || !c->need_more) return;
+  double arm[kArmExtra];
+  ctrl_sum<kArmExtra, FP64>(d, SLOT_ARMX, arm, false);
+  if (threadIdx.x != 0) return;
+  double lam = c->theta * c->theta * c->theta * c->theta;
+  const double gTd = c->gTd;
+  for (int i = 0; i < kArmExtra && 4 + i <= c->max_backtracks; ++i) {
+    const bool ok = FP64 ? (arm[i] <= c->beta * lam * gTd)
+                         : (float(arm[i]) <= float(c->beta) * float(lam) * float(gTd));
+    if (ok) { sgp_accept(d, c, 4 + i, lam, arm[i]); return; }
+    lam *= c->theta;
+  }
+  c->need_more = 0;
+  c->status = 6;                      // line search failed: stop at f^(k)
+  c->done = 2;
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(kCtrlBlock) k_ctrl_rl(const ImgDesc* __restrict__ imgs) {
+  const ImgDesc& d = imgs[blockIdx.x];
+  CtrlState* c = d.ctrl;
+  if (c->done >= 2) return;
+  double kl[1], rr[1];
+  ctrl_sum<1, FP64>(d, SLOT_KL, kl, true);
+  ctrl_sum<1, FP64>(d, SLOT_RHO, rr, false);
+  if (threadIdx.x != 0) return;
+  const bool updated = c->have_v;
+  if (updated) c->k += 1;
+  c->have_v = 1;
+  if (!isfinite(kl[0])) { c->status = 8; c->done = 2; return; }
+  c->J_prev = c->J;
+  c->J = kl[0];
+  if (updated) trace_push(d, c, c->k, c->J, 0.0, 1.0, 0, 0, 0.0);
+  if (c->stop_kind == STOP_MIN_ERROR && c->ftrue_norm2 > 0.0) {
+    const double rho = sqrt(rr[0] / c->ftrue_norm2);
+    c->rho = rho;
+    if (c->k >= 1 && rho > c->rho_prev) { c->done = 2; c->result_prev = 1; return; }
+    c->rho_prev = rho;
+  }
+  bool stop = c->k >= c->max_iter;
+  if (updated && c->stop_kind == STOP_CONVERGENCE && fabs(c->J - c->J_prev) <= c->tol * c->J_prev) stop = true;
+  if (c->stop_kind == STOP_DISCREPANCY && 2.0 * c->J * c->inv_pS <= c->eta) stop = true;
+  if (stop) c->done = 2;
+}
+
+// After the set-up passes: J_0 (from the ratio pass) and L1/L2 (Sect. 3.2) from one RL step.
+template <bool FP64>
+__global__ void __launch_bounds__(kCtrlBlock) k_ctrl_setup(const ImgDesc* __restrict__ imgs, int adaptive,
+                                                          int want_bounds) {
+  const ImgDesc& d = imgs[blockIdx.x];
+  CtrlState* c = d.ctrl;
+  double s[1];
+  ctrl_sum<1, FP64>(d, SLOT_KL, s, true);
+  double mn = 0.0, mx = 0.0;
+  if (want_bounds) ctrl_minmax(d, mn, mx);
+  if (threadIdx.x != 0) return;
+  c->J = s[0];
+  c->J_prev = s[0];
+  if (!isfinite(s[0])) { c->status = 8; c->done = 2; return; }
+  if (want_bounds && adaptive) {
+    if (!(mn < INFINITY) || mx <= 0.0) { c->status = 1; c->done = 2; return; }
+    if (mx / mn < 50.0) { c->L1 = mn / 10.0; c->L2 = mx * 10.0; }
+    else { c->L1 = mn; c->L2 = mx; }
+  }
+}
+
+// (Re)arm the stop rule of every problem: kind, max_iter (relative to the current k or absolute).
+__global__ void k_ctrl_arm(const ImgDesc* __restrict__ imgs, int n, int kind, int n_iter, double tol,
+                           double eta, int relative) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  CtrlState* c = imgs[i].ctrl;
+  if (c->status != 0) return;          // a failed problem stays stopped
+  c->stop_kind = kind;
+  c->max_iter = relative ? c->k + n_iter : n_iter;
+  c->tol = tol;
+  c->eta = eta;
+  c->done = 0;
+  c->result_prev = 0;
+  c->need_more = 0;
+}
+
+// ------------------------------------------------------------------------------ set-up kernels
+// g_int = g on S, -1 outside S (boundary); counts non-finite or negative samples.
+__global__ void k_prepare_data(const float* __restrict__ g, const uint8_t* __restrict__ mask,
+                               float* __restrict__ out, size_t P, int p, int* __restrict__ bad) {
+  const size_t n = P * size_t(p);
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    float v = g[i];
+    if (!isfinite(v) || v < 0.0f) { atomicAdd(bad, 1); v = 0.0f; }
+    if (mask && !mask[i % P]) v = -1.0f;
+    out[i] = v;
+  }
+}
+
+// per plane: sum, max, min, count of non-finite samples (one block per plane)
+__global__ void __launch_bounds__(256) k_plane_stats(const float* __restrict__ x, size_t P, double* __restrict__ out) {
+  const float* a = x + size_t(blockIdx.x) * P;
+  double s = 0.0;
+  float mx = -INFINITY, mn = INFINITY;
+  int nf = 0;
+  for (size_t i = threadIdx.x; i < P; i += blockDim.x) {
+    const float v = a[i];
+    if (!isfinite(v)) { ++nf; continue; }
+    s += v; mx = fmaxf(mx, v); mn = fminf(mn, v);
+  }
+  __shared__ double rs[256];
+  __shared__ float rmx[256], rmn[256];
+  __shared__ int rnf[256];
+  rs[threadIdx.x] = s; rmx[threadIdx.x] = mx; rmn[threadIdx.x] = mn; rnf[threadIdx.x] = nf;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      rs[threadIdx.x] += rs[threadIdx.x + o];
+      rmx[threadIdx.x] = fmaxf(rmx[threadIdx.x], rmx[threadIdx.x + o]);
+      rmn[threadIdx.x] = fminf(rmn[threadIdx.x], rmn[threadIdx.x + o]);
+      rnf[threadIdx.x] += rnf[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[4 * blockIdx.x + 0] = rs[0];
+    out[4 * blockIdx.x + 1] = rmx[0];
+    out[4 * blockIdx.x + 2] = rmn[0];
+    out[4 * blockIdx.x + 3] = rnf[0];
+  }
+}
+
+// sums over S of g_j (g >= 0 marks S) and of b_j, and |S|: out[3*j + {0,1,2}] (one block per view)
+__global__ void __launch_bounds__(256) k_data_sums(const float* __restrict__ g, const float* __restrict__ b,
+                                                  const float* __restrict__ bconst, size_t P, double* __restrict__ out) {
+  const int j = blockIdx.x;
+  const float* gj = g + size_t(j) * P;
+  const float* bj = b ? b + size_t(j) * P : nullptr;
+  double sg = 0.0, sb = 0.0, ns = 0.0;
+  for (size_t i = threadIdx.x; i < P; i += blockDim.x) {
+    const float v = gj[i];
+    if (v < 0.0f) continue;
+    sg += v; sb += bj ? bj[i] : bconst[j]; ns += 1.0;
+  }
+  __shared__ double r[3][256];
+  r[0][threadIdx.x] = sg; r[1][threadIdx.x] = sb; r[2][threadIdx.x] = ns;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int q = 0; q < 3; ++q) r[q][threadIdx.x] += r[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) out[3 * j + q] = r[q][0];
+}
+
+// f = value on R (w > 0), 0 elsewhere; or f = max(src, 0) restricted to R when src != nullptr
+__global__ void k_fill_start(float* __restrict__ f, const float* __restrict__ w, const float* __restrict__ src,
+                             float value, size_t P) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < P; i += size_t(gridDim.x) * blockDim.x) {
+    const bool inR = !w || w[i] > 0.0f;
+    float v = src ? fmaxf(src[i], 0.0f) : value;
+    if (!isfinite(v)) v = 0.0f;
+    f[i] = inR ? v : 0.0f;
+  }
+}
+
+// boundary set-up: R = {alpha_j >= sigma for every j}, w = M_R / sum_j alpha_j (Eq. Rdef, boundaryRL)
+__global__ void k_make_w(const float* __restrict__ alpha, int p, size_t P, float sigma, float* __restrict__ w) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < P; i += size_t(gridDim.x) * blockDim.x) {
+    float s = 0.0f;
+    bool inR = true;
+    for (int j = 0; j < p; ++j) {
+      const float a = alpha[size_t(j) * P + i];
+      inR = inR && (a >= sigma);
+      s += a;
+    }
+    w[i] = (inR && s > 0.0f) ? 1.0f / s : 0.0f;
+  }
+}
+
+__global__ void k_u8_to_float(const uint8_t* __restrict__ m, float* __restrict__ out, size_t P) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < P; i += size_t(gridDim.x) * blockDim.x)
+    out[i] = m[i] ? 1.0f : 0.0f;
+}
+
+// x *= mask for nplanes planes: mask = (w > 0) [M_R] when w is given, (g >= 0) [M_S] when g is given
+__global__ void k_apply_mask(float* __restrict__ x, size_t P, int nplanes, const float* __restrict__ w,
+                             const float* __restrict__ g) {
+  const size_t n = P * size_t(nplanes);
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    const size_t q = i % P;
+    bool keep = true;
+    if (w) keep = w[q] > 0.0f;
+    if (g) keep = g[i] >= 0.0f;
+    if (!keep) x[i] = 0.0f;
+  }
+}
+
+// sum of squares of x (one block): out[0]
+__global__ void __launch_bounds__(256) k_sumsq(const float* __restrict__ x, size_t P, double* __restrict__ out) {
+  double s = 0.0;
+  for (size_t i = threadIdx.x; i < P; i += blockDim.x) s += double(x[i]) * x[i];
+  __shared__ double r[256];
+  r[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) r[threadIdx.x] += r[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = r[0];
+}
+
+}  // namespace sgp
