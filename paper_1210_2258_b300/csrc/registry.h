@@ -1,0 +1,36 @@
+// Kernel registry: function pointers and launch geometry of the size-templated passes.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace sgp {
+
+constexpr int kNumSides = 15;
+constexpr int kSides[kNumSides] = {16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048};
+inline int side_index(int n) {
+  for (int i = 0; i < kNumSides; ++i)
+    if (kSides[i] == n) return i;
+  return -1;
+}
+
+enum RowOp {
+  ROP_SGP_UPDATE = 0, ROP_SGP_GRAD, ROP_SGP_Y, ROP_SGP_AD, ROP_SGP_ARMX, ROP_RL_UPDATE, ROP_RL_RATIO,
+  ROP_MINMAX, ROP_R2C, ROP_C2R, ROP_COUNT
+};
+// column variants: COL_KHAT, COL_1TOP, COL_1TOP_CONJ, COL_PTO1 (any p), COL_PTO1 for p = 1, p = 3
+constexpr int kColModes = 6;
+constexpr int kColPto1P1 = 4, kColPto1P3 = 5;
+
+struct Registry {
+  const void* row[ROP_COUNT][2][kNumSides];   // [op][fp64][side]
+  const void* col[kColModes][kNumSides];      // [variant][side]
+  size_t row_smem[kNumSides], col_smem[kNumSides];
+  int row_rows[kNumSides], col_cols[kNumSides];
+  cudaError_t (*twiddle_init[3])(const float2*);
+};
+
+void register_small(Registry&);
+void register_mid(Registry&);
+void register_large(Registry&);
+
+}  // namespace sgp
