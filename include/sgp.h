@@ -1,0 +1,197 @@
+/*
+ * sgp.h -- C ABI of the B300 (sm_103a) Richardson-Lucy / scaled gradient projection (SGP)
+ * deconvolution library.
+ *
+ * The methods are those of Prato, Cavicchioli, Zanni, Boccacci & Bertero, "Efficient
+ * deconvolution methods for astronomical imaging: algorithms and IDL-GPU codes":
+ *   - the imaging model A_j f = K_j * f with unit-volume PSFs K_j (Sect. 1, Sect. 2.3) and, with a
+ *     boundary mask, A_j f = M_S (K_j * (M_R f)), A_j^T y = M_R (K_j (x) (M_S y)) on an extended
+ *     domain (Sect. 2.4, Eq. projection / backprojection);
+ *   - the KL divergence J_0 (Sect. 1, Eq. KL; Sect. 2.3, Eq. multipleKL) and its gradient
+ *     (Eq. KLgrad, multiplegradient, gradientboundary);
+ *   - Richardson-Lucy in single, multiple and boundary form (Eq. RL, multipleRL, boundaryRL);
+ *   - SGP, Algorithm 1, with the scaled Barzilai-Borwein step lengths (Eq. BB1, BB2), their
+ *     safeguards and alternation (Eq. alphadef), the RL scaling (Eq. Dk, Dkbound), the Armijo line
+ *     search, the parameter values and adaptive bounds of Sect. 3.2;
+ *   - the starting points of Sect. 3.1 and the stopping rules of Sect. 3.3 (fixed number,
+ *     Eq. convergence, minimum reconstruction error, Eq. discrepancy).
+ *
+ * Conventions
+ *   - Every pointer documented as "device" is a CUDA device pointer owned by the caller.  The
+ *     library copies the inputs it needs (PSFs, data, backgrounds, masks) into the caller's
+ *     workspace during the call and keeps no caller pointer afterwards, except the reference object
+ *     given to sgp_set_truth, which must stay valid while solves use it.
+ *   - Arrays are float32, C-contiguous: a p-view array is p x H x W, an image is H x W.
+ *   - Supported sides: H, W in {16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536,
+ *     2048} (powers of two and three times powers of two); 1 <= p <= 8 views.
+ *   - The workspace (device memory of sgp_workspace_bytes bytes, 256-byte aligned) is owned by
+ *     the caller and must outlive the context; the library never allocates device memory.
+ *   - `stream` is a cudaStream_t (passed as void*; NULL = legacy default stream).  Calls are
+ *     ordered with that stream.  sgp_create, sgp_set_data, sgp_set_start, kl_value, sgp_get_*,
+ *     sgp_solve_until and rl_solve_until synchronise; rl_iterate, sgp_iterate, sgp_apply_A and
+ *     sgp_apply_AT are asynchronous.
+ *   - Every call returns an sgp_status; sgp_last_error() gives a message for the calling thread.
+ *   - A context is not thread safe; use one context per host thread.
+ */
+#ifndef SGP_B300_H
+#define SGP_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgp_ctx sgp_ctx;
+
+typedef enum {
+  SGP_OK = 0,
+  SGP_ERR_ARG = 1,              /* invalid argument, missing data, no positive pixel for L1/L2 */
+  SGP_ERR_SIZE_UNSUPPORTED = 2, /* H, W or p outside the supported set */
+  SGP_ERR_PSF = 3,              /* PSF not finite, sum <= 0, or significantly negative */
+  SGP_ERR_CUDA = 4,             /* a CUDA runtime call failed */
+  SGP_ERR_WORKSPACE = 5,        /* workspace too small or misaligned */
+  SGP_ERR_LINESEARCH = 6,       /* Armijo loop exceeded max_backtracks reductions */
+  SGP_ERR_TIMEOUT = 7,          /* iteration cap reached before the stop rule */
+  SGP_ERR_NONFINITE = 8,        /* non-finite data, objective or gradient */
+  SGP_ERR_STATE = 9             /* call not valid in the current state */
+} sgp_status;
+
+enum { SGP_STOP_FIXED = 0, SGP_STOP_CONVERGENCE = 1, SGP_STOP_DISCREPANCY = 2, SGP_STOP_MIN_ERROR = 3 };
+enum { SGP_START_ZERO = 0, SGP_START_DATA = 1, SGP_START_CONSTANT = 2, SGP_START_USER = 3 };
+enum { SGP_PSF_CENTER = 0, SGP_PSF_CORNER = 1 };
+
+/* One problem: p detected images of an H x W object (Sect. 2.3); has_mask selects boundary-effect
+ * correction on the extended domain H x W (Sect. 2.4); psf_origin: SGP_PSF_CENTER = PSF origin at
+ * pixel (H/2, W/2), SGP_PSF_CORNER = at (0, 0). */
+typedef struct {
+  int H, W, p;
+  int has_mask;
+  int psf_origin;
+} sgp_shape;
+
+/* Method parameters; sgp_params_default() gives the values of Sect. 3.2. */
+typedef struct {
+  double beta;          /* Armijo parameter (1e-4) */
+  double theta;         /* backtracking factor (0.4) */
+  double alpha0;        /* first step length (1.3) */
+  double tau1;          /* alternation threshold tau_1 (0.5) */
+  double alpha_min;     /* 1e-5 */
+  double alpha_max;     /* 1e5 */
+  int M_alpha;          /* BB2 window (3), <= 16 */
+  int warmup_iters;     /* iterations using the windowed BB2 before alternating (20) */
+  int adaptive_L;       /* 1: L1/L2 from one RL step (Sect. 3.2); 0: use L1, L2 below */
+  int max_backtracks;   /* cap on Armijo reductions (30, <= 30) */
+  double L1, L2;        /* fixed scaling bounds when adaptive_L == 0 (1e-10, 1e10) */
+  double sigma_R;       /* threshold of Eq. (Rdef) for the reconstruction domain R (1e-2) */
+  int constraint;       /* 0: f >= 0; 1: f >= 0 and sum f = flux_c (projection in the D^-1 metric) */
+  double flux_c;        /* flux for constraint 1; <= 0 means mean over views of sum_S (g - b) */
+  int reduce_fp64;      /* 1: FP64 accumulation of KL / BB / Armijo sums (default); 0: plain FP32 */
+  int trace_cap;        /* per-problem iteration records kept on the device (4096) */
+} sgp_params;
+
+typedef struct {
+  int kind;              /* SGP_STOP_* */
+  int max_iter;          /* cap on the number of further iterations */
+  double tol;            /* convergence: |J_{k+1} - J_k| <= tol J_k */
+  double eta;            /* discrepancy: stop at the first k with 2 J_0 / (p |S|) <= eta */
+} sgp_stop_rule;
+
+typedef struct {
+  const float* psfs;     /* device, p x H x W, PSF samples (normalised by the library) */
+  const float* b;        /* device, p x H x W backgrounds, or NULL to use b_const */
+  float b_const[8];      /* constant background per view */
+  const uint8_t* mask;   /* device, H x W, M_S (nonzero on detected pixels); required iff has_mask */
+} sgp_inputs;
+
+typedef struct {
+  int k;                 /* iterations performed (index of the current iterate) */
+  int status;            /* device-side sgp_status of this problem */
+  int stopped;           /* 1 when the last stop rule fired */
+  int trace_n;           /* number of trace records written */
+  double J;              /* J_0 at the current iterate */
+  double D;              /* discrepancy 2 J_0 / (p |S|) */
+  double L1, L2;         /* scaling bounds in use */
+  double alpha, tau, lambda, rho;
+  double nS;             /* |S| (pixels of the detected image) */
+  double flux_c;         /* constant start value c of Sect. 3.1 */
+} sgp_info;
+
+/* Fill *out with the parameter values of Sect. 3.2. */
+void sgp_params_default(sgp_params* out);
+
+/* Workspace bytes needed for n problems of the given shapes (params may be NULL = defaults). */
+size_t sgp_workspace_bytes(int n, const sgp_shape* shapes, const sgp_params* params);
+
+/* Create a context for n problems that advance together (n = 1 for a single problem).
+ * For each problem: validate the shape, normalise each PSF to unit volume over the (extended)
+ * domain (Sect. 2.4), move its origin to (0, 0), store its spectrum, copy the backgrounds, and for
+ * boundary problems compute alpha_j = K_j (x) M_S, R = {alpha_j >= sigma_R}, M_R / alpha
+ * (Eq. Rdef; reading: alpha_j without the garbled factor g).
+ * Errors: SGP_ERR_ARG, SGP_ERR_SIZE_UNSUPPORTED, SGP_ERR_PSF, SGP_ERR_WORKSPACE, SGP_ERR_CUDA. */
+sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const sgp_inputs* inputs,
+                            const sgp_params* params, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Single-problem form of sgp_create_batch. b: device p x H x W or NULL; b_const: host array of p
+ * constant backgrounds (used when b is NULL); mask: device H x W or NULL. */
+sgp_status sgp_create(sgp_ctx** out, const sgp_shape* shape, const float* psfs, const float* b,
+                      const float* b_const, const uint8_t* mask, const sgp_params* params,
+                      void* workspace, size_t workspace_bytes, void* stream);
+
+/* Detected images g (device, p x H x W, counts >= 0) of problem `image`; pixels outside S are
+ * ignored.  Sets the constant starting point of Sect. 3.1 unless sgp_set_start is called later.
+ * Errors: SGP_ERR_NONFINITE for negative or non-finite data, SGP_ERR_ARG. */
+sgp_status sgp_set_data(sgp_ctx* ctx, int image, const float* g);
+
+/* Starting point (Sect. 3.1): SGP_START_ZERO, SGP_START_DATA (g_1), SGP_START_CONSTANT
+ * (mean over views of sum_S (g - b) / |S|, on R), SGP_START_USER (device H x W f0, clipped at 0
+ * and restricted to R).  Resets the iteration count. */
+sgp_status sgp_set_start(sgp_ctx* ctx, int image, int mode, const float* f0);
+
+/* Reference object for the minimum-reconstruction-error stop (Sect. 3.3); device H x W, must stay
+ * valid while solves run; NULL clears it. */
+sgp_status sgp_set_truth(sgp_ctx* ctx, int image, const float* f_true);
+
+/* n Richardson-Lucy iterations of every problem (Eq. RL, multipleRL, boundaryRL).  Asynchronous. */
+sgp_status rl_iterate(sgp_ctx* ctx, int n);
+
+/* n SGP iterations (Algorithm 1) of every problem.  Asynchronous. */
+sgp_status sgp_iterate(sgp_ctx* ctx, int n);
+
+/* Iterate SGP (resp. RL) on every problem until its stop rule fires or max_iter further
+ * iterations; iters (n ints, may be NULL) receives each problem's iteration count.
+ * Returns SGP_ERR_TIMEOUT if some problem reached max_iter before a non-FIXED rule fired, or the
+ * first device-side error status. */
+sgp_status sgp_solve_until(sgp_ctx* ctx, const sgp_stop_rule* rule, int* iters);
+sgp_status rl_solve_until(sgp_ctx* ctx, const sgp_stop_rule* rule, int* iters);
+
+/* J_0 (FP64) at the current iterate of problem `image` (Eq. KL / multipleKL). */
+sgp_status kl_value(sgp_ctx* ctx, int image, double* out);
+
+/* Copy the current iterate (the returned one after a minimum-error stop) to dst (device H x W). */
+sgp_status sgp_get_f(sgp_ctx* ctx, int image, float* dst);
+
+/* Per-iteration records, 8 doubles each: k, J_0, discrepancy, alpha, lambda, backtracks,
+ * branch (0 alpha_0, 1 BB1, 2 windowed BB2), grad'd.  out: host, cap records. */
+sgp_status sgp_get_trace(sgp_ctx* ctx, int image, double* out, int cap, int* count);
+
+sgp_status sgp_get_info(sgp_ctx* ctx, int image, sgp_info* out);
+
+/* Operators of problem `image` (Eq. projection / backprojection): out_j = A_j f for every view
+ * (out: device p x H x W); out = sum_j A_j^T y_j (y: device p x H x W, out: device H x W).
+ * They use the problem's iteration buffers as scratch: the next iterate call re-initialises the
+ * iteration from the current iterate.  Asynchronous. */
+sgp_status sgp_apply_A(sgp_ctx* ctx, int image, const float* f, float* out);
+sgp_status sgp_apply_AT(sgp_ctx* ctx, int image, const float* y, float* out);
+
+/* Release the context (not the workspace). */
+sgp_status sgp_destroy(sgp_ctx* ctx);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* sgp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGP_B300_H */
