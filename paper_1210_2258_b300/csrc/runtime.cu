@@ -1,0 +1,1015 @@
+// Host runtime and C ABI: workspace layout, set-up passes, iteration sequencing (captured into
+// CUDA graphs), stop-rule polling and result access.  Declarations and contracts: include/sgp.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/sgp.h"
+#include "ctrl.cuh"
+#include "registry.h"
+#include "state.cuh"
+
+using namespace sgp;
+
+namespace {
+
+thread_local std::string g_err;
+
+sgp_status fail(sgp_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define CU(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(SGP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
+  } while (0)
+
+// ------------------------------------------------------------------------------ registry
+Registry g_reg;
+bool g_reg_ready = false;
+bool g_dev_ready[64] = {false};
+
+sgp_status ensure_device_ready(int dev) {
+  if (!g_reg_ready) {
+    memset(&g_reg, 0, sizeof(g_reg));
+    register_small(g_reg);
+    register_mid(g_reg);
+    register_large(g_reg);
+    g_reg_ready = true;
+  }
+  if (dev < 0 || dev >= 64) return fail(SGP_ERR_CUDA, "device index out of range");
+  if (g_dev_ready[dev]) return SGP_OK;
+  // twiddle tables exp(-2 pi i q / L) for every supported length, computed in double
+  static const int lens[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048};
+  std::vector<float2> tab(kTwiddleTotal);
+  for (int L : lens) {
+    const int off = tw_offset(L);
+    for (int q = 0; q < L; ++q) {
+      const double a = -2.0 * M_PI * double(q) / double(L);
+      tab[off + q] = make_float2(float(cos(a)), float(sin(a)));
+    }
+  }
+  for (int i = 0; i < 3; ++i) CU(g_reg.twiddle_init[i](tab.data()));
+  for (int s = 0; s < kNumSides; ++s) {
+    for (int op = 0; op < ROP_COUNT; ++op)
+      for (int f = 0; f < 2; ++f)
+        CU(cudaFuncSetAttribute(g_reg.row[op][f][s], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(g_reg.row_smem[s])));
+    for (int m = 0; m < kColModes; ++m)
+      CU(cudaFuncSetAttribute(g_reg.col[m][s], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(g_reg.col_smem[s])));
+  }
+  g_dev_ready[dev] = true;
+  return SGP_OK;
+}
+
+// ------------------------------------------------------------------------------ workspace carving
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+int rows_per_item(int W) { return g_reg.row_rows[side_index(W)]; }
+int cols_per_item(int H) { return g_reg.col_cols[side_index(H)]; }
+
+struct Layout {
+  std::vector<ImgDesc> d;              // per problem
+  std::vector<float*> khat, khatq;     // per problem (p planes each)
+  std::vector<float*> bcopy;           // per problem (nullptr when constant backgrounds)
+  std::vector<double*> scratch;        // per problem 64 doubles
+  std::vector<uint8_t*> mS;            // per problem M_S bytes (boundary problems)
+  CtrlState* ctrl = nullptr;
+  ImgDesc* d_imgs = nullptr;
+  int2* d_row = nullptr;               // row list
+  int2* d_rv = nullptr;                // row-view list
+  int2* d_colv = nullptr;              // column list with views (1 -> p passes)
+  int2* d_col = nullptr;               // column list (p -> 1 passes)
+  int2* d_colk = nullptr;              // column list of the PSF spectrum jobs
+  ColJob* d_jobs = nullptr;            // 5 jobs per problem: A, AT, CONJ, A_raw, AT_raw, then p KHAT jobs
+  int* d_flag = nullptr;
+  size_t bytes = 0;
+  int n_row = 0, n_rv = 0, n_colv = 0, n_col = 0, n_colk = 0, n_jobs = 0;
+};
+
+// Count items and carve every array (base == nullptr: only measure).
+void plan_layout(char* base, int n, const sgp_shape* sh, int trace_cap, const bool* has_b, Layout& L) {
+  Carver cv{base};
+  L.d.assign(n, ImgDesc{});
+  L.khat.assign(n, nullptr);
+  L.khatq.assign(n, nullptr);
+  L.bcopy.assign(n, nullptr);
+  L.scratch.assign(n, nullptr);
+  L.mS.assign(n, nullptr);
+  L.n_row = L.n_rv = L.n_colv = L.n_col = L.n_colk = 0;
+  for (int i = 0; i < n; ++i) {
+    const int H = sh[i].H, W = sh[i].W, p = sh[i].p;
+    const size_t P = size_t(H) * W;
+    ImgDesc& d = L.d[i];
+    d.H = H; d.W = W; d.p = p; d.boundary = sh[i].has_mask ? 1 : 0; d.P = P;
+    const int rpi = rows_per_item(W), cpi = cols_per_item(H), M = W / 2;
+    const int nr = (H + rpi - 1) / rpi, nc = (M + cpi - 1) / cpi;
+    d.row_item0 = 0; d.n_row_items = nr;      // indices within the problem's own range
+    d.rv_item0 = 0; d.n_rv_items = nr * p;
+    L.n_row += nr; L.n_rv += nr * p; L.n_col += nc; L.n_colv += nc * p; L.n_colk += nc * p;
+    d.f[0] = cv.take<float>(P); d.f[1] = cv.take<float>(P);
+    d.grad[0] = cv.take<float>(P); d.grad[1] = cv.take<float>(P);
+    d.u = cv.take<float>(P * p);
+    d.Ad = cv.take<float>(P * p);
+    d.g = cv.take<float>(P * p);
+    L.bcopy[i] = (has_b && has_b[i]) ? cv.take<float>(P * p) : nullptr;
+    d.b = L.bcopy[i];
+    d.w = d.boundary ? cv.take<float>(P) : nullptr;
+    d.spec = cv.take<float>(P * (p + 1));
+    L.khat[i] = cv.take<float>(P * p);
+    L.khatq[i] = cv.take<float>(size_t(2) * H * p);
+    d.part = cv.take<double>(size_t(nr) * kPartStride);
+    d.partv = cv.take<double>(size_t(nr) * p * kPartStride);
+    d.trace = cv.take<double>(size_t(trace_cap) * kTraceStride);
+    L.scratch[i] = cv.take<double>(64);
+    L.mS[i] = d.boundary ? cv.take<uint8_t>(P) : nullptr;
+  }
+  L.ctrl = cv.take<CtrlState>(n);
+  for (int i = 0; i < n; ++i) L.d[i].ctrl = L.ctrl ? L.ctrl + i : nullptr;
+  L.d_imgs = cv.take<ImgDesc>(n);
+  L.d_row = cv.take<int2>(L.n_row);
+  L.d_rv = cv.take<int2>(L.n_rv);
+  L.d_colv = cv.take<int2>(L.n_colv);
+  L.d_col = cv.take<int2>(L.n_col);
+  L.d_colk = cv.take<int2>(L.n_colk);
+  int nj = 0;
+  for (int i = 0; i < n; ++i) nj += 5 + sh[i].p;
+  L.n_jobs = nj;
+  L.d_jobs = cv.take<ColJob>(nj);
+  L.d_flag = cv.take<int>(16);
+  L.bytes = cv.off + 256;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ context
+struct sgp_ctx {
+  int device = 0;
+  int n = 0;
+  cudaStream_t s = nullptr;        // internal stream (graphs are captured on it)
+  cudaStream_t user = nullptr;     // caller's stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_poll[2] = {nullptr, nullptr};
+  sgp_params prm;
+  std::vector<sgp_shape> sh;
+  Layout L;
+  int H = 0, W = 0, p = 0;         // common geometry (every problem of a context has the same H, W, p)
+  int fp64 = 1;
+  // host mirrors
+  std::vector<int2> row, rv, colv, col, colk;
+  std::vector<ColJob> jobs;        // per problem: [A, AT, CONJ, A_raw, AT_raw, KHAT x p]
+  std::vector<int> job_base;
+  std::vector<int> colv_begin, colv_count, col_begin, col_count;
+  std::vector<double> c_const;     // constant start per problem
+  std::vector<double> nS;          // |S| per problem
+  std::vector<int> has_data;
+  std::vector<const float*> truth;
+  std::vector<int> start_in_f0;    // 1: a new start was written to f[0] since the last set-up
+  int mode = 0;                    // 0 not prepared, 1 SGP, 2 RL
+  cudaGraphExec_t g_sgp = nullptr, g_rl = nullptr;
+  int graph_units = 8;
+  CtrlState* h_ctrl = nullptr;     // pinned mirror of the controller array (2 slots for polling)
+};
+
+namespace {
+
+// ---- launch helpers -----------------------------------------------------------------------------
+sgp_status launch(const void* fn, int grid, int block, size_t smem, cudaStream_t s, void** args) {
+  if (grid <= 0) return SGP_OK;
+  CU(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s));
+  return SGP_OK;
+}
+
+sgp_status row_pass(sgp_ctx* c, RowOp op, bool view_list, int extra = -1) {
+  const int si = side_index(c->W);
+  const void* fn = g_reg.row[op][c->fp64][si];
+  const ImgDesc* imgs = c->L.d_imgs;
+  const int2* items = view_list ? c->L.d_rv : c->L.d_row;
+  int n = view_list ? c->L.n_rv : c->L.n_row;
+  void* args4[] = {(void*)&imgs, (void*)&items, (void*)&n, (void*)&extra};
+  return launch(fn, n, kRowBlock, g_reg.row_smem[si], c->s, args4);
+}
+
+// variant: COL_1TOP (views list), COL_1TOP_CONJ, COL_PTO1; job_off selects A/AT/CONJ/raw jobs
+sgp_status col_pass(sgp_ctx* c, int variant, int job_off, int image = -1) {
+  const int si = side_index(c->H);
+  int v = variant;
+  if (variant == COL_PTO1) v = c->p == 1 ? kColPto1P1 : (c->p == 3 ? kColPto1P3 : COL_PTO1);
+  const void* fn = g_reg.col[v][si];
+  const bool views = variant != COL_PTO1;
+  const int2* items = views ? c->L.d_colv : c->L.d_col;
+  int n = views ? c->L.n_colv : c->L.n_col;
+  if (image >= 0) {
+    items += views ? c->colv_begin[image] : c->col_begin[image];
+    n = views ? c->colv_count[image] : c->col_count[image];
+  }
+  // the job index of an item is the problem index; job_off picks the job kind
+  const ColJob* jobs = c->L.d_jobs + job_off;
+  void* args[] = {(void*)&jobs, (void*)&items, (void*)&n};
+  return launch(fn, n, kColBlock, g_reg.col_smem[si], c->s, args);
+}
+
+sgp_status ctrl_pass(sgp_ctx* c, const void* fn) {
+  const ImgDesc* imgs = c->L.d_imgs;
+  void* args[] = {(void*)&imgs};
+  return launch(fn, c->n, kCtrlBlock, 0, c->s, args);
+}
+
+// jobs are stored job-kind-major: kind k of problem i at index k * n + i; KHAT jobs at 5n + ...
+enum JobKind { JOB_A = 0, JOB_AT = 1, JOB_CONJ = 2, JOB_A_RAW = 3, JOB_AT_RAW = 4 };
+
+sgp_status enter(sgp_ctx* c) {
+  CU(cudaSetDevice(c->device));
+  CU(cudaEventRecord(c->ev_in, c->user));
+  CU(cudaStreamWaitEvent(c->s, c->ev_in, 0));
+  return SGP_OK;
+}
+sgp_status leave(sgp_ctx* c) {
+  CU(cudaEventRecord(c->ev_out, c->s));
+  CU(cudaStreamWaitEvent(c->user, c->ev_out, 0));
+  return SGP_OK;
+}
+
+sgp_status read_ctrl(sgp_ctx* c, CtrlState* dst) {
+  CU(cudaMemcpyAsync(dst, c->L.ctrl, sizeof(CtrlState) * c->n, cudaMemcpyDeviceToHost, c->s));
+  CU(cudaStreamSynchronize(c->s));
+  return SGP_OK;
+}
+
+int grid_for(size_t n) { return int(std::min<size_t>((n + 255) / 256, 148 * 16)); }
+
+// ---- iteration sequences --------------------------------------------------------------------------
+sgp_status seq_rl_unit(sgp_ctx* c) {
+  sgp_status st;
+  if ((st = row_pass(c, ROP_RL_UPDATE, false))) return st;
+  if ((st = col_pass(c, COL_1TOP, JOB_A * c->n))) return st;
+  if ((st = row_pass(c, ROP_RL_RATIO, true, 0))) return st;
+  if ((st = col_pass(c, COL_PTO1, JOB_AT * c->n))) return st;
+  return ctrl_pass(c, c->fp64 ? (const void*)&k_ctrl_rl<true> : (const void*)&k_ctrl_rl<false>);
+}
+
+sgp_status seq_sgp_unit(sgp_ctx* c) {
+  sgp_status st;
+  const bool f = c->fp64;
+  if ((st = row_pass(c, ROP_SGP_UPDATE, true))) return st;
+  if ((st = col_pass(c, COL_PTO1, JOB_AT * c->n))) return st;
+  if ((st = row_pass(c, ROP_SGP_GRAD, false))) return st;
+  if ((st = ctrl_pass(c, f ? (const void*)&k_ctrl_alpha<true> : (const void*)&k_ctrl_alpha<false>))) return st;
+  if ((st = row_pass(c, ROP_SGP_Y, false))) return st;
+  if ((st = col_pass(c, COL_1TOP, JOB_A * c->n))) return st;
+  if ((st = row_pass(c, ROP_SGP_AD, true))) return st;
+  if ((st = ctrl_pass(c, f ? (const void*)&k_ctrl_lambda<true> : (const void*)&k_ctrl_lambda<false>))) return st;
+  if ((st = row_pass(c, ROP_SGP_ARMX, false))) return st;
+  return ctrl_pass(c, f ? (const void*)&k_ctrl_lambda_extra<true> : (const void*)&k_ctrl_lambda_extra<false>);
+}
+
+sgp_status seq_sgp_finalize(sgp_ctx* c) {
+  sgp_status st;
+  if ((st = row_pass(c, ROP_SGP_UPDATE, true))) return st;
+  return ctrl_pass(c, c->fp64 ? (const void*)&k_ctrl_alpha<true> : (const void*)&k_ctrl_alpha<false>);
+}
+
+sgp_status build_graph(sgp_ctx* c, bool sgp, cudaGraphExec_t* out) {
+  if (*out) return SGP_OK;
+  cudaGraph_t g = nullptr;
+  CU(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+  sgp_status st = SGP_OK;
+  for (int u = 0; u < c->graph_units && st == SGP_OK; ++u) st = sgp ? seq_sgp_unit(c) : seq_rl_unit(c);
+  cudaError_t e = cudaStreamEndCapture(c->s, &g);
+  if (st) { if (g) cudaGraphDestroy(g); return st; }
+  if (e != cudaSuccess) return fail(SGP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(SGP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return SGP_OK;
+}
+
+// Fresh controller state for every problem, with the current iterate moved to f[0].
+sgp_status reset_ctrl(sgp_ctx* c) {
+  CtrlState* h = c->h_ctrl;
+  CU(cudaMemcpyAsync(h, c->L.ctrl, sizeof(CtrlState) * c->n, cudaMemcpyDeviceToHost, c->s));
+  CU(cudaStreamSynchronize(c->s));
+  for (int i = 0; i < c->n; ++i) {
+    const int cur = c->start_in_f0[i] ? 0 : ((h[i].k - h[i].result_prev) & 1);
+    c->start_in_f0[i] = 0;
+    if (cur) CU(cudaMemcpyAsync(c->L.d[i].f[0], c->L.d[i].f[1], sizeof(float) * c->L.d[i].P,
+                                cudaMemcpyDeviceToDevice, c->s));
+    CtrlState z;
+    memset(&z, 0, sizeof(z));
+    const sgp_params& P = c->prm;
+    z.k = 0; z.fresh = 1; z.done = 0; z.status = 0; z.have_v = 0;
+    z.trace_cap = P.trace_cap;
+    z.stop_kind = STOP_FIXED; z.max_iter = 0;
+    z.M_alpha = P.M_alpha; z.warmup = P.warmup_iters; z.max_backtracks = P.max_backtracks;
+    z.fp64 = c->fp64; z.constraint = P.constraint;
+    z.alpha = P.alpha0; z.alpha_prev = P.alpha0; z.tau = P.tau1; z.lambda = 1.0;
+    z.L1 = P.L1; z.L2 = P.L2;
+    z.beta = P.beta; z.theta = P.theta; z.alpha0 = P.alpha0; z.tau1 = P.tau1;
+    z.alpha_min = P.alpha_min; z.alpha_max = P.alpha_max;
+    z.tol = 0; z.eta = 1.0;
+    z.inv_pS = c->nS[i] > 0 ? 1.0 / (double(c->L.d[i].p) * c->nS[i]) : 0.0;
+    z.ftrue_norm2 = h[i].ftrue_norm2;
+    z.rho_prev = INFINITY;
+    h[i] = z;
+  }
+  CU(cudaMemcpyAsync(c->L.ctrl, h, sizeof(CtrlState) * c->n, cudaMemcpyHostToDevice, c->s));
+  CU(cudaStreamSynchronize(c->s));
+  return SGP_OK;
+}
+
+// Set-up passes from f^(0): A_j f0 (kept in u), J_0, one RL step -> L1/L2 (SGP).  mode 1 SGP, 2 RL.
+sgp_status prepare(sgp_ctx* c, int mode) {
+  for (int i = 0; i < c->n; ++i)
+    if (!c->has_data[i]) return fail(SGP_ERR_STATE, "sgp_set_data was not called for every problem");
+  sgp_status st;
+  if ((st = reset_ctrl(c))) return st;
+  if ((st = row_pass(c, ROP_RL_UPDATE, false))) return st;       // R2C of f0 into plane 0
+  if ((st = col_pass(c, COL_1TOP, JOB_A * c->n))) return st;
+  if ((st = row_pass(c, ROP_RL_RATIO, true, 1))) return st;      // u = A f0, J_0, r spectra
+  if ((st = col_pass(c, COL_PTO1, JOB_AT * c->n))) return st;    // plane 0 = sum_j A_j^T r_j
+  const bool bounds = mode == 1;
+  if (bounds && (st = row_pass(c, ROP_MINMAX, false))) return st;
+  {
+    const ImgDesc* imgs = c->L.d_imgs;
+    int adaptive = c->prm.adaptive_L, wb = bounds ? 1 : 0;
+    void* args[] = {(void*)&imgs, (void*)&adaptive, (void*)&wb};
+    if ((st = launch(c->fp64 ? (const void*)&k_ctrl_setup<true> : (const void*)&k_ctrl_setup<false>, c->n,
+                     kCtrlBlock, 0, c->s, args)))
+      return st;
+  }
+  if (mode == 2) {
+    // the set-up left sum_j A_j^T r_j of f0 in plane 0: RL continues from there
+    for (int i = 0; i < c->n; ++i) {
+      int one = 1;
+      CU(cudaMemcpyAsync(&c->L.ctrl[i].have_v, &one, sizeof(int), cudaMemcpyHostToDevice, c->s));
+      CU(cudaStreamSynchronize(c->s));
+    }
+  }
+  CU(read_ctrl(c, c->h_ctrl) == SGP_OK ? cudaSuccess : cudaErrorUnknown);
+  for (int i = 0; i < c->n; ++i)
+    if (c->h_ctrl[i].status)
+      return fail(sgp_status(c->h_ctrl[i].status), "set-up failed for problem " + std::to_string(i) +
+                                                       " (no positive pixel after one RL step, or non-finite J)");
+  c->mode = mode;
+  return SGP_OK;
+}
+
+sgp_status arm(sgp_ctx* c, int kind, int n_iter, double tol, double eta) {
+  const ImgDesc* imgs = c->L.d_imgs;
+  int n = c->n, rel = 1;
+  void* args[] = {(void*)&imgs, (void*)&n, (void*)&kind, (void*)&n_iter, (void*)&tol, (void*)&eta, (void*)&rel};
+  return launch((const void*)&k_ctrl_arm, (n + 127) / 128, 128, 0, c->s, args);
+}
+
+sgp_status run_fixed(sgp_ctx* c, bool sgp, int n_iter) {
+  if (n_iter < 0) return fail(SGP_ERR_ARG, "negative iteration count");
+  sgp_status st;
+  if (c->mode != (sgp ? 1 : 2) && (st = prepare(c, sgp ? 1 : 2))) return st;
+  if (n_iter == 0) return SGP_OK;
+  if ((st = build_graph(c, sgp, sgp ? &c->g_sgp : &c->g_rl))) return st;
+  if ((st = arm(c, STOP_FIXED, n_iter, 0.0, 1.0))) return st;
+  const int launches = (n_iter + c->graph_units - 1) / c->graph_units;
+  for (int l = 0; l < launches; ++l) CU(cudaGraphLaunch(sgp ? c->g_sgp : c->g_rl, c->s));
+  if (sgp && (st = seq_sgp_finalize(c))) return st;
+  return SGP_OK;
+}
+
+sgp_status run_until(sgp_ctx* c, bool sgp, const sgp_stop_rule* rule, int* iters) {
+  if (!rule) return fail(SGP_ERR_ARG, "rule is NULL");
+  if (rule->kind < 0 || rule->kind > 3) return fail(SGP_ERR_ARG, "unknown stop rule");
+  if (rule->max_iter <= 0) return fail(SGP_ERR_ARG, "max_iter must be positive");
+  sgp_status st;
+  if (c->mode != (sgp ? 1 : 2) && (st = prepare(c, sgp ? 1 : 2))) return st;
+  if (rule->kind == STOP_MIN_ERROR)
+    for (int i = 0; i < c->n; ++i)
+      if (!c->truth[i]) return fail(SGP_ERR_ARG, "minimum-error stop needs sgp_set_truth");
+  if ((st = build_graph(c, sgp, sgp ? &c->g_sgp : &c->g_rl))) return st;
+  if ((st = arm(c, rule->kind, rule->max_iter, rule->tol, rule->eta))) return st;
+  cudaGraphExec_t g = sgp ? c->g_sgp : c->g_rl;
+  const int max_launches = rule->max_iter / c->graph_units + 2;
+  CtrlState* slot[2] = {c->h_ctrl, c->h_ctrl + c->n};
+  // keep one chunk in flight while the flags of the previous one are inspected
+  CU(cudaGraphLaunch(g, c->s));
+  CU(cudaMemcpyAsync(slot[0], c->L.ctrl, sizeof(CtrlState) * c->n, cudaMemcpyDeviceToHost, c->s));
+  CU(cudaEventRecord(c->ev_poll[0], c->s));
+  int cur = 0;
+  for (int l = 1; l < max_launches; ++l) {
+    CU(cudaGraphLaunch(g, c->s));
+    CU(cudaMemcpyAsync(slot[cur ^ 1], c->L.ctrl, sizeof(CtrlState) * c->n, cudaMemcpyDeviceToHost, c->s));
+    CU(cudaEventRecord(c->ev_poll[cur ^ 1], c->s));
+    CU(cudaEventSynchronize(c->ev_poll[cur]));
+    bool all = true;
+    for (int i = 0; i < c->n; ++i) all = all && slot[cur][i].done >= 1;
+    if (all) break;
+    cur ^= 1;
+  }
+  if (sgp && (st = seq_sgp_finalize(c))) return st;
+  if ((st = read_ctrl(c, c->h_ctrl))) return st;
+  sgp_status res = SGP_OK;
+  for (int i = 0; i < c->n; ++i) {
+    const CtrlState& h = c->h_ctrl[i];
+    if (iters) iters[i] = h.k - h.result_prev;
+    if (h.status && res == SGP_OK) res = fail(sgp_status(h.status), "problem " + std::to_string(i) + " stopped with an error");
+    if (res == SGP_OK && h.done < 1) res = fail(SGP_ERR_TIMEOUT, "stop rule not reached");
+  }
+  return res;
+}
+
+sgp_status check_image(sgp_ctx* c, int image) {
+  if (!c) return fail(SGP_ERR_ARG, "ctx is NULL");
+  if (image < 0 || image >= c->n) return fail(SGP_ERR_ARG, "image index out of range");
+  return SGP_OK;
+}
+
+}  // namespace
+
+// ================================================================================== C ABI
+extern "C" {
+
+void sgp_params_default(sgp_params* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->beta = 1e-4; o->theta = 0.4; o->alpha0 = 1.3; o->tau1 = 0.5;
+  o->alpha_min = 1e-5; o->alpha_max = 1e5; o->M_alpha = 3; o->warmup_iters = 20;
+  o->adaptive_L = 1; o->max_backtracks = 30; o->L1 = 1e-10; o->L2 = 1e10; o->sigma_R = 1e-2;
+  o->constraint = 0; o->flux_c = 0.0; o->reduce_fp64 = 1; o->trace_cap = 4096;
+}
+
+const char* sgp_last_error(void) { return g_err.c_str(); }
+
+static sgp_status validate_shapes(int n, const sgp_shape* sh) {
+  if (n <= 0 || !sh) return fail(SGP_ERR_ARG, "need at least one problem");
+  for (int i = 0; i < n; ++i) {
+    if (side_index(sh[i].H) < 0 || side_index(sh[i].W) < 0)
+      return fail(SGP_ERR_SIZE_UNSUPPORTED, "H and W must be 16..2048 and a power of two or 3 times one");
+    if (sh[i].p < 1 || sh[i].p > kMaxViews) return fail(SGP_ERR_SIZE_UNSUPPORTED, "p must be 1..8");
+    if (sh[i].psf_origin != SGP_PSF_CENTER && sh[i].psf_origin != SGP_PSF_CORNER)
+      return fail(SGP_ERR_ARG, "psf_origin must be SGP_PSF_CENTER or SGP_PSF_CORNER");
+    if (sh[i].H != sh[0].H || sh[i].W != sh[0].W || sh[i].p != sh[0].p)
+      return fail(SGP_ERR_SIZE_UNSUPPORTED, "problems of one context must share H, W and p");
+  }
+  return SGP_OK;
+}
+
+size_t sgp_workspace_bytes(int n, const sgp_shape* shapes, const sgp_params* params) {
+  if (validate_shapes(n, shapes) != SGP_OK) return 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!g_reg_ready) {
+    memset(&g_reg, 0, sizeof(g_reg));
+    register_small(g_reg);
+    register_mid(g_reg);
+    register_large(g_reg);
+    g_reg_ready = true;
+  }
+  sgp_params P;
+  if (params) P = *params; else sgp_params_default(&P);
+  std::vector<unsigned char> hb(n, 1);   // count room for background arrays
+  Layout L;
+  plan_layout(nullptr, n, shapes, std::max(P.trace_cap, 1), reinterpret_cast<const bool*>(hb.data()), L);
+  return L.bytes;
+}
+
+sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const sgp_inputs* in,
+                            const sgp_params* params, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!out) return fail(SGP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  sgp_status st = validate_shapes(n, shapes);
+  if (st) return st;
+  if (!in) return fail(SGP_ERR_ARG, "inputs are NULL");
+  if (!workspace) return fail(SGP_ERR_WORKSPACE, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(workspace) & 255) return fail(SGP_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  for (int i = 0; i < n; ++i) {
+    if (!in[i].psfs) return fail(SGP_ERR_ARG, "psfs is NULL");
+    if (shapes[i].has_mask && !in[i].mask) return fail(SGP_ERR_ARG, "has_mask set but mask is NULL");
+  }
+  sgp_params P;
+  if (params) P = *params; else sgp_params_default(&P);
+  if (P.M_alpha < 1 || P.M_alpha > kMaxHist) return fail(SGP_ERR_ARG, "M_alpha must be 1..16");
+  if (P.max_backtracks < 0 || P.max_backtracks > 30) return fail(SGP_ERR_ARG, "max_backtracks must be 0..30");
+  if (!(P.theta > 0 && P.theta < 1) || !(P.beta > 0 && P.beta < 1)) return fail(SGP_ERR_ARG, "beta, theta must lie in (0,1)");
+  if (!(P.alpha_min > 0 && P.alpha_min < P.alpha_max)) return fail(SGP_ERR_ARG, "need 0 < alpha_min < alpha_max");
+  if (!P.adaptive_L && !(P.L1 > 0 && P.L1 < P.L2)) return fail(SGP_ERR_ARG, "need 0 < L1 < L2");
+  if (P.trace_cap < 1) P.trace_cap = 1;
+  if (P.constraint != 0) return fail(SGP_ERR_ARG, "flux constraint is not available in this build");
+
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if ((st = ensure_device_ready(dev))) return st;
+
+  sgp_ctx* c = new sgp_ctx();
+  c->device = dev;
+  c->n = n;
+  c->prm = P;
+  c->fp64 = P.reduce_fp64 ? 1 : 0;
+  c->sh.assign(shapes, shapes + n);
+  c->H = shapes[0].H; c->W = shapes[0].W; c->p = shapes[0].p;
+  c->user = reinterpret_cast<cudaStream_t>(stream);
+  auto bail = [&](sgp_status s) { sgp_destroy(c); return s; };
+  if (cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_poll[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_poll[1], cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(SGP_ERR_CUDA, "stream/event creation failed"));
+  if (cudaMallocHost(&c->h_ctrl, sizeof(CtrlState) * 2 * n) != cudaSuccess)
+    return bail(fail(SGP_ERR_CUDA, "pinned host buffer allocation failed"));
+
+  std::vector<unsigned char> hb(n);
+  for (int i = 0; i < n; ++i) hb[i] = in[i].b != nullptr;
+  plan_layout(nullptr, n, shapes, P.trace_cap, reinterpret_cast<const bool*>(hb.data()), c->L);
+  if (c->L.bytes > workspace_bytes)
+    return bail(fail(SGP_ERR_WORKSPACE, "workspace too small: need " + std::to_string(c->L.bytes) + " bytes"));
+  plan_layout(static_cast<char*>(workspace), n, shapes, P.trace_cap, reinterpret_cast<const bool*>(hb.data()), c->L);
+  Layout& L = c->L;
+  if ((st = enter(c))) return bail(st);
+
+  // item lists (each problem's items contiguous) and per-problem descriptors
+  const int rpi = rows_per_item(c->W), cpi = cols_per_item(c->H), M = c->W / 2;
+  int r0 = 0, rv0 = 0;
+  c->colv_begin.resize(n); c->colv_count.resize(n); c->col_begin.resize(n); c->col_count.resize(n);
+  for (int i = 0; i < n; ++i) {
+    ImgDesc& d = L.d[i];
+    d.row_item0 = r0; d.rv_item0 = rv0;
+    for (int y = 0; y < d.H; y += rpi) c->row.push_back(make_int2(i, y));
+    for (int j = 0; j < d.p; ++j)
+      for (int y = 0; y < d.H; y += rpi) c->rv.push_back(make_int2(i, y | (j << 16)));
+    r0 += d.n_row_items; rv0 += d.n_rv_items;
+    c->colv_begin[i] = int(c->colv.size());
+    for (int j = 0; j < d.p; ++j)
+      for (int x = 0; x < M; x += cpi) c->colv.push_back(make_int2(i, x | (j << 16)));
+    c->colv_count[i] = int(c->colv.size()) - c->colv_begin[i];
+    c->col_begin[i] = int(c->col.size());
+    for (int x = 0; x < M; x += cpi) c->col.push_back(make_int2(i, x));
+    c->col_count[i] = int(c->col.size()) - c->col_begin[i];
+    d.w_scalar = 1.0f / float(d.p);
+    d.a1_scalar = float(d.p);
+    for (int j = 0; j < kMaxViews; ++j) d.bs[j] = j < d.p ? in[i].b_const[j] : 0.0f;
+    d.ftrue = nullptr;
+  }
+  // column jobs: kinds A, AT, CONJ, A_raw, AT_raw (index kind*n + i), then p KHAT jobs per problem
+  c->jobs.assign(L.n_jobs, ColJob{});
+  int kh = 5 * n;
+  for (int i = 0; i < n; ++i) {
+    ImgDesc& d = L.d[i];
+    const size_t ps = d.P / 2;
+    float2* spec = reinterpret_cast<float2*>(d.spec);
+    ColJob base{};
+    base.khat = reinterpret_cast<const float2*>(L.khat[i]);
+    base.khatq = reinterpret_cast<float2*>(L.khatq[i]);
+    base.H = d.H; base.M = d.W / 2; base.plane_stride = ps;
+    ColJob a = base;      a.in = spec; a.out = spec + ps; a.nin = 1; a.nout = d.p; a.ctrl = L.ctrl + i;
+    ColJob at = base;     at.in = spec + ps; at.out = spec; at.nin = d.p; at.nout = 1; at.ctrl = L.ctrl + i;
+    ColJob cj = a;        cj.ctrl = nullptr;
+    ColJob ar = a;        ar.ctrl = nullptr;
+    ColJob atr = at;      atr.ctrl = nullptr;
+    c->jobs[JOB_A * n + i] = a;
+    c->jobs[JOB_AT * n + i] = at;
+    c->jobs[JOB_CONJ * n + i] = cj;
+    c->jobs[JOB_A_RAW * n + i] = ar;
+    c->jobs[JOB_AT_RAW * n + i] = atr;
+    for (int j = 0; j < d.p; ++j) {
+      ColJob k = base;
+      k.in = spec + size_t(j + 1) * ps;
+      k.out = reinterpret_cast<float2*>(L.khat[i]) + size_t(j) * ps;
+      k.khatq = reinterpret_cast<float2*>(L.khatq[i]) + size_t(j) * d.H;
+      k.nin = 1; k.nout = 1; k.ctrl = nullptr;
+      k.corner = shapes[i].psf_origin == SGP_PSF_CORNER;
+      c->jobs[kh++] = k;
+    }
+  }
+  // the column-item lists address job index = problem index; the spectrum set-up needs its own
+  for (int i = 0, jb = 5 * n; i < n; ++i)
+    for (int j = 0; j < L.d[i].p; ++j, ++jb)
+      for (int x = 0; x < M; x += cpi) c->colk.push_back(make_int2(jb, x));
+  c->c_const.assign(n, 0.0);
+  c->nS.assign(n, 0.0);
+  c->has_data.assign(n, 0);
+  c->truth.assign(n, nullptr);
+  c->start_in_f0.assign(n, 1);
+
+  // PSF statistics and normalisation scale (Sect. 1 / 2.4: unit volume over the domain)
+  const size_t P0 = L.d[0].P;
+  std::vector<double> stats(4 * kMaxViews);
+  for (int i = 0; i < n && st == SGP_OK; ++i) {
+    ImgDesc& d = L.d[i];
+    void* a[] = {(void*)&in[i].psfs, (void*)&d.P, (void*)&L.scratch[i]};
+    if ((st = launch((const void*)&k_plane_stats, d.p, 256, 0, c->s, a))) break;
+    if (cudaMemcpyAsync(stats.data(), L.scratch[i], sizeof(double) * 4 * d.p, cudaMemcpyDeviceToHost, c->s) != cudaSuccess ||
+        cudaStreamSynchronize(c->s) != cudaSuccess) { st = fail(SGP_ERR_CUDA, "PSF statistics failed"); break; }
+    for (int j = 0; j < d.p; ++j) {
+      const double sum = stats[4 * j], mx = stats[4 * j + 1], mn = stats[4 * j + 2], nf = stats[4 * j + 3];
+      if (nf > 0 || !(sum > 0) || !(mx > 0)) { st = fail(SGP_ERR_PSF, "PSF must be finite with a positive sum"); break; }
+      if (mn < -1e-6 * mx) { st = fail(SGP_ERR_PSF, "PSF has significantly negative samples"); break; }
+      // scale folds the unit-volume normalisation and the 1/(H*M) of the unnormalised transforms;
+      // tiny negative round-off is clamped to 0 by the row pass (its effect on the sum is below 1e-6)
+      int idx = 5 * n;
+      for (int q = 0; q < i; ++q) idx += L.d[q].p;
+      c->jobs[idx + j].scale = float(1.0 / (sum * double(d.H) * double(d.W / 2)));
+    }
+    if (st) break;
+    // R2C of each view's PSF into spectrum planes 1..p
+    const int si = side_index(d.W);
+    const float* src = in[i].psfs;
+    float2* dst = reinterpret_cast<float2*>(d.spec) + d.P / 2;
+    size_t ivs = d.P, ovs = d.P / 2;
+    int Hh = d.H, nv = d.p, clamp = 1;
+    const int per_view = (d.H + rows_per_item(d.W) - 1) / rows_per_item(d.W);
+    void* a2[] = {(void*)&src, (void*)&ivs, (void*)&dst, (void*)&ovs, (void*)&Hh, (void*)&nv, (void*)&clamp};
+    if ((st = launch(g_reg.row[ROP_R2C][0][si], per_view * d.p, kRowBlock, g_reg.row_smem[si], c->s, a2))) break;
+  }
+  if (st) return bail(st);
+  if (cudaMemcpyAsync(L.d_jobs, c->jobs.data(), sizeof(ColJob) * L.n_jobs, cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
+      cudaMemcpyAsync(L.d_imgs, L.d.data(), sizeof(ImgDesc) * n, cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
+      cudaMemcpyAsync(L.d_row, c->row.data(), sizeof(int2) * c->row.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
+      cudaMemcpyAsync(L.d_rv, c->rv.data(), sizeof(int2) * c->rv.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
+      cudaMemcpyAsync(L.d_colv, c->colv.data(), sizeof(int2) * c->colv.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
+      cudaMemcpyAsync(L.d_col, c->col.data(), sizeof(int2) * c->col.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
+      cudaMemcpyAsync(L.d_colk, c->colk.data(), sizeof(int2) * c->colk.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess)
+    return bail(fail(SGP_ERR_CUDA, "descriptor upload failed"));
+  {  // PSF spectra (forward column transforms, P/Q packing, scaling, origin shift)
+    const int si = side_index(c->H);
+    const ColJob* jobs = L.d_jobs;
+    const int2* items = L.d_colk;
+    int nk = L.n_colk;
+    void* a[] = {(void*)&jobs, (void*)&items, (void*)&nk};
+    if ((st = launch(g_reg.col[COL_KHAT][si], nk, kColBlock, g_reg.col_smem[si], c->s, a))) return bail(st);
+  }
+  for (int i = 0; i < n; ++i) {
+    ImgDesc& d = L.d[i];
+    if (in[i].b && cudaMemcpyAsync(L.bcopy[i], in[i].b, sizeof(float) * d.P * d.p, cudaMemcpyDeviceToDevice, c->s) != cudaSuccess)
+      return bail(fail(SGP_ERR_CUDA, "background copy failed"));
+    // zero state so that stray reads are finite
+    if (cudaMemsetAsync(d.f[0], 0, sizeof(float) * d.P * 4, c->s) != cudaSuccess)   // f[0], f[1], grad[0], grad[1]
+      return bail(fail(SGP_ERR_CUDA, "memset failed"));
+  }
+  // boundary problems: alpha_j = K_j (x) M_S, R and M_R / alpha (Sect. 2.4, Eq. Rdef)
+  for (int i = 0; i < n; ++i) {
+    ImgDesc& d = L.d[i];
+    if (!d.boundary) continue;
+    if (cudaMemcpyAsync(L.mS[i], in[i].mask, d.P, cudaMemcpyDeviceToDevice, c->s) != cudaSuccess)
+      return bail(fail(SGP_ERR_CUDA, "mask copy failed"));
+    float* mf = d.u;   // scratch plane
+    void* a[] = {(void*)&in[i].mask, (void*)&mf, (void*)&d.P};
+    if ((st = launch((const void*)&k_u8_to_float, grid_for(d.P), 256, 0, c->s, a))) return bail(st);
+    const int si = side_index(d.W);
+    float2* sp0 = reinterpret_cast<float2*>(d.spec);
+    size_t ivs = d.P, ovs = d.P / 2;
+    int Hh = d.H, one = 1, clamp = 0;
+    const int per_view = (d.H + rows_per_item(d.W) - 1) / rows_per_item(d.W);
+    const float* mfc = mf;
+    void* a2[] = {(void*)&mfc, (void*)&ivs, (void*)&sp0, (void*)&ovs, (void*)&Hh, (void*)&one, (void*)&clamp};
+    if ((st = launch(g_reg.row[ROP_R2C][0][si], per_view, kRowBlock, g_reg.row_smem[si], c->s, a2))) return bail(st);
+    if ((st = col_pass(c, COL_1TOP_CONJ, JOB_CONJ * n, i))) return bail(st);
+    const float2* sp1 = sp0 + d.P / 2;
+    float* alpha = d.Ad;
+    int nv = d.p;
+    float sc = 1.0f;
+    void* a3[] = {(void*)&sp1, (void*)&ovs, (void*)&alpha, (void*)&ivs, (void*)&Hh, (void*)&nv, (void*)&sc};
+    if ((st = launch(g_reg.row[ROP_C2R][0][si], per_view * d.p, kRowBlock, g_reg.row_smem[si], c->s, a3))) return bail(st);
+    float sig = float(P.sigma_R);
+    float* w = const_cast<float*>(d.w);
+    const float* al = alpha;
+    void* a4[] = {(void*)&al, (void*)&nv, (void*)&d.P, (void*)&sig, (void*)&w};
+    if ((st = launch((const void*)&k_make_w, grid_for(d.P), 256, 0, c->s, a4))) return bail(st);
+  }
+  // controller array: zero, then fresh state at first use
+  if (cudaMemsetAsync(L.ctrl, 0, sizeof(CtrlState) * n, c->s) != cudaSuccess) return bail(fail(SGP_ERR_CUDA, "memset failed"));
+  if (cudaStreamSynchronize(c->s) != cudaSuccess) {
+    return bail(fail(SGP_ERR_CUDA, std::string("set-up kernels failed: ") + cudaGetErrorString(cudaGetLastError())));
+  }
+  (void)P0;
+  if ((st = leave(c))) return bail(st);
+  *out = c;
+  return SGP_OK;
+}
+
+sgp_status sgp_create(sgp_ctx** out, const sgp_shape* shape, const float* psfs, const float* b,
+                      const float* b_const, const uint8_t* mask, const sgp_params* params,
+                      void* workspace, size_t workspace_bytes, void* stream) {
+  if (!shape) return fail(SGP_ERR_ARG, "shape is NULL");
+  sgp_inputs in;
+  memset(&in, 0, sizeof(in));
+  in.psfs = psfs;
+  in.b = b;
+  in.mask = mask;
+  if (!b) {
+    if (!b_const) return fail(SGP_ERR_ARG, "give either a background array or constants");
+    for (int j = 0; j < shape->p && j < kMaxViews; ++j) in.b_const[j] = b_const[j];
+  }
+  return sgp_create_batch(out, 1, shape, &in, params, workspace, workspace_bytes, stream);
+}
+
+sgp_status sgp_set_data(sgp_ctx* c, int image, const float* g) {
+  sgp_status st = check_image(c, image);
+  if (st) return st;
+  if (!g) return fail(SGP_ERR_ARG, "g is NULL");
+  if ((st = enter(c))) return st;
+  ImgDesc& d = c->L.d[image];
+  int* bad = c->L.d_flag;
+  CU(cudaMemsetAsync(bad, 0, sizeof(int), c->s));
+  const uint8_t* mask = c->L.mS[image];
+  size_t P = d.P;
+  int p = d.p;
+  {
+    float* gout = d.g;
+    void* a[] = {(void*)&g, (void*)&mask, (void*)&gout, (void*)&P, (void*)&p, (void*)&bad};
+    if ((st = launch((const void*)&k_prepare_data, grid_for(P * p), 256, 0, c->s, a))) return st;
+  }
+  {
+    const float* gg = d.g;
+    const float* bb = d.b;
+    float* bc = reinterpret_cast<float*>(c->L.scratch[image] + 32);   // p floats of constants
+    CU(cudaMemcpyAsync(bc, d.bs, sizeof(float) * kMaxViews, cudaMemcpyHostToDevice, c->s));
+    const float* bcc = bc;
+    double* out = c->L.scratch[image];
+    void* a[] = {(void*)&gg, (void*)&bb, (void*)&bcc, (void*)&P, (void*)&out};
+    if ((st = launch((const void*)&k_data_sums, p, 256, 0, c->s, a))) return st;
+  }
+  int hbad = 0;
+  double sums[3 * kMaxViews];
+  CU(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+  CU(cudaMemcpyAsync(sums, c->L.scratch[image], sizeof(double) * 3 * p, cudaMemcpyDeviceToHost, c->s));
+  CU(cudaStreamSynchronize(c->s));
+  if (hbad) return fail(SGP_ERR_NONFINITE, "data contain negative or non-finite values");
+  // constant start of Sect. 3.1: mean over views of (sum_S g - sum_S b) / |S|
+  double cm = 0.0, gm = 0.0;
+  const double nS = sums[2];
+  if (!(nS > 0)) return fail(SGP_ERR_ARG, "the mask selects no pixel");
+  for (int j = 0; j < p; ++j) { cm += (sums[3 * j] - sums[3 * j + 1]) / nS; gm += sums[3 * j] / nS; }
+  cm /= p; gm /= p;
+  if (!(cm > 0)) cm = std::max(gm, 1e-3);
+  c->c_const[image] = cm;
+  c->nS[image] = nS;
+  c->has_data[image] = 1;
+  {
+    float* f0 = d.f[0];
+    const float* w = d.w;
+    const float* src = nullptr;
+    float v = float(cm);
+    void* a[] = {(void*)&f0, (void*)&w, (void*)&src, (void*)&v, (void*)&P};
+    if ((st = launch((const void*)&k_fill_start, grid_for(P), 256, 0, c->s, a))) return st;
+  }
+  c->start_in_f0[image] = 1;
+  c->mode = 0;
+  return leave(c);
+}
+
+sgp_status sgp_set_start(sgp_ctx* c, int image, int mode, const float* f0) {
+  sgp_status st = check_image(c, image);
+  if (st) return st;
+  if (!c->has_data[image]) return fail(SGP_ERR_STATE, "call sgp_set_data first");
+  if ((st = enter(c))) return st;
+  ImgDesc& d = c->L.d[image];
+  float* dst = d.f[0];
+  const float* w = d.w;
+  const float* src = nullptr;
+  float v = 0.0f;
+  switch (mode) {
+    case SGP_START_ZERO: v = 0.0f; break;
+    case SGP_START_DATA: src = d.g; break;   // g_1; pixels outside S carry -1 and clip to 0
+    case SGP_START_CONSTANT: v = float(c->c_const[image]); break;
+    case SGP_START_USER:
+      if (!f0) return fail(SGP_ERR_ARG, "f0 is NULL");
+      src = f0;
+      break;
+    default: return fail(SGP_ERR_ARG, "unknown start mode");
+  }
+  size_t P = d.P;
+  void* a[] = {(void*)&dst, (void*)&w, (void*)&src, (void*)&v, (void*)&P};
+  if ((st = launch((const void*)&k_fill_start, grid_for(P), 256, 0, c->s, a))) return st;
+  c->start_in_f0[image] = 1;
+  c->mode = 0;
+  CU(cudaStreamSynchronize(c->s));
+  return leave(c);
+}
+
+sgp_status sgp_set_truth(sgp_ctx* c, int image, const float* f_true) {
+  sgp_status st = check_image(c, image);
+  if (st) return st;
+  if ((st = enter(c))) return st;
+  ImgDesc& d = c->L.d[image];
+  c->truth[image] = f_true;
+  d.ftrue = f_true;
+  CU(cudaMemcpyAsync(c->L.d_imgs + image, &d, sizeof(ImgDesc), cudaMemcpyHostToDevice, c->s));
+  double nrm = 0.0;
+  if (f_true) {
+    double* out = c->L.scratch[image] + 40;
+    size_t P = d.P;
+    void* a[] = {(void*)&f_true, (void*)&P, (void*)&out};
+    if ((st = launch((const void*)&k_sumsq, 1, 256, 0, c->s, a))) return st;
+    CU(cudaMemcpyAsync(&nrm, out, sizeof(double), cudaMemcpyDeviceToHost, c->s));
+  }
+  CU(cudaMemcpyAsync(&c->L.ctrl[image].ftrue_norm2, &nrm, sizeof(double), cudaMemcpyHostToDevice, c->s));
+  CU(cudaStreamSynchronize(c->s));
+  return leave(c);
+}
+
+sgp_status rl_iterate(sgp_ctx* c, int n) {
+  if (!c) return fail(SGP_ERR_ARG, "ctx is NULL");
+  sgp_status st = enter(c);
+  if (st || (st = run_fixed(c, false, n))) return st;
+  return leave(c);
+}
+
+sgp_status sgp_iterate(sgp_ctx* c, int n) {
+  if (!c) return fail(SGP_ERR_ARG, "ctx is NULL");
+  sgp_status st = enter(c);
+  if (st || (st = run_fixed(c, true, n))) return st;
+  return leave(c);
+}
+
+sgp_status sgp_solve_until(sgp_ctx* c, const sgp_stop_rule* rule, int* iters) {
+  if (!c) return fail(SGP_ERR_ARG, "ctx is NULL");
+  sgp_status st = enter(c);
+  if (st) return st;
+  const sgp_status res = run_until(c, true, rule, iters);
+  if ((st = leave(c))) return st;
+  return res;
+}
+
+sgp_status rl_solve_until(sgp_ctx* c, const sgp_stop_rule* rule, int* iters) {
+  if (!c) return fail(SGP_ERR_ARG, "ctx is NULL");
+  sgp_status st = enter(c);
+  if (st) return st;
+  const sgp_status res = run_until(c, false, rule, iters);
+  if ((st = leave(c))) return st;
+  return res;
+}
+
+sgp_status sgp_get_info(sgp_ctx* c, int image, sgp_info* o) {
+  sgp_status st = check_image(c, image);
+  if (st) return st;
+  if (!o) return fail(SGP_ERR_ARG, "out is NULL");
+  if ((st = enter(c))) return st;
+  if (c->mode == 0 && (st = prepare(c, 1))) return st;
+  CtrlState h;
+  CU(cudaMemcpyAsync(&h, c->L.ctrl + image, sizeof(CtrlState), cudaMemcpyDeviceToHost, c->s));
+  CU(cudaStreamSynchronize(c->s));
+  memset(o, 0, sizeof(*o));
+  o->k = h.k - h.result_prev;
+  o->status = h.status;
+  o->stopped = h.done >= 1;
+  o->trace_n = h.trace_n;
+  o->J = h.J;
+  o->D = 2.0 * h.J * h.inv_pS;
+  o->L1 = h.L1; o->L2 = h.L2; o->alpha = h.alpha; o->tau = h.tau; o->lambda = h.lambda; o->rho = h.rho;
+  o->nS = c->nS[image];
+  o->flux_c = c->c_const[image];
+  return leave(c);
+}
+
+sgp_status kl_value(sgp_ctx* c, int image, double* out) {
+  if (!out) return fail(SGP_ERR_ARG, "out is NULL");
+  sgp_info info;
+  sgp_status st = sgp_get_info(c, image, &info);
+  if (st) return st;
+  *out = info.J;
+  return SGP_OK;
+}
+
+sgp_status sgp_get_f(sgp_ctx* c, int image, float* dst) {
+  sgp_status st = check_image(c, image);
+  if (st) return st;
+  if (!dst) return fail(SGP_ERR_ARG, "dst is NULL");
+  if ((st = enter(c))) return st;
+  ImgDesc& d = c->L.d[image];
+  int par = 0;
+  if (!c->start_in_f0[image]) {
+    CtrlState h;
+    CU(cudaMemcpyAsync(&h, c->L.ctrl + image, sizeof(CtrlState), cudaMemcpyDeviceToHost, c->s));
+    CU(cudaStreamSynchronize(c->s));
+    par = (h.k - h.result_prev) & 1;
+  }
+  CU(cudaMemcpyAsync(dst, d.f[par], sizeof(float) * d.P, cudaMemcpyDeviceToDevice, c->s));
+  CU(cudaStreamSynchronize(c->s));
+  return leave(c);
+}
+
+sgp_status sgp_get_trace(sgp_ctx* c, int image, double* out, int cap, int* count) {
+  sgp_status st = check_image(c, image);
+  if (st) return st;
+  if ((st = enter(c))) return st;
+  CtrlState h;
+  CU(cudaMemcpyAsync(&h, c->L.ctrl + image, sizeof(CtrlState), cudaMemcpyDeviceToHost, c->s));
+  CU(cudaStreamSynchronize(c->s));
+  const int avail = std::min(h.trace_n, h.trace_cap);
+  const int m = out ? std::min(avail, cap) : 0;
+  if (m > 0) {
+    CU(cudaMemcpyAsync(out, c->L.d[image].trace, sizeof(double) * kTraceStride * m, cudaMemcpyDeviceToHost, c->s));
+    CU(cudaStreamSynchronize(c->s));
+  }
+  if (count) *count = avail;
+  return leave(c);
+}
+
+sgp_status sgp_apply_A(sgp_ctx* c, int image, const float* f, float* out) {
+  sgp_status st = check_image(c, image);
+  if (st) return st;
+  if (!f || !out) return fail(SGP_ERR_ARG, "NULL array");
+  if ((st = enter(c))) return st;
+  ImgDesc& d = c->L.d[image];
+  const int si = side_index(d.W);
+  const int per_view = (d.H + rows_per_item(d.W) - 1) / rows_per_item(d.W);
+  size_t P = d.P, ivs = d.P, ovs = d.P / 2;
+  int Hh = d.H, one = 1, clamp = 0, p = d.p;
+  const float* src = f;
+  if (d.boundary) {   // M_R f (into a scratch plane)
+    CU(cudaMemcpyAsync(d.Ad, f, sizeof(float) * P, cudaMemcpyDeviceToDevice, c->s));
+    float* x = d.Ad;
+    const float* w = d.w;
+    const float* gnull = nullptr;
+    void* a[] = {(void*)&x, (void*)&P, (void*)&one, (void*)&w, (void*)&gnull};
+    if ((st = launch((const void*)&k_apply_mask, grid_for(P), 256, 0, c->s, a))) return st;
+    src = d.Ad;
+  }
+  float2* sp0 = reinterpret_cast<float2*>(d.spec);
+  void* a2[] = {(void*)&src, (void*)&ivs, (void*)&sp0, (void*)&ovs, (void*)&Hh, (void*)&one, (void*)&clamp};
+  if ((st = launch(g_reg.row[ROP_R2C][0][si], per_view, kRowBlock, g_reg.row_smem[si], c->s, a2))) return st;
+  if ((st = col_pass(c, COL_1TOP, JOB_A_RAW * c->n, image))) return st;
+  const float2* sp1 = sp0 + P / 2;
+  float sc = 1.0f;
+  void* a3[] = {(void*)&sp1, (void*)&ovs, (void*)&out, (void*)&ivs, (void*)&Hh, (void*)&p, (void*)&sc};
+  if ((st = launch(g_reg.row[ROP_C2R][0][si], per_view * p, kRowBlock, g_reg.row_smem[si], c->s, a3))) return st;
+  if (d.boundary) {   // M_S (A f)
+    const float* wnull = nullptr;
+    const float* gg = d.g;   // sentinel -1 outside S, per view
+    void* a[] = {(void*)&out, (void*)&P, (void*)&p, (void*)&wnull, (void*)&gg};
+    if ((st = launch((const void*)&k_apply_mask, grid_for(P * p), 256, 0, c->s, a))) return st;
+  }
+  c->mode = 0;
+  return leave(c);
+}
+
+sgp_status sgp_apply_AT(sgp_ctx* c, int image, const float* y, float* out) {
+  sgp_status st = check_image(c, image);
+  if (st) return st;
+  if (!y || !out) return fail(SGP_ERR_ARG, "NULL array");
+  if ((st = enter(c))) return st;
+  ImgDesc& d = c->L.d[image];
+  const int si = side_index(d.W);
+  const int per_view = (d.H + rows_per_item(d.W) - 1) / rows_per_item(d.W);
+  size_t P = d.P, ivs = d.P, ovs = d.P / 2;
+  int Hh = d.H, one = 1, clamp = 0, p = d.p;
+  const float* src = y;
+  if (d.boundary) {   // M_S y_j
+    CU(cudaMemcpyAsync(d.Ad, y, sizeof(float) * P * p, cudaMemcpyDeviceToDevice, c->s));
+    float* x = d.Ad;
+    const float* wnull = nullptr;
+    const float* gg = d.g;
+    void* a[] = {(void*)&x, (void*)&P, (void*)&p, (void*)&wnull, (void*)&gg};
+    if ((st = launch((const void*)&k_apply_mask, grid_for(P * p), 256, 0, c->s, a))) return st;
+    src = d.Ad;
+  }
+  float2* sp1 = reinterpret_cast<float2*>(d.spec) + P / 2;
+  void* a2[] = {(void*)&src, (void*)&ivs, (void*)&sp1, (void*)&ovs, (void*)&Hh, (void*)&p, (void*)&clamp};
+  if ((st = launch(g_reg.row[ROP_R2C][0][si], per_view * p, kRowBlock, g_reg.row_smem[si], c->s, a2))) return st;
+  if ((st = col_pass(c, COL_PTO1, JOB_AT_RAW * c->n, image))) return st;
+  const float2* sp0 = reinterpret_cast<const float2*>(d.spec);
+  float sc = 1.0f;
+  void* a3[] = {(void*)&sp0, (void*)&ovs, (void*)&out, (void*)&ivs, (void*)&Hh, (void*)&one, (void*)&sc};
+  if ((st = launch(g_reg.row[ROP_C2R][0][si], per_view, kRowBlock, g_reg.row_smem[si], c->s, a3))) return st;
+  if (d.boundary) {   // M_R (...)
+    const float* w = d.w;
+    const float* gnull = nullptr;
+    void* a[] = {(void*)&out, (void*)&P, (void*)&one, (void*)&w, (void*)&gnull};
+    if ((st = launch((const void*)&k_apply_mask, grid_for(P), 256, 0, c->s, a))) return st;
+  }
+  c->mode = 0;
+  return leave(c);
+}
+
+sgp_status sgp_destroy(sgp_ctx* c) {
+  if (!c) return SGP_OK;
+  if (c->s) cudaStreamSynchronize(c->s);
+  if (c->g_sgp) cudaGraphExecDestroy(c->g_sgp);
+  if (c->g_rl) cudaGraphExecDestroy(c->g_rl);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  for (auto& e : c->ev_poll)
+    if (e) cudaEventDestroy(e);
+  if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+  if (c->s) cudaStreamDestroy(c->s);
+  delete c;
+  return SGP_OK;
+}
+
+}  // extern "C"
