@@ -21,7 +21,6 @@
 
 namespace sgp {
 
-enum ColMode { COL_KHAT = 0, COL_1TOP = 1, COL_1TOP_CONJ = 2, COL_PTO1 = 3 };
 
 template <int H> struct ColGeo {
   using P = Plan<H>;

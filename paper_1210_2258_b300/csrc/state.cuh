@@ -29,6 +29,8 @@ enum Slot {
 };
 constexpr int kArmExtra = 27;
 
+enum ColMode { COL_KHAT = 0, COL_1TOP = 1, COL_1TOP_CONJ = 2, COL_PTO1 = 3 };
+
 enum StopKind { STOP_FIXED = 0, STOP_CONVERGENCE = 1, STOP_DISCREPANCY = 2, STOP_MIN_ERROR = 3 };
 
 // Controller state of one problem (in the workspace; read by every hot kernel).
@@ -50,6 +52,7 @@ struct CtrlState {
   int proj_pass;    // flux projection search pass
   double J;         // J_0 at the current iterate
   double J_pred;    // J_0 at the accepted trial point
+  double J_prev;    // RL: J_0 at the previous iterate
   double alpha, alpha_prev, tau, lambda, gTd, dJ, mu, rho_prev, rho;
   double L1, L2;
   double hist[kMaxHist];
