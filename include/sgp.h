@@ -43,6 +43,12 @@
 extern "C" {
 #endif
 
+#if defined(__GNUC__)
+#define SGP_API __attribute__((visibility("default")))
+#else
+#define SGP_API
+#endif
+
 typedef struct sgp_ctx sgp_ctx;
 
 typedef enum {
@@ -119,10 +125,10 @@ typedef struct {
 } sgp_info;
 
 /* Fill *out with the parameter values of Sect. 3.2. */
-void sgp_params_default(sgp_params* out);
+SGP_API void sgp_params_default(sgp_params* out);
 
 /* Workspace bytes needed for n problems of the given shapes (params may be NULL = defaults). */
-size_t sgp_workspace_bytes(int n, const sgp_shape* shapes, const sgp_params* params);
+SGP_API size_t sgp_workspace_bytes(int n, const sgp_shape* shapes, const sgp_params* params);
 
 /* Create a context for n problems that advance together (n = 1 for a single problem).
  * For each problem: validate the shape, normalise each PSF to unit volume over the (extended)
@@ -130,66 +136,76 @@ size_t sgp_workspace_bytes(int n, const sgp_shape* shapes, const sgp_params* par
  * boundary problems compute alpha_j = K_j (x) M_S, R = {alpha_j >= sigma_R}, M_R / alpha
  * (Eq. Rdef; reading: alpha_j without the garbled factor g).
  * Errors: SGP_ERR_ARG, SGP_ERR_SIZE_UNSUPPORTED, SGP_ERR_PSF, SGP_ERR_WORKSPACE, SGP_ERR_CUDA. */
-sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const sgp_inputs* inputs,
+SGP_API sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const sgp_inputs* inputs,
                             const sgp_params* params, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Single-problem form of sgp_create_batch. b: device p x H x W or NULL; b_const: host array of p
  * constant backgrounds (used when b is NULL); mask: device H x W or NULL. */
-sgp_status sgp_create(sgp_ctx** out, const sgp_shape* shape, const float* psfs, const float* b,
+SGP_API sgp_status sgp_create(sgp_ctx** out, const sgp_shape* shape, const float* psfs, const float* b,
                       const float* b_const, const uint8_t* mask, const sgp_params* params,
                       void* workspace, size_t workspace_bytes, void* stream);
 
 /* Detected images g (device, p x H x W, counts >= 0) of problem `image`; pixels outside S are
  * ignored.  Sets the constant starting point of Sect. 3.1 unless sgp_set_start is called later.
  * Errors: SGP_ERR_NONFINITE for negative or non-finite data, SGP_ERR_ARG. */
-sgp_status sgp_set_data(sgp_ctx* ctx, int image, const float* g);
+SGP_API sgp_status sgp_set_data(sgp_ctx* ctx, int image, const float* g);
 
 /* Starting point (Sect. 3.1): SGP_START_ZERO, SGP_START_DATA (g_1), SGP_START_CONSTANT
  * (mean over views of sum_S (g - b) / |S|, on R), SGP_START_USER (device H x W f0, clipped at 0
  * and restricted to R).  Resets the iteration count. */
-sgp_status sgp_set_start(sgp_ctx* ctx, int image, int mode, const float* f0);
+SGP_API sgp_status sgp_set_start(sgp_ctx* ctx, int image, int mode, const float* f0);
 
 /* Reference object for the minimum-reconstruction-error stop (Sect. 3.3); device H x W, must stay
  * valid while solves run; NULL clears it. */
-sgp_status sgp_set_truth(sgp_ctx* ctx, int image, const float* f_true);
+SGP_API sgp_status sgp_set_truth(sgp_ctx* ctx, int image, const float* f_true);
 
 /* n Richardson-Lucy iterations of every problem (Eq. RL, multipleRL, boundaryRL).  Asynchronous. */
-sgp_status rl_iterate(sgp_ctx* ctx, int n);
+SGP_API sgp_status rl_iterate(sgp_ctx* ctx, int n);
 
 /* n SGP iterations (Algorithm 1) of every problem.  Asynchronous. */
-sgp_status sgp_iterate(sgp_ctx* ctx, int n);
+SGP_API sgp_status sgp_iterate(sgp_ctx* ctx, int n);
 
 /* Iterate SGP (resp. RL) on every problem until its stop rule fires or max_iter further
  * iterations; iters (n ints, may be NULL) receives each problem's iteration count.
  * Returns SGP_ERR_TIMEOUT if some problem reached max_iter before a non-FIXED rule fired, or the
  * first device-side error status. */
-sgp_status sgp_solve_until(sgp_ctx* ctx, const sgp_stop_rule* rule, int* iters);
-sgp_status rl_solve_until(sgp_ctx* ctx, const sgp_stop_rule* rule, int* iters);
+SGP_API sgp_status sgp_solve_until(sgp_ctx* ctx, const sgp_stop_rule* rule, int* iters);
+SGP_API sgp_status rl_solve_until(sgp_ctx* ctx, const sgp_stop_rule* rule, int* iters);
 
 /* J_0 (FP64) at the current iterate of problem `image` (Eq. KL / multipleKL). */
-sgp_status kl_value(sgp_ctx* ctx, int image, double* out);
+SGP_API sgp_status kl_value(sgp_ctx* ctx, int image, double* out);
 
 /* Copy the current iterate (the returned one after a minimum-error stop) to dst (device H x W). */
-sgp_status sgp_get_f(sgp_ctx* ctx, int image, float* dst);
+SGP_API sgp_status sgp_get_f(sgp_ctx* ctx, int image, float* dst);
 
 /* Per-iteration records, 8 doubles each: k, J_0, discrepancy, alpha, lambda, backtracks,
  * branch (0 alpha_0, 1 BB1, 2 windowed BB2), grad'd.  out: host, cap records. */
-sgp_status sgp_get_trace(sgp_ctx* ctx, int image, double* out, int cap, int* count);
+SGP_API sgp_status sgp_get_trace(sgp_ctx* ctx, int image, double* out, int cap, int* count);
 
-sgp_status sgp_get_info(sgp_ctx* ctx, int image, sgp_info* out);
+SGP_API sgp_status sgp_get_info(sgp_ctx* ctx, int image, sgp_info* out);
 
 /* Operators of problem `image` (Eq. projection / backprojection): out_j = A_j f for every view
  * (out: device p x H x W); out = sum_j A_j^T y_j (y: device p x H x W, out: device H x W).
  * They use the problem's iteration buffers as scratch: the next iterate call re-initialises the
  * iteration from the current iterate.  Asynchronous. */
-sgp_status sgp_apply_A(sgp_ctx* ctx, int image, const float* f, float* out);
-sgp_status sgp_apply_AT(sgp_ctx* ctx, int image, const float* y, float* out);
+SGP_API sgp_status sgp_apply_A(sgp_ctx* ctx, int image, const float* f, float* out);
+SGP_API sgp_status sgp_apply_AT(sgp_ctx* ctx, int image, const float* y, float* out);
+
+/* Measurement aid: run `iters` SGP iterations launching each pass separately, bracketed by CUDA
+ * events on the library's stream, and return the mean duration in ms of the 10 passes of an
+ * iteration in ms_out[0..9]: K1 update+ratio, column A^T, K3 gradient+BB, step-length controller,
+ * K4 projection, column A, K6 A d + Armijo, line-search controller, extra Armijo, extra controller.
+ * The iterations advance the state; the next solve restarts from the current iterate. */
+SGP_API sgp_status sgp_time_passes(sgp_ctx* ctx, int iters, double* ms_out, int n_out);
+
+/* Number of kernels this context has enqueued so far (graph launches count their nodes). */
+SGP_API long long sgp_launch_count(sgp_ctx* ctx);
 
 /* Release the context (not the workspace). */
-sgp_status sgp_destroy(sgp_ctx* ctx);
+SGP_API sgp_status sgp_destroy(sgp_ctx* ctx);
 
 /* Message of the last error on the calling thread ("" if none). */
-const char* sgp_last_error(void);
+SGP_API const char* sgp_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -32,16 +32,17 @@ def nvcc() -> str:
     return p
 
 
-def _headers_mtime() -> float:
-    hs = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
-        glob.glob(os.path.join(HERE, "..", "include", "*.h"))
+def _headers_mtime(unit: str) -> float:
+    hs = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
+    if unit == "runtime.cu":
+        hs += glob.glob(os.path.join(HERE, "..", "include", "*.h"))
     return max(os.path.getmtime(h) for h in hs)
 
 
 def _compile(unit: str, force: bool) -> str:
     src = os.path.join(CSRC, unit)
     obj = os.path.join(OBJDIR, unit.replace(".cu", ".o"))
-    if not force and os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _headers_mtime()):
+    if not force and os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _headers_mtime(unit)):
         return obj
     cmd = [nvcc()] + ARCH + FLAGS + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)

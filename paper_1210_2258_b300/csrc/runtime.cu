@@ -186,15 +186,19 @@ struct sgp_ctx {
   int mode = 0;                    // 0 not prepared, 1 SGP, 2 RL
   cudaGraphExec_t g_sgp = nullptr, g_rl = nullptr;
   int graph_units = 8;
+  long long launches = 0;          // kernels enqueued (graph nodes counted per graph launch)
   CtrlState* h_ctrl = nullptr;     // pinned mirror of the controller array (2 slots for polling)
 };
 
 namespace {
 
 // ---- launch helpers -----------------------------------------------------------------------------
+long long* g_launch_counter = nullptr;   // set while a context is being driven
+
 sgp_status launch(const void* fn, int grid, int block, size_t smem, cudaStream_t s, void** args) {
   if (grid <= 0) return SGP_OK;
   CU(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s));
+  if (g_launch_counter) ++*g_launch_counter;
   return SGP_OK;
 }
 
@@ -237,6 +241,7 @@ sgp_status ctrl_pass(sgp_ctx* c, const void* fn) {
 enum JobKind { JOB_A = 0, JOB_AT = 1, JOB_CONJ = 2, JOB_A_RAW = 3, JOB_AT_RAW = 4 };
 
 sgp_status enter(sgp_ctx* c) {
+  g_launch_counter = &c->launches;
   CU(cudaSetDevice(c->device));
   CU(cudaEventRecord(c->ev_in, c->user));
   CU(cudaStreamWaitEvent(c->s, c->ev_in, 0));
@@ -291,9 +296,12 @@ sgp_status build_graph(sgp_ctx* c, bool sgp, cudaGraphExec_t* out) {
   if (*out) return SGP_OK;
   cudaGraph_t g = nullptr;
   CU(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+  long long* saved = g_launch_counter;
+  g_launch_counter = nullptr;
   sgp_status st = SGP_OK;
   for (int u = 0; u < c->graph_units && st == SGP_OK; ++u) st = sgp ? seq_sgp_unit(c) : seq_rl_unit(c);
   cudaError_t e = cudaStreamEndCapture(c->s, &g);
+  g_launch_counter = saved;
   if (st) { if (g) cudaGraphDestroy(g); return st; }
   if (e != cudaSuccess) return fail(SGP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   e = cudaGraphInstantiate(out, g, 0);
@@ -387,7 +395,10 @@ sgp_status run_fixed(sgp_ctx* c, bool sgp, int n_iter) {
   if ((st = build_graph(c, sgp, sgp ? &c->g_sgp : &c->g_rl))) return st;
   if ((st = arm(c, STOP_FIXED, n_iter, 0.0, 1.0))) return st;
   const int launches = (n_iter + c->graph_units - 1) / c->graph_units;
-  for (int l = 0; l < launches; ++l) CU(cudaGraphLaunch(sgp ? c->g_sgp : c->g_rl, c->s));
+  for (int l = 0; l < launches; ++l) {
+    CU(cudaGraphLaunch(sgp ? c->g_sgp : c->g_rl, c->s));
+    c->launches += c->graph_units * (sgp ? 10 : 5);
+  }
   if (sgp && (st = seq_sgp_finalize(c))) return st;
   return SGP_OK;
 }
@@ -407,12 +418,15 @@ sgp_status run_until(sgp_ctx* c, bool sgp, const sgp_stop_rule* rule, int* iters
   const int max_launches = rule->max_iter / c->graph_units + 2;
   CtrlState* slot[2] = {c->h_ctrl, c->h_ctrl + c->n};
   // keep one chunk in flight while the flags of the previous one are inspected
+  const int per_graph = c->graph_units * (sgp ? 10 : 5);
   CU(cudaGraphLaunch(g, c->s));
+  c->launches += per_graph;
   CU(cudaMemcpyAsync(slot[0], c->L.ctrl, sizeof(CtrlState) * c->n, cudaMemcpyDeviceToHost, c->s));
   CU(cudaEventRecord(c->ev_poll[0], c->s));
   int cur = 0;
   for (int l = 1; l < max_launches; ++l) {
     CU(cudaGraphLaunch(g, c->s));
+    c->launches += per_graph;
     CU(cudaMemcpyAsync(slot[cur ^ 1], c->L.ctrl, sizeof(CtrlState) * c->n, cudaMemcpyDeviceToHost, c->s));
     CU(cudaEventRecord(c->ev_poll[cur ^ 1], c->s));
     CU(cudaEventSynchronize(c->ev_poll[cur]));
@@ -706,6 +720,8 @@ sgp_status sgp_create(sgp_ctx** out, const sgp_shape* shape, const float* psfs, 
                       const float* b_const, const uint8_t* mask, const sgp_params* params,
                       void* workspace, size_t workspace_bytes, void* stream) {
   if (!shape) return fail(SGP_ERR_ARG, "shape is NULL");
+  sgp_status st0 = validate_shapes(1, shape);
+  if (st0) return st0;
   sgp_inputs in;
   memset(&in, 0, sizeof(in));
   in.psfs = psfs;
@@ -996,6 +1012,46 @@ sgp_status sgp_apply_AT(sgp_ctx* c, int image, const float* y, float* out) {
   c->mode = 0;
   return leave(c);
 }
+
+sgp_status sgp_time_passes(sgp_ctx* c, int iters, double* ms_out, int n_out) {
+  if (!c || !ms_out || n_out < 10 || iters <= 0) return fail(SGP_ERR_ARG, "need ctx, iters > 0 and 10 outputs");
+  sgp_status st = enter(c);
+  if (st) return st;
+  if (c->mode != 1 && (st = prepare(c, 1))) return st;
+  if ((st = arm(c, STOP_FIXED, 1 << 30, 0.0, 1.0))) return st;
+  std::vector<cudaEvent_t> ev(11);
+  for (auto& e : ev) CU(cudaEventCreate(&e));
+  std::vector<double> acc(10, 0.0);
+  const bool f = c->fp64;
+  for (int it = 0; it < iters && st == SGP_OK; ++it) {
+    int q = 0;
+    CU(cudaEventRecord(ev[q++], c->s));
+    auto step = [&](sgp_status s2) { if (!st) st = s2; cudaEventRecord(ev[q++], c->s); };
+    step(row_pass(c, ROP_SGP_UPDATE, true));
+    step(col_pass(c, COL_PTO1, JOB_AT * c->n));
+    step(row_pass(c, ROP_SGP_GRAD, false));
+    step(ctrl_pass(c, f ? (const void*)&k_ctrl_alpha<true> : (const void*)&k_ctrl_alpha<false>));
+    step(row_pass(c, ROP_SGP_Y, false));
+    step(col_pass(c, COL_1TOP, JOB_A * c->n));
+    step(row_pass(c, ROP_SGP_AD, true));
+    step(ctrl_pass(c, f ? (const void*)&k_ctrl_lambda<true> : (const void*)&k_ctrl_lambda<false>));
+    step(row_pass(c, ROP_SGP_ARMX, false));
+    step(ctrl_pass(c, f ? (const void*)&k_ctrl_lambda_extra<true> : (const void*)&k_ctrl_lambda_extra<false>));
+    CU(cudaEventSynchronize(ev[10]));
+    for (int k = 0; k < 10; ++k) {
+      float ms = 0.0f;
+      CU(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+      acc[k] += ms;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (st) return st;
+  for (int k = 0; k < 10; ++k) ms_out[k] = acc[k] / iters;
+  c->mode = 0;   // the timed iterations advanced the state; the next solve re-initialises
+  return leave(c);
+}
+
+long long sgp_launch_count(sgp_ctx* c) { return c ? c->launches : 0; }
 
 sgp_status sgp_destroy(sgp_ctx* c) {
   if (!c) return SGP_OK;

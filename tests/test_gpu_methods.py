@@ -1,0 +1,165 @@
+"""GPU parity of Richardson-Lucy and SGP against the FP64 oracle on the same seeded inputs.
+
+Tolerances (FP32 GPU vs FP64 oracle): after 200 iterations the KL value within 1e-5 relative and
+the reconstruction within 1e-3 relative l2; step-length and line-search decisions identical."""
+import numpy as np
+import pytest
+
+from oracle import sgp_oracle as O
+from paper_1210_2258_b300 import scenes
+from tests.gpu_util import dev, gpu_problem, host, oracle_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def stars256():
+    return scenes.stars_scene(seed=0, N=256)
+
+
+def test_rl_200_iterations_stars_256(gpu, stars256):
+    sc = stars256
+    orc = oracle_problem(sc)
+    ref = O.rl(orc, stop=O.StopRule("fixed", max_iter=200))
+    prob = gpu_problem(gpu, sc)
+    prob.rl_iterate(200)
+    f = host(prob.get_f())
+    info = prob.info()
+    assert info.k == 200
+    assert abs(info.J - ref.J) <= 1e-5 * ref.J, (info.J, ref.J)
+    assert rel_l2(f, ref.f) <= 1e-3, rel_l2(f, ref.f)
+    tr = prob.trace()
+    assert tr.shape[0] == 200
+    Jo = np.array([t["J"] for t in ref.trace])
+    assert np.max(np.abs(tr[:, 1] - Jo) / Jo) <= 1e-5
+
+
+def test_sgp_200_iterations_stars_256(gpu, stars256):
+    sc = stars256
+    orc = oracle_problem(sc)
+    ref = O.sgp(orc, stop=O.StopRule("fixed", max_iter=200))
+    prob = gpu_problem(gpu, sc)
+    prob.sgp_iterate(200)
+    f = host(prob.get_f())
+    info = prob.info()
+    assert info.k == 200
+    assert abs(info.L1 - ref.L1) <= 1e-4 * ref.L1 and abs(info.L2 - ref.L2) <= 1e-4 * ref.L2
+    assert abs(info.J - ref.J) <= 1e-5 * ref.J, (info.J, ref.J)
+    assert rel_l2(f, ref.f) <= 1e-3, rel_l2(f, ref.f)
+    tr = prob.trace()
+    bt = np.array([t["backtracks"] for t in ref.trace])
+    br = np.array([t["branch"] for t in ref.trace])
+    assert np.array_equal(tr[:, 5].astype(int), bt)
+    assert np.array_equal(tr[:, 6].astype(int), br)
+    al = np.array([t["alpha"] for t in ref.trace])
+    assert np.max(np.abs(tr[:, 3] - al) / al) <= 1e-2
+
+
+def test_multi_view_rl_and_sgp(gpu):
+    sc = scenes.cluster_multiview_scene(seed=1, N=128, p=3, n_sources=40)
+    orc = oracle_problem(sc)
+    ref_rl = O.rl(orc, stop=O.StopRule("fixed", max_iter=40))
+    prob = gpu_problem(gpu, sc)
+    prob.rl_iterate(40)
+    assert rel_l2(host(prob.get_f()), ref_rl.f) <= 1e-3
+    assert abs(prob.kl_value() - ref_rl.J) <= 1e-5 * ref_rl.J
+    ref = O.sgp(orc, stop=O.StopRule("fixed", max_iter=40))
+    prob2 = gpu_problem(gpu, sc)
+    prob2.sgp_iterate(40)
+    assert rel_l2(host(prob2.get_f()), ref.f) <= 1e-3
+    assert abs(prob2.kl_value() - ref.J) <= 1e-5 * ref.J
+
+
+def test_boundary_rl_and_sgp(gpu):
+    sc = scenes.boundary_scene(scenes.rng_for(5), 96, 2.0, 10.0)
+    orc = oracle_problem(sc)
+    ref_rl = O.rl(orc, stop=O.StopRule("fixed", max_iter=30))
+    prob = gpu_problem(gpu, sc)
+    prob.rl_iterate(30)
+    assert rel_l2(host(prob.get_f()), ref_rl.f) <= 1e-3
+    assert abs(prob.kl_value() - ref_rl.J) <= 1e-5 * ref_rl.J
+    ref = O.sgp(orc, stop=O.StopRule("fixed", max_iter=30))
+    prob2 = gpu_problem(gpu, sc)
+    prob2.sgp_iterate(30)
+    assert rel_l2(host(prob2.get_f()), ref.f) <= 1e-3
+    assert abs(prob2.kl_value() - ref.J) <= 1e-5 * ref.J
+    f = host(prob2.get_f())
+    assert np.all(f[orc.MR == 0] == 0) and np.all(f >= 0)
+
+
+def test_discrepancy_stop_matches_oracle(gpu):
+    sc = scenes.galaxy_scene(seed=0, N=128, n_stars=16)
+    orc = oracle_problem(sc)
+    ref = O.sgp(orc, stop=O.StopRule("discrepancy", max_iter=3000, eta=1.0))
+    prob = gpu_problem(gpu, sc)
+    it = prob.solve_until(gpu.STOP_DISCREPANCY, max_iter=3000, eta=1.0)[0]
+    assert it == ref.iters, (it, ref.iters)
+    info = prob.info()
+    assert info.D <= 1.0 and abs(info.J - ref.J) <= 1e-5 * ref.J
+    ref_rl = O.rl(orc, stop=O.StopRule("discrepancy", max_iter=3000, eta=1.0))
+    prob_rl = gpu_problem(gpu, sc)
+    it_rl = prob_rl.solve_until(gpu.STOP_DISCREPANCY, max_iter=3000, eta=1.0, method="rl")[0]
+    assert abs(it_rl - ref_rl.iters) <= 1 and it_rl > 4 * it
+
+
+def test_convergence_and_min_error_stops(gpu):
+    sc = scenes.stars_scene(seed=3, N=64, n_stars=12)
+    orc = oracle_problem(sc)
+    ref = O.sgp(orc, stop=O.StopRule("convergence", max_iter=2000, tol=1e-4))
+    prob = gpu_problem(gpu, sc)
+    it = prob.solve_until(gpu.STOP_CONVERGENCE, max_iter=2000, tol=1e-4)[0]
+    assert abs(it - ref.iters) <= 1, (it, ref.iters)
+    ft = np.asarray(sc.f_true, np.float32)
+    ref2 = O.sgp(orc, stop=O.StopRule("min_error", max_iter=2000, f_true=ft.astype(np.float64)))
+    prob2 = gpu_problem(gpu, sc)
+    prob2.set_truth(0, dev(ft))
+    it2 = prob2.solve_until(gpu.STOP_MIN_ERROR, max_iter=2000)[0]
+    assert it2 == ref2.iters
+    assert rel_l2(host(prob2.get_f()), ref2.f) <= 1e-3
+
+
+def test_plain_fp32_reductions_variant(gpu, stars256):
+    sc = stars256
+    orc = oracle_problem(sc)
+    ref = O.sgp(orc, stop=O.StopRule("fixed", max_iter=50))
+    prob = gpu_problem(gpu, sc, gpu.default_params(reduce_fp64=0))
+    prob.sgp_iterate(50)
+    assert rel_l2(host(prob.get_f()), ref.f) <= 1e-2
+    assert abs(prob.kl_value() - ref.J) <= 1e-3 * ref.J
+
+
+def test_batch_equals_individual_runs(gpu):
+    scs = [scenes.stars_scene(seed=s, N=64, n_stars=10) for s in range(3)]
+    batch = gpu.Problems([dev(np.asarray(s.psfs, np.float32)) for s in scs],
+                         [list(np.asarray(s.b, np.float32)) for s in scs])
+    for i, s in enumerate(scs):
+        batch.set_data(i, dev(np.asarray(s.g, np.float32)))
+    batch.sgp_iterate(25)
+    for i, s in enumerate(scs):
+        single = gpu_problem(gpu, s)
+        single.sgp_iterate(25)
+        assert np.array_equal(host(batch.get_f(i)), host(single.get_f()))
+
+
+def test_iterations_resume_consistently(gpu):
+    sc = scenes.stars_scene(seed=4, N=64, n_stars=10)
+    a = gpu_problem(gpu, sc)
+    a.sgp_iterate(30)
+    b = gpu_problem(gpu, sc)
+    b.sgp_iterate(10)
+    b.sgp_iterate(20)
+    assert np.array_equal(host(a.get_f()), host(b.get_f()))
+    assert a.info().k == b.info().k == 30
+
+
+def test_starting_points(gpu):
+    sc = scenes.stars_scene(seed=5, N=32, n_stars=5)
+    orc = oracle_problem(sc)
+    prob = gpu_problem(gpu, sc)
+    c = orc.initial("constant")
+    assert abs(prob.info().flux_c - c[0, 0]) <= 1e-6 * c[0, 0]
+    prob.set_start(0, gpu.START_DATA)
+    np.testing.assert_allclose(host(prob.get_f()), orc.initial("data"), rtol=1e-6)
+    user = scenes.rng_for(1).random((32, 32)).astype(np.float32) - 0.2
+    prob.set_start(0, gpu.START_USER, dev(user))
+    np.testing.assert_allclose(host(prob.get_f()), np.maximum(user, 0), rtol=1e-6)
