@@ -1,0 +1,309 @@
+#!/usr/bin/env python3
+"""Benchmark of the single-image SGP hot path at 2048 x 2048.
+
+Workload: a synthetic galaxy (5 Sersic profiles, peak 1e4) plus 500 log-uniform stars, blurred by
+the Airy PSF of a circular pupil of diameter N/8, background 50, Poisson noise (seeded).  One step
+is one SGP solve from the constant starting point to the discrepancy-principle stop (eta = 1),
+with FP64-accumulated reductions.  `value` is SGP iterations per second over the timed steps
+(inputs resident in HBM, L2 flushed before each step by writing a 512 MB buffer); `e2e` is the same
+metric through the public API with host buffers (pinned host -> device copies of PSF and data, a
+new context, the solve, and the device -> host copy of the result inside the timed region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (torchrun): every rank solves its own replica (different seed); `value` is the total of the
+iterations of all ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+METRIC = "2048² SGP iters/s & time-to-stop vs plain FP32 on same GPU; % HBM roofline"
+ROOT = os.path.dirname(os.path.abspath(__file__))
+FALLBACK_HBM_GBS = 6400.0
+# algorithmic bytes per launch of each pass of one SGP iteration, in units of one H x W float32
+# plane (single view): K1 reads f, grad, A f, A d, g and writes f, A f, the ratio spectrum; the
+# column passes read a spectrum and the PSF spectrum and write a spectrum; K3 reads the spectrum,
+# f, f_prev, grad_prev and writes grad; K4 reads f, grad and writes a spectrum; K6 reads the
+# spectrum, A f, g and writes A d.  Controllers move O(1) bytes.
+PASS_NAMES = ["update_ratio", "col_AT", "grad_bb", "ctrl_alpha", "proj_y", "col_A", "ad_armijo",
+              "ctrl_lambda", "armijo_extra", "ctrl_extra"]
+PASS_PLANES = [8, 3, 5, 0, 3, 3, 4, 0, 0, 0]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=2048)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        busy = [s for s in sm if s > 0.5 * smax] or sm
+        return {"sm_mhz": float(np.median(busy)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def make_scene(args, rank):
+    from paper_1210_2258_b300 import scenes
+    return scenes.galaxy_scene(seed=args.seed + rank, N=args.N)
+
+
+def cpu_baseline(sc, iters=2):
+    """The FP64 oracle as it stands, timed on this host on a bounded sample of the workload."""
+    from oracle import sgp_oracle as O
+    t0 = time.perf_counter()
+    prob = O.Problem(sc.psfs.astype(np.float32).astype(np.float64), sc.g.astype(np.float32).astype(np.float64),
+                     sc.b.astype(np.float64))
+    t1 = time.perf_counter()
+    res = O.sgp(prob, stop=O.StopRule("fixed", max_iter=iters))
+    t2 = time.perf_counter()
+    return {"value": res.iters / (t2 - t1), "unit": "iter/s", "cores": 1, "kind": "oracle",
+            "sample": f"{iters} SGP iterations (incl. the L1/L2 set-up RL step) of the {sc.g.shape[1]}x"
+                      f"{sc.g.shape[2]} workload, FP64 numpy oracle, single thread (pocketfft); problem "
+                      f"set-up {t1 - t0:.2f} s excluded"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    sc = make_scene(args, 0)
+    from oracle import sgp_oracle as O
+    prob = O.Problem(sc.psfs.astype(np.float32).astype(np.float64), sc.g.astype(np.float32).astype(np.float64),
+                     sc.b.astype(np.float64))
+    f = prob.initial()
+    # one step = one SGP iteration of the oracle (bounded sample of the workload)
+    for _ in range(args.warmup):
+        O.sgp(prob, f0=f, stop=O.StopRule("fixed", max_iter=1))
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(args.steps):
+        its += O.sgp(prob, f0=f, stop=O.StopRule("fixed", max_iter=1)).iters
+    dt = time.perf_counter() - t0
+    v = its / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"galaxy {args.N}x{args.N} SGP, one iteration per step",
+                                            "N": args.N},
+            "cpu_baseline": {"value": v, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                             "sample": "one SGP iteration (with the L1/L2 set-up RL step) per step"},
+            "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    from paper_1210_2258_b300 import sgp as lib
+    lib.load()
+    sc = make_scene(args, rank)
+    N = args.N
+    psf_h = torch.from_numpy(sc.psfs.astype(np.float32)).pin_memory()
+    g_h = torch.from_numpy(sc.g.astype(np.float32)).pin_memory()
+    psf_d, g_d = psf_h.cuda(), g_h.cuda()
+    prob = lib.Problems(psf_d, [float(sc.b[0])])
+    prob.set_data(0, g_d)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    max_iter = 20000
+
+    def solve(pr):
+        pr.set_start(0, lib.START_CONSTANT)
+        return pr.solve_until(lib.STOP_DISCREPANCY, max_iter=max_iter, eta=1.0)[0]
+
+    for _ in range(args.warmup):
+        solve(prob)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total_ms, total_it = 0.0, 0
+    l0 = prob.launch_count()
+    for _ in range(args.steps):
+        flush.zero_()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ev0.record()
+        total_it += solve(prob)
+        ev1.record()
+        torch.cuda.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+    launches = prob.launch_count() - l0
+    clocks = sampler.stop() if sampler else None
+    info = prob.info()
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        it = torch.tensor([total_it], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(it, op=torch.distributed.ReduceOp.SUM)
+        total_ms, total_it_all = float(t.item()), int(it.item())
+    else:
+        total_it_all = total_it
+    value = total_it_all / (total_ms / 1e3)
+
+    # per-pass durations (CUDA events on the library's stream) -> roofline of the dominant pass
+    passes = prob.time_passes(10)
+    B = N * N * 4
+    shares = [ms for ms in passes]
+    dom = int(np.argmax(shares))
+    peak, peak_kind = measured_peaks()
+    achieved = PASS_PLANES[dom] * B / (passes[dom] / 1e3) / 1e9
+    iter_ms = sum(passes)
+    roofline = {"bound": "hbm", "kernel": PASS_NAMES[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "algorithmic_bytes_per_launch": PASS_PLANES[dom] * B,
+                "iteration": {"modelled_bytes": sum(PASS_PLANES) * B, "ms_sum_of_passes": iter_ms,
+                              "achieved_gbs": sum(PASS_PLANES) * B / (iter_ms / 1e3) / 1e9},
+                "pass_ms": dict(zip(PASS_NAMES, passes))}
+
+    # plain-FP32 comparison line (same GPU, same workload)
+    plain = lib.Problems(psf_d, [float(sc.b[0])], params=lib.default_params(reduce_fp64=0))
+    plain.set_data(0, g_d)
+    solve(plain)
+    torch.cuda.synchronize()
+    flush.zero_()
+    torch.cuda.synchronize()
+    ev0.record()
+    it_plain = solve(plain)
+    ev1.record()
+    torch.cuda.synchronize()
+    plain_ms = ev0.elapsed_time(ev1)
+    plain_info = plain.info()
+    plain.close()
+
+    # end to end through the public API with host buffers
+    f_h = torch.empty((N, N), dtype=torch.float32).pin_memory()
+    e2e_ms, e2e_it = 0.0, 0
+    for s in range(args.steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pd = psf_h.cuda(non_blocking=True)
+        gd = g_h.cuda(non_blocking=True)
+        pr = lib.Problems(pd, [float(sc.b[0])])
+        pr.set_data(0, gd)
+        it = pr.solve_until(lib.STOP_DISCREPANCY, max_iter=max_iter, eta=1.0)[0]
+        f_h.copy_(pr.get_f(), non_blocking=True)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) * 1e3
+        pr.close()
+        if s > 0:
+            e2e_ms += dt
+            e2e_it += it
+    e2e = {"value": e2e_it / (e2e_ms / 1e3), "unit": "iter/s", "h2d_bytes_per_step": int(psf_h.numel() * 4 + g_h.numel() * 4),
+           "d2h_bytes_per_step": int(f_h.numel() * 4), "time_to_stop_ms": e2e_ms / args.steps}
+
+    if rank != 0:
+        return 0
+    cpu = None if args.no_cpu_baseline else cpu_baseline(sc)
+    line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"galaxy+stars {N}x{N}, Airy PSF (pupil N/8), b=50, Poisson, seed {args.seed}; "
+                                   "SGP from the constant start to the discrepancy stop eta=1, FP64 reductions",
+                       "N": N, "p": 1, "l2": "flushed (512 MB write) before each step",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "time_to_stop_ms": total_ms / args.steps, "iterations_per_solve": total_it / args.steps,
+            "final_kl": info.J, "final_discrepancy": info.D,
+            "plain_fp32": {"time_to_stop_ms": plain_ms, "iterations": it_plain, "final_kl": plain_info.J,
+                           "final_discrepancy": plain_info.D, "iters_per_s": it_plain / (plain_ms / 1e3)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
