@@ -11,7 +11,8 @@
 //   Armijo     J(f + lam d) - J(f) = sum lam Ad - g log(1 + lam Ad / u)
 //              = sum (u - g) q + g phi(q),  q = lam Ad / u         (no cancellation)
 //   scaling    D = w clip(f, L1, L2), w = 1/p (periodic) or M_R/alpha (boundary), Eq. (Dk),(Dkbound)
-//   gradient   grad = alpha_sum - sum_j A_j^T r_j on R (0 outside R), Eq. (KLgrad),(gradientboundary)
+//   gradient   grad = sum_j A_j^T (1 - r_j) on R (0 outside R), Eq. (KLgrad),(gradientboundary);
+//              the row passes transform r - 1, so no 1 - A^T r cancellation
 //   step       y = P_+(f - alpha D grad), d = y - f, Eq. (diry); flux mode y = max(0, x - mu D)
 #pragma once
 #include "fft.cuh"
@@ -67,6 +68,13 @@ __device__ __forceinline__ float armijo_term(float g, float u0, float dl) {
 }
 __device__ __forceinline__ float ratio_term(float g, float u0) {
   return (g > 0.0f && u0 > 0.0f) ? g / u0 : 0.0f;
+}
+// r - 1 on S (0 outside S): the row passes transform this instead of r, so that
+// sum_j A_j^T (r_j - 1) = -grad J_0 (Eq. gradientboundary with A_j^T 1 moved inside) is computed
+// without the cancellation of 1 - A^T r when A^T r -> 1
+__device__ __forceinline__ float ratio_m1(float g, float u0) {
+  if (g < 0.0f) return 0.0f;
+  return (g > 0.0f && u0 > 0.0f) ? (g - u0) / u0 : -1.0f;
 }
 
 // ------------------------------------------------------------------------------ reductions
@@ -379,7 +387,7 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_update_ratio(const ImgDesc* _
         const float u0x = u.x + b.x, u0y = u.y + b.y;
         acc[0].add(kl_term(g.x, u0x));
         acc[0].add(kl_term(g.y, u0y));
-        x(t + q * G::T) = make_float2(ratio_term(g.x, u0x), ratio_term(g.y, u0y));
+        x(t + q * G::T) = make_float2(ratio_m1(g.x, u0x), ratio_m1(g.y, u0y));
       }
     }
   }
@@ -420,12 +428,10 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_grad_bb(const ImgDesc* __rest
 #pragma unroll 4
       for (int q = 0; q < G::E; ++q) {
         const size_t i = off + t + q * G::T;
-        const float2 v = x(t + q * G::T), w = w_pair(d, i);
-        const float a1x = d.w ? (w.x > 0.0f ? 1.0f / w.x : 0.0f) : d.a1_scalar;
-        const float a1y = d.w ? (w.y > 0.0f ? 1.0f / w.y : 0.0f) : d.a1_scalar;
+        const float2 v = x(t + q * G::T), w = w_pair(d, i);   // v = sum_j A_j^T (r_j - 1)
         float2 gr;
-        gr.x = w.x > 0.0f ? a1x - v.x : 0.0f;
-        gr.y = w.y > 0.0f ? a1y - v.y : 0.0f;
+        gr.x = w.x > 0.0f ? -v.x : 0.0f;
+        gr.y = w.y > 0.0f ? -v.y : 0.0f;
         st2(gn, i, gr);
         if (bb) {
           const float2 fc = ld2(f, i), fo = ld2(fp, i), go = ld2(gp, i);
@@ -446,7 +452,7 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_grad_bb(const ImgDesc* __rest
   }
 }
 
-// SGP K4: y = P(f - alpha D grad) (Alg. 1 step 2) -> R2C into plane 0, with the grad'd partials.
+// SGP K4: y = P(f - alpha D grad) (Alg. 1 step 2), d = y - f -> R2C into plane 0, grad'd partials.
 template <int W, bool FP64>
 __global__ void __launch_bounds__(kRowBlock) k_sgp_y(const ImgDesc* __restrict__ imgs,
                                                     const int2* __restrict__ items, int n_items) {
@@ -476,9 +482,10 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_y(const ImgDesc* __restrict__
         const float2 fv = ld2(f, i), gv = ld2(gr, i), w = w_pair(d, i);
         const float yx = proj_step(fv.x, gv.x, w.x, alpha, mu, L1, L2);
         const float yy = proj_step(fv.y, gv.y, w.y, alpha, mu, L1, L2);
-        acc[0].add(gv.x * (yx - fv.x));
-        acc[0].add(gv.y * (yy - fv.y));
-        x(t + q * G::T) = make_float2(yx, yy);
+        const float dx = yx - fv.x, dy = yy - fv.y;
+        acc[0].add(gv.x * dx);
+        acc[0].add(gv.y * dy);
+        x(t + q * G::T) = make_float2(dx, dy);   // A d is transformed directly (no A y - A f cancellation)
       }
     }
     row_real_to_spec<W>(x, spec_plane(d, 0) + off, t, act);
@@ -486,8 +493,8 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_y(const ImgDesc* __restrict__
   }
 }
 
-// SGP K6: per view, C2R of plane j+1 (= A_j y) -> A_j d = A_j y - A_j f (linearity, no FFT per
-// backtrack) and the Armijo partial sums Delta J(theta^i), i = 0..3 (Alg. 1 step 5).
+// SGP K6: per view, C2R of plane j+1 (= A_j d) -> stored A_j d (A(f + lam d) = A f + lam A d: no FFT
+// per backtrack) and the Armijo partial sums Delta J(theta^i), i = 0..3 (Alg. 1 step 5).
 template <int W, bool FP64>
 __global__ void __launch_bounds__(kRowBlock) k_sgp_ad_armijo(const ImgDesc* __restrict__ imgs,
                                                             const int2* __restrict__ items, int n_items) {
@@ -516,8 +523,7 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_ad_armijo(const ImgDesc* __re
 #pragma unroll 2
     for (int q = 0; q < G::E; ++q) {
       const size_t i = off + t + q * G::T;
-      const float2 ay = x(t + q * G::T), u = ld2(uj, i), g = ld2(gj, i), b = b_pair(d, j, i);
-      const float2 ad = make_float2(ay.x - u.x, ay.y - u.y);
+      const float2 ad = x(t + q * G::T), u = ld2(uj, i), g = ld2(gj, i), b = b_pair(d, j, i);
       st2(adj, i, ad);
       const float u0x = u.x + b.x, u0y = u.y + b.y;
 #pragma unroll
@@ -602,10 +608,10 @@ __global__ void __launch_bounds__(kRowBlock) k_rl_update(const ImgDesc* __restri
       for (int q = 0; q < G::E; ++q) {
         const size_t i = off + t + q * G::T;
         float2 f = ld2(fo, i);
-        if (hv) {
+        if (hv) {   // w f sum_j A_j^T r_j = f (1 + w v) on R, v = sum_j A_j^T (r_j - 1)
           const float2 v = x(t + q * G::T), w = w_pair(d, i);
-          f.x = w.x * f.x * v.x;
-          f.y = w.y * f.y * v.y;
+          f.x = w.x > 0.0f ? fmaf(f.x * w.x, v.x, f.x) : 0.0f;
+          f.y = w.y > 0.0f ? fmaf(f.y * w.y, v.y, f.y) : 0.0f;
           st2(fn, i, f);
         }
         if (rho) {
@@ -652,7 +658,7 @@ __global__ void __launch_bounds__(kRowBlock) k_rl_ratio(const ImgDesc* __restric
       const float u0x = u.x + b.x, u0y = u.y + b.y;
       acc[0].add(kl_term(g.x, u0x));
       acc[0].add(kl_term(g.y, u0y));
-      x(t + q * G::T) = make_float2(ratio_term(g.x, u0x), ratio_term(g.y, u0y));
+      x(t + q * G::T) = make_float2(ratio_m1(g.x, u0x), ratio_m1(g.y, u0y));
     }
   }
   row_real_to_spec<W>(x, sp, t, act);
@@ -682,7 +688,8 @@ __global__ void __launch_bounds__(kRowBlock) k_rl_step_minmax(const ImgDesc* __r
       for (int q = 0; q < G::E; ++q) {
         const size_t i = off + t + q * G::T;
         const float2 v = x(t + q * G::T), fv = ld2(f, i), w = w_pair(d, i);
-        const float y0 = w.x * fv.x * v.x, y1 = w.y * fv.y * v.y;
+        const float y0 = w.x > 0.0f ? fmaf(fv.x * w.x, v.x, fv.x) : 0.0f;
+        const float y1 = w.y > 0.0f ? fmaf(fv.y * w.y, v.y, fv.y) : 0.0f;
         if (y0 > 0.0f) mn = fminf(mn, y0);
         if (y1 > 0.0f) mn = fminf(mn, y1);
         mx = fmaxf(mx, fmaxf(y0, y1));
