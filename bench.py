@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--N", type=int, default=2048)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", type=int, default=0,
+                    help="profiling driver: set up the workload, run this many SGP iterations, exit")
     return ap.parse_args()
 
 
@@ -175,8 +177,25 @@ def run_reference(args):
     return 0
 
 
+def run_profile(args):
+    """Minimal launch sequence for ncu: set-up plus a few SGP iterations of the same workload."""
+    import torch
+    from paper_1210_2258_b300 import sgp as lib
+    sc = make_scene(args, 0)
+    psf = torch.from_numpy(sc.psfs.astype(np.float32)).cuda()
+    g = torch.from_numpy(sc.g.astype(np.float32)).cuda()
+    prob = lib.Problems(psf, [float(sc.b[0])])
+    prob.set_data(0, g)
+    prob.sgp_iterate(args.profile)
+    torch.cuda.synchronize()
+    print(f"profile run: {args.profile} SGP iterations, J = {prob.kl_value():.6g}")
+    return 0
+
+
 def run_ours(args):
     import torch
+    if args.profile:
+        return run_profile(args)
     ws, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
     from paper_1210_2258_b300 import sgp as lib
