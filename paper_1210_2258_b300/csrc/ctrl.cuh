@@ -267,61 +267,69 @@ __global__ void k_prepare_data(const float* __restrict__ g, const uint8_t* __res
   }
 }
 
-// per plane: sum, max, min, count of non-finite samples (one block per plane)
-__global__ void __launch_bounds__(256) k_plane_stats(const float* __restrict__ x, size_t P, double* __restrict__ out) {
-  const float* a = x + size_t(blockIdx.x) * P;
-  double s = 0.0;
-  float mx = -INFINITY, mn = INFINITY;
-  int nf = 0;
-  for (size_t i = threadIdx.x; i < P; i += blockDim.x) {
+// Grid-wide statistics in two stages (blocks x planes partials, then one block per plane).
+// Stage 1, mode 0 (PSF): per plane sum, max, min, count of non-finite samples.
+// Stage 1, mode 1 (data): per view sum over S of g (g >= 0 marks S), sum over S of b, |S|.
+__global__ void __launch_bounds__(256) k_stats_partial(const float* __restrict__ x, const float* __restrict__ b,
+                                                      const float* __restrict__ bconst, size_t P, int mode,
+                                                      double* __restrict__ part) {
+  const int plane = blockIdx.y;
+  const float* a = x + size_t(plane) * P;
+  const float* bj = b ? b + size_t(plane) * P : nullptr;
+  const float bc = bconst ? bconst[plane] : 0.0f;
+  double s0 = 0.0, s1 = mode ? 0.0 : -INFINITY, s2 = mode ? 0.0 : INFINITY, s3 = 0.0;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < P; i += size_t(gridDim.x) * blockDim.x) {
     const float v = a[i];
-    if (!isfinite(v)) { ++nf; continue; }
-    s += v; mx = fmaxf(mx, v); mn = fminf(mn, v);
+    if (mode == 0) {
+      if (!isfinite(v)) { s3 += 1.0; continue; }
+      s0 += v; s1 = fmax(s1, double(v)); s2 = fmin(s2, double(v));
+    } else {
+      if (v < 0.0f) continue;
+      s0 += v; s1 += bj ? bj[i] : bc; s2 += 1.0;
+    }
   }
-  __shared__ double rs[256];
-  __shared__ float rmx[256], rmn[256];
-  __shared__ int rnf[256];
-  rs[threadIdx.x] = s; rmx[threadIdx.x] = mx; rmn[threadIdx.x] = mn; rnf[threadIdx.x] = nf;
+  __shared__ double r[4][256];
+  r[0][threadIdx.x] = s0; r[1][threadIdx.x] = s1; r[2][threadIdx.x] = s2; r[3][threadIdx.x] = s3;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if (threadIdx.x < o) {
-      rs[threadIdx.x] += rs[threadIdx.x + o];
-      rmx[threadIdx.x] = fmaxf(rmx[threadIdx.x], rmx[threadIdx.x + o]);
-      rmn[threadIdx.x] = fminf(rmn[threadIdx.x], rmn[threadIdx.x + o]);
-      rnf[threadIdx.x] += rnf[threadIdx.x + o];
+      r[0][threadIdx.x] += r[0][threadIdx.x + o];
+      r[3][threadIdx.x] += r[3][threadIdx.x + o];
+      if (mode == 0) {
+        r[1][threadIdx.x] = fmax(r[1][threadIdx.x], r[1][threadIdx.x + o]);
+        r[2][threadIdx.x] = fmin(r[2][threadIdx.x], r[2][threadIdx.x + o]);
+      } else {
+        r[1][threadIdx.x] += r[1][threadIdx.x + o];
+        r[2][threadIdx.x] += r[2][threadIdx.x + o];
+      }
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    out[4 * blockIdx.x + 0] = rs[0];
-    out[4 * blockIdx.x + 1] = rmx[0];
-    out[4 * blockIdx.x + 2] = rmn[0];
-    out[4 * blockIdx.x + 3] = rnf[0];
-  }
+  if (threadIdx.x < 4) part[(size_t(plane) * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = r[threadIdx.x][0];
 }
 
-// sums over S of g_j (g >= 0 marks S) and of b_j, and |S|: out[3*j + {0,1,2}] (one block per view)
-__global__ void __launch_bounds__(256) k_data_sums(const float* __restrict__ g, const float* __restrict__ b,
-                                                  const float* __restrict__ bconst, size_t P, double* __restrict__ out) {
-  const int j = blockIdx.x;
-  const float* gj = g + size_t(j) * P;
-  const float* bj = b ? b + size_t(j) * P : nullptr;
-  double sg = 0.0, sb = 0.0, ns = 0.0;
-  for (size_t i = threadIdx.x; i < P; i += blockDim.x) {
-    const float v = gj[i];
-    if (v < 0.0f) continue;
-    sg += v; sb += bj ? bj[i] : bconst[j]; ns += 1.0;
+// Stage 2: one block per plane combines the nb partials of stage 1 into out[4 * plane + 0..3].
+__global__ void __launch_bounds__(256) k_stats_final(const double* __restrict__ part, int nb, int mode,
+                                                    double* __restrict__ out) {
+  const int plane = blockIdx.x;
+  __shared__ double r[4][256];
+  double s0 = 0.0, s1 = mode ? 0.0 : -INFINITY, s2 = mode ? 0.0 : INFINITY, s3 = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    const double* q = part + (size_t(plane) * nb + i) * 4;
+    s0 += q[0]; s3 += q[3];
+    if (mode == 0) { s1 = fmax(s1, q[1]); s2 = fmin(s2, q[2]); }
+    else { s1 += q[1]; s2 += q[2]; }
   }
-  __shared__ double r[3][256];
-  r[0][threadIdx.x] = sg; r[1][threadIdx.x] = sb; r[2][threadIdx.x] = ns;
+  r[0][threadIdx.x] = s0; r[1][threadIdx.x] = s1; r[2][threadIdx.x] = s2; r[3][threadIdx.x] = s3;
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o)
-      for (int q = 0; q < 3; ++q) r[q][threadIdx.x] += r[q][threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int t = 1; t < int(blockDim.x); ++t) {   // fixed order: deterministic
+      r[0][0] += r[0][t]; r[3][0] += r[3][t];
+      if (mode == 0) { r[1][0] = fmax(r[1][0], r[1][t]); r[2][0] = fmin(r[2][0], r[2][t]); }
+      else { r[1][0] += r[1][t]; r[2][0] += r[2][t]; }
+    }
+    for (int k = 0; k < 4; ++k) out[4 * plane + k] = r[k][0];
   }
-  if (threadIdx.x == 0)
-    for (int q = 0; q < 3; ++q) out[3 * j + q] = r[q][0];
 }
 
 // f = value on R (w > 0), 0 elsewhere; or f = max(src, 0) restricted to R when src != nullptr

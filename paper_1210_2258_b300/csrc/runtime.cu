@@ -261,6 +261,17 @@ sgp_status read_ctrl(sgp_ctx* c, CtrlState* dst) {
 
 int grid_for(size_t n) { return int(std::min<size_t>((n + 255) / 256, 148 * 16)); }
 
+// plane statistics (see k_stats_partial): out[4 * plane + 0..3]; `scratch` needs 4 * nb * planes doubles
+sgp_status plane_stats(cudaStream_t s, const float* x, const float* b, const float* bconst, size_t P, int planes,
+                       int mode, double* scratch, double* out) {
+  int nb = int(std::min<size_t>(std::max<size_t>(P / 4096, 1), 296));
+  void* a1[] = {(void*)&x, (void*)&b, (void*)&bconst, (void*)&P, (void*)&mode, (void*)&scratch};
+  CU(cudaLaunchKernel((const void*)&k_stats_partial, dim3(nb, planes), dim3(256), a1, 0, s));
+  void* a2[] = {(void*)&scratch, (void*)&nb, (void*)&mode, (void*)&out};
+  CU(cudaLaunchKernel((const void*)&k_stats_final, dim3(planes), dim3(256), a2, 0, s));
+  return SGP_OK;
+}
+
 // ---- iteration sequences --------------------------------------------------------------------------
 sgp_status seq_rl_unit(sgp_ctx* c) {
   sgp_status st;
@@ -625,8 +636,8 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
   std::vector<double> stats(4 * kMaxViews);
   for (int i = 0; i < n && st == SGP_OK; ++i) {
     ImgDesc& d = L.d[i];
-    void* a[] = {(void*)&in[i].psfs, (void*)&d.P, (void*)&L.scratch[i]};
-    if ((st = launch((const void*)&k_plane_stats, d.p, 256, 0, c->s, a))) break;
+    if ((st = plane_stats(c->s, in[i].psfs, nullptr, nullptr, d.P, d.p, 0, reinterpret_cast<double*>(d.Ad),
+                          L.scratch[i]))) break;
     if (cudaMemcpyAsync(stats.data(), L.scratch[i], sizeof(double) * 4 * d.p, cudaMemcpyDeviceToHost, c->s) != cudaSuccess ||
         cudaStreamSynchronize(c->s) != cudaSuccess) { st = fail(SGP_ERR_CUDA, "PSF statistics failed"); break; }
     for (int j = 0; j < d.p; ++j) {
@@ -751,21 +762,19 @@ sgp_status sgp_set_data(sgp_ctx* c, int image, const float* g) {
     if ((st = launch((const void*)&k_prepare_data, grid_for(P * p), 256, 0, c->s, a))) return st;
   }
   {
-    const float* gg = d.g;
-    const float* bb = d.b;
-    float* bc = reinterpret_cast<float*>(c->L.scratch[image] + 32);   // p floats of constants
+    float* bc = reinterpret_cast<float*>(c->L.scratch[image] + 56);   // p floats of constants
     CU(cudaMemcpyAsync(bc, d.bs, sizeof(float) * kMaxViews, cudaMemcpyHostToDevice, c->s));
-    const float* bcc = bc;
-    double* out = c->L.scratch[image];
-    void* a[] = {(void*)&gg, (void*)&bb, (void*)&bcc, (void*)&P, (void*)&out};
-    if ((st = launch((const void*)&k_data_sums, p, 256, 0, c->s, a))) return st;
+    if ((st = plane_stats(c->s, d.g, d.b, bc, P, p, 1, reinterpret_cast<double*>(d.Ad), c->L.scratch[image])))
+      return st;
   }
   int hbad = 0;
-  double sums[3 * kMaxViews];
+  double st4[4 * kMaxViews], sums[3 * kMaxViews];
   CU(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->s));
-  CU(cudaMemcpyAsync(sums, c->L.scratch[image], sizeof(double) * 3 * p, cudaMemcpyDeviceToHost, c->s));
+  CU(cudaMemcpyAsync(st4, c->L.scratch[image], sizeof(double) * 4 * p, cudaMemcpyDeviceToHost, c->s));
   CU(cudaStreamSynchronize(c->s));
   if (hbad) return fail(SGP_ERR_NONFINITE, "data contain negative or non-finite values");
+  for (int j = 0; j < p; ++j)
+    for (int q = 0; q < 3; ++q) sums[3 * j + q] = st4[4 * j + q];
   // constant start of Sect. 3.1: mean over views of (sum_S g - sum_S b) / |S|
   double cm = 0.0, gm = 0.0;
   const double nS = sums[2];
