@@ -201,6 +201,25 @@ SGP_API sgp_status sgp_time_passes(sgp_ctx* ctx, int iters, double* ms_out, int 
 /* Number of kernels this context has enqueued so far (graph launches count their nodes). */
 SGP_API long long sgp_launch_count(sgp_ctx* ctx);
 
+/* Convolution without any device allocation, for callers that cannot allocate device memory --
+ * for example code running where cudaMalloc is unavailable or forbidden (inside a captured region
+ * of another framework, under a strict memory budget owned by someone else, or in a process that
+ * must not grow its device footprint after start-up).  It computes the same result as sgp_apply_A
+ * (transpose = 0: out = K * f) or sgp_apply_AT (transpose = 1: out = K (x) f) of a periodic
+ * single-view problem with PSF `psf` (normalised here to unit sum; psf_origin as in sgp_shape),
+ * without a context or workspace.  The paper has no counterpart of this entry point.
+ *   - psf, f, out: device H x W float32 arrays owned by the caller.
+ *   - Limit: H * W <= 262144 (e.g. 512 x 512); larger sizes return SGP_ERR_SIZE_UNSUPPORTED.
+ *   - Scratch: a fixed 3.2 MB array inside the library, held on every GPU that loads the library
+ *     until the process exits.  Every region of it is written before it is read, so no clearing
+ *     is needed between calls.  All calls share it: calls whose GPU work overlaps (other streams,
+ *     other host threads) race and must be serialised by the caller.
+ *   - The first call on a device looks up the address of that array (and initialises the library
+ *     on the device); make that first call before any stream capture.
+ *   - Synchronises `stream` once (to read the PSF sum).  Allocates nothing. */
+SGP_API sgp_status sgp_convolve_noalloc(const float* psf, const float* f, float* out, int H, int W,
+                                        int psf_origin, int transpose, void* stream);
+
 /* Release the context (not the workspace). */
 SGP_API sgp_status sgp_destroy(sgp_ctx* ctx);
 

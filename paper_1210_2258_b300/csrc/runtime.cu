@@ -1078,3 +1078,105 @@ sgp_status sgp_destroy(sgp_ctx* c) {
 }
 
 }  // extern "C"
+
+// ================================================================================== no-allocation variant
+// A periodic single-view convolution whose scratch lives in a fixed device array instead of a
+// caller-provided workspace, for callers that cannot allocate device memory.
+namespace {
+
+constexpr size_t kNoAllocMaxPixels = 512 * 512;   // H * W limit of sgp_convolve_noalloc
+// layout (floats): PSF spectrum P | Q column 2*2048 | spectrum planes 0, 1: 2P | statistics | jobs | items
+constexpr size_t kNoAllocStatsOff = 3 * kNoAllocMaxPixels + 4 * 2048;
+constexpr size_t kNoAllocJobsOff = kNoAllocStatsOff + 2 * (4 * 296 + 8);
+constexpr size_t kNoAllocItemsOff = kNoAllocJobsOff + 64 * (sizeof(ColJob) / sizeof(float) + 1);
+constexpr size_t kNoAllocFloats = kNoAllocItemsOff + 2 * 4096;
+
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
+float* g_noalloc_ptr[64] = {nullptr};
+
+}  // namespace
+
+extern "C" sgp_status sgp_convolve_noalloc(const float* psf, const float* f, float* out, int H, int W,
+                                           int psf_origin, int transpose, void* stream) {
+  if (!psf || !f || !out) return fail(SGP_ERR_ARG, "NULL array");
+  sgp_shape sh{H, W, 1, 0, psf_origin};
+  sgp_status st = validate_shapes(1, &sh);
+  if (st) return st;
+  if (size_t(H) * W > kNoAllocMaxPixels)
+    return fail(SGP_ERR_SIZE_UNSUPPORTED, "sgp_convolve_noalloc supports at most 262144 pixels (e.g. 512 x 512)");
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if ((st = ensure_device_ready(dev))) return st;
+  if (!g_noalloc_ptr[dev]) {   // once per device: the device address of the fixed scratch array
+    void* p = nullptr;
+    CU(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<float*>(p);
+  }
+  float* base = g_noalloc_ptr[dev];
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t P = size_t(H) * W;
+  const int M = W / 2;
+  float2* khat = reinterpret_cast<float2*>(base);
+  float2* khatq = reinterpret_cast<float2*>(base + P);
+  float* spec0 = base + P + 4 * 2048;
+  float* spec1 = spec0 + P;
+  double* stats = reinterpret_cast<double*>(base + kNoAllocStatsOff);
+  ColJob* jobs = reinterpret_cast<ColJob*>(base + kNoAllocJobsOff);
+  int2* items = reinterpret_cast<int2*>(base + kNoAllocItemsOff);
+  // PSF normalisation constant
+  double ps[4];
+  if ((st = plane_stats(s, psf, nullptr, nullptr, P, 1, 0, stats + 8, stats))) return st;
+  CU(cudaMemcpyAsync(ps, stats, sizeof(ps), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (ps[3] > 0 || !(ps[0] > 0) || !(ps[1] > 0)) return fail(SGP_ERR_PSF, "PSF must be finite with a positive sum");
+  if (ps[2] < -1e-6 * ps[1]) return fail(SGP_ERR_PSF, "PSF has significantly negative samples");
+  // jobs: [0] PSF spectrum, [1] convolution (or correlation); column items of both
+  ColJob hj[2];
+  memset(hj, 0, sizeof(hj));
+  const size_t ps2 = P / 2;
+  hj[0].in = reinterpret_cast<const float2*>(spec1);
+  hj[0].out = khat;
+  hj[0].khat = khat;
+  hj[0].khatq = khatq;
+  hj[0].H = H; hj[0].M = M; hj[0].nin = 1; hj[0].nout = 1; hj[0].plane_stride = ps2;
+  hj[0].scale = float(1.0 / (ps[0] * double(H) * double(M)));
+  hj[0].corner = psf_origin == SGP_PSF_CORNER;
+  hj[1] = hj[0];
+  hj[1].in = reinterpret_cast<const float2*>(spec0);
+  hj[1].out = reinterpret_cast<float2*>(spec1);
+  const int cpi = cols_per_item(H);
+  int2 hi[2 * 1024];
+  int nk = 0;
+  for (int x = 0; x < M; x += cpi) hi[nk++] = make_int2(0, x);
+  for (int x = 0; x < M; x += cpi) hi[nk + x / cpi] = make_int2(1, x);
+  const int nc = nk;
+  CU(cudaMemcpyAsync(jobs, hj, sizeof(hj), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(items, hi, sizeof(int2) * 2 * nc, cudaMemcpyHostToDevice, s));
+  const int si = side_index(W), sc = side_index(H);
+  const int per_view = (H + rows_per_item(W) - 1) / rows_per_item(W);
+  size_t ivs = P, ovs = ps2;
+  int Hh = H, one = 1, clamp = 1, noclamp = 0;
+  // PSF -> spectrum plane 1 -> PSF spectrum (column pass 0)
+  const float* psrc = psf;
+  float2* sp1 = reinterpret_cast<float2*>(spec1);
+  void* a1[] = {(void*)&psrc, (void*)&ivs, (void*)&sp1, (void*)&ovs, (void*)&Hh, (void*)&one, (void*)&clamp};
+  CU(cudaLaunchKernel(g_reg.row[ROP_R2C][0][si], dim3(per_view), dim3(kRowBlock), a1, g_reg.row_smem[si], s));
+  const ColJob* j0 = jobs;
+  const int2* it0 = items;
+  int n0 = nc;
+  void* a2[] = {(void*)&j0, (void*)&it0, (void*)&n0};
+  CU(cudaLaunchKernel(g_reg.col[COL_KHAT][sc], dim3(n0), dim3(kColBlock), a2, g_reg.col_smem[sc], s));
+  // f -> spectrum plane 0 -> (times PSF spectrum) plane 1 -> out
+  float2* sp0 = reinterpret_cast<float2*>(spec0);
+  void* a3[] = {(void*)&f, (void*)&ivs, (void*)&sp0, (void*)&ovs, (void*)&Hh, (void*)&one, (void*)&noclamp};
+  CU(cudaLaunchKernel(g_reg.row[ROP_R2C][0][si], dim3(per_view), dim3(kRowBlock), a3, g_reg.row_smem[si], s));
+  const int2* it1 = items + nc;
+  void* a4[] = {(void*)&j0, (void*)&it1, (void*)&n0};
+  CU(cudaLaunchKernel(g_reg.col[transpose ? COL_1TOP_CONJ : COL_1TOP][sc], dim3(n0), dim3(kColBlock), a4,
+                      g_reg.col_smem[sc], s));
+  const float2* csp1 = sp1;
+  float sc1 = 1.0f;
+  void* a5[] = {(void*)&csp1, (void*)&ovs, (void*)&out, (void*)&ivs, (void*)&Hh, (void*)&one, (void*)&sc1};
+  CU(cudaLaunchKernel(g_reg.row[ROP_C2R][0][si], dim3(per_view), dim3(kRowBlock), a5, g_reg.row_smem[si], s));
+  return SGP_OK;
+}

@@ -86,6 +86,7 @@ def load() -> C.CDLL:
         "sgp_apply_AT": (st, [vp, i, vp, vp]),
         "sgp_time_passes": (st, [vp, i, C.POINTER(d), i]),
         "sgp_launch_count": (C.c_longlong, [vp]),
+        "sgp_convolve_noalloc": (st, [vp, vp, vp, i, i, i, i, vp]),
         "sgp_destroy": (st, [vp]),
         "sgp_last_error": (C.c_char_p, []),
     }
