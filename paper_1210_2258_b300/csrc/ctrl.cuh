@@ -254,6 +254,164 @@ __global__ void k_ctrl_arm(const ImgDesc* __restrict__ imgs, int n, int kind, in
   c->need_more = 0;
 }
 
+// ------------------------------------------------------------------------------ flux projection
+// Projection onto {y >= 0, sum y = c} in the D^-1 metric (SGP step 2 with the flux constraint):
+// y_i = max(0, x_i - mu D_i), x = f - alpha D grad; pixels with D_i = 0 keep y_i = x_i.
+// mu is the root of the non-increasing piecewise-linear phi(mu) = sum max(0, x - mu D) - c'.
+// Passes: bounds (breakpoint range, sums) -> kFluxPasses candidate evaluations narrowing the bracket
+// -> final exact solve on the active set.  Every pass reads f and grad of the current iterate.
+__device__ __forceinline__ void flux_xd(const ImgDesc& d, const CtrlState* c, size_t i, float& x, float& D) {
+  const float f = d.f[c->k & 1][i], gr = d.grad[c->k & 1][i];
+  const float w = d.w ? d.w[i] : d.w_scalar;
+  D = w * clipf(f, float(c->L1), float(c->L2));
+  x = f - float(c->alpha) * D * gr;
+}
+
+// mode 0: bounds; mode 1: candidate sums; mode 2: final active-set sums
+template <bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_flux_pass(const ImgDesc* __restrict__ imgs, const int2* __restrict__ items,
+                                                        int n_items, int mode) {
+  const int it = blockIdx.x;
+  if (it >= n_items) return;
+  const int2 item = items[it];
+  const ImgDesc& d = imgs[item.x];
+  const CtrlState* c = d.ctrl;
+  if (c->done >= 1 || c->constraint == 0) return;
+  const int row0 = item.y & 0xffff;
+  const int rows = min(d.rpi, d.H - row0);
+  const size_t base = size_t(row0) * d.W, n = size_t(rows) * d.W;
+  double* out = part_of(d, it);
+  if (mode == 0) {
+    KSum acc[3];   // sum x (D > 0), sum D (D > 0), sum x (D = 0)
+    float tmin = f_inf(), tmax = -f_inf();
+    for (size_t q = threadIdx.x; q < n; q += blockDim.x) {
+      float x, D;
+      flux_xd(d, c, base + q, x, D);
+      if (D > 0.0f) {
+        acc[0].add(x); acc[1].add(D);
+        const float t = x / D;
+        tmin = fminf(tmin, t); tmax = fmaxf(tmax, t);
+      } else {
+        acc[2].add(x);
+      }
+    }
+    block_sum_store<3, FP64>(acc, out + SLOT_PROJ);
+    // min t into SLOT_MIN, -max t into SLOT_MAX (stored negated so both reduce as minima)
+    __shared__ float rmn[kRowBlock / 32], rmx[kRowBlock / 32];
+    float a = tmin, b = -tmax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a = fminf(a, __shfl_xor_sync(0xffffffffu, a, o));
+      b = fminf(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { rmn[wid] = a; rmx[wid] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < int(blockDim.x >> 5); ++w) { a = fminf(a, rmn[w]); b = fminf(b, rmx[w]); }
+      a = fminf(rmn[0], a); b = fminf(rmx[0], b);
+      out[SLOT_MIN] = a;
+      out[SLOT_MAX] = b;
+    }
+  } else if (mode == 1) {
+    KSum acc[kFluxCand];
+    float mu[kFluxCand];
+    const double lo = c->mu_lo, hi = c->mu_hi;
+#pragma unroll
+    for (int q = 0; q < kFluxCand; ++q) mu[q] = float(lo + (hi - lo) * double(q + 1) / double(kFluxCand + 1));
+    for (size_t q = threadIdx.x; q < n; q += blockDim.x) {
+      float x, D;
+      flux_xd(d, c, base + q, x, D);
+      if (D > 0.0f) {
+#pragma unroll
+        for (int m = 0; m < kFluxCand; ++m) acc[m].add(fmaxf(x - mu[m] * D, 0.0f));
+      }
+    }
+    block_sum_store<kFluxCand, FP64>(acc, out + SLOT_ARMX);
+  } else {
+    KSum acc[2];   // sum x, sum D over the pixels with t > mu_lo (active just above mu_lo)
+    const float a = float(c->mu_lo);
+    for (size_t q = threadIdx.x; q < n; q += blockDim.x) {
+      float x, D;
+      flux_xd(d, c, base + q, x, D);
+      if (D > 0.0f && x - a * D > 0.0f) { acc[0].add(x); acc[1].add(D); }
+    }
+    block_sum_store<2, FP64>(acc, out + SLOT_PROJ + 3);
+  }
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(kCtrlBlock) k_ctrl_flux(const ImgDesc* __restrict__ imgs, int mode) {
+  const ImgDesc& d = imgs[blockIdx.x];
+  CtrlState* c = d.ctrl;
+  if (c->done >= 1 || c->constraint == 0) return;
+  if (mode == 0) {
+    double s[3], mn = 0.0, mxneg = 0.0;
+    ctrl_sum<3, FP64>(d, SLOT_PROJ, s, false);
+    {   // minima of SLOT_MIN (min t) and SLOT_MAX (-max t)
+      __shared__ double ra[kCtrlBlock / 32], rb[kCtrlBlock / 32];
+      double a = INFINITY, b = INFINITY;
+      for (int i = threadIdx.x; i < d.n_row_items; i += blockDim.x) {
+        a = fmin(a, d.part[size_t(i) * kPartStride + SLOT_MIN]);
+        b = fmin(b, d.part[size_t(i) * kPartStride + SLOT_MAX]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = fmin(b, __shfl_xor_sync(0xffffffffu, b, o));
+      }
+      if ((threadIdx.x & 31) == 0) { ra[threadIdx.x >> 5] = a; rb[threadIdx.x >> 5] = b; }
+      __syncthreads();
+      mn = INFINITY; mxneg = INFINITY;
+      for (int w = 0; w < int(blockDim.x >> 5); ++w) { mn = fmin(mn, ra[w]); mxneg = fmin(mxneg, rb[w]); }
+      __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double cp = c->flux_c - s[2];
+    c->phi_lo = cp;                              // target of the active part
+    if (!(cp > 0.0) || !(s[1] > 0.0)) {          // nothing to distribute: y = 0 on D > 0
+      c->mu = -mxneg + 1.0;
+      c->mu_lo = c->mu_hi = c->mu;
+      c->proj_pass = -1;
+      return;
+    }
+    const double tmax = -mxneg;
+    c->mu_hi = tmax;                                         // phi(mu_hi) = 0 <= cp
+    c->mu_lo = fmin(mn, (s[0] - cp) / s[1]);                 // all active: phi = sum x - mu sum D >= cp
+    c->proj_pass = 0;
+  } else if (mode == 1) {
+    double s[kFluxCand];
+    ctrl_sum<kFluxCand, FP64>(d, SLOT_ARMX, s, false);
+    if (threadIdx.x != 0 || c->proj_pass < 0) return;
+    const double lo = c->mu_lo, hi = c->mu_hi, cp = c->phi_lo;
+    double nlo = lo, nhi = hi;
+    for (int q = 0; q < kFluxCand; ++q) {               // phi is non-increasing in mu
+      const double m = lo + (hi - lo) * double(q + 1) / double(kFluxCand + 1);
+      if (s[q] >= cp) nlo = m; else { nhi = m; break; }
+    }
+    c->mu_lo = nlo;
+    c->mu_hi = nhi;
+    c->proj_pass += 1;
+  } else {
+    double s[2];
+    ctrl_sum<2, FP64>(d, SLOT_PROJ + 3, s, false);
+    if (threadIdx.x != 0) return;
+    if (c->proj_pass < 0) return;
+    double mu = s[1] > 0.0 ? (s[0] - c->phi_lo) / s[1] : c->mu_hi;
+    if (!(mu >= c->mu_lo)) mu = c->mu_lo;                 // clamp to the bracket
+    if (!(mu <= c->mu_hi)) mu = c->mu_hi;
+    c->mu = mu;
+  }
+}
+
+// Scale f[0] by flux_c / sum f (flux-constrained start); sum from the set-up statistics
+__global__ void k_scale(float* __restrict__ f, size_t P, const double* __restrict__ sum, double target) {
+  const double s = sum[0];
+  const float a = s > 0.0 ? float(target / s) : 1.0f;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < P; i += size_t(gridDim.x) * blockDim.x)
+    f[i] *= a;
+}
+
 // ------------------------------------------------------------------------------ set-up kernels
 // g_int = g on S, -1 outside S (boundary); counts non-finite or negative samples.
 __global__ void k_prepare_data(const float* __restrict__ g, const uint8_t* __restrict__ mask,

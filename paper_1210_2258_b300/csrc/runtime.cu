@@ -122,6 +122,7 @@ void plan_layout(char* base, int n, const sgp_shape* sh, int trace_cap, const bo
     ImgDesc& d = L.d[i];
     d.H = H; d.W = W; d.p = p; d.boundary = sh[i].has_mask ? 1 : 0; d.P = P;
     const int rpi = rows_per_item(W), cpi = cols_per_item(H), M = W / 2;
+    d.rpi = rpi;
     const int nr = (H + rpi - 1) / rpi, nc = (M + cpi - 1) / cpi;
     d.row_item0 = 0; d.n_row_items = nr;      // indices within the problem's own range
     d.rv_item0 = 0; d.n_rv_items = nr * p;
@@ -282,6 +283,25 @@ sgp_status seq_rl_unit(sgp_ctx* c) {
   return ctrl_pass(c, c->fp64 ? (const void*)&k_ctrl_rl<true> : (const void*)&k_ctrl_rl<false>);
 }
 
+// flux-constrained projection: bracket, kFluxPasses candidate passes, exact final solve
+sgp_status seq_flux(sgp_ctx* c) {
+  sgp_status st;
+  const bool f = c->fp64;
+  const void* fp = f ? (const void*)&k_flux_pass<true> : (const void*)&k_flux_pass<false>;
+  const void* fc = f ? (const void*)&k_ctrl_flux<true> : (const void*)&k_ctrl_flux<false>;
+  const ImgDesc* imgs = c->L.d_imgs;
+  const int2* items = c->L.d_row;
+  int n = c->L.n_row;
+  for (int step = 0; step < kFluxPasses + 2; ++step) {
+    int mode = step == 0 ? 0 : (step <= kFluxPasses ? 1 : 2);
+    void* a[] = {(void*)&imgs, (void*)&items, (void*)&n, (void*)&mode};
+    if ((st = launch(fp, n, kRowBlock, 0, c->s, a))) return st;
+    void* b[] = {(void*)&imgs, (void*)&mode};
+    if ((st = launch(fc, c->n, kCtrlBlock, 0, c->s, b))) return st;
+  }
+  return SGP_OK;
+}
+
 sgp_status seq_sgp_unit(sgp_ctx* c) {
   sgp_status st;
   const bool f = c->fp64;
@@ -289,6 +309,7 @@ sgp_status seq_sgp_unit(sgp_ctx* c) {
   if ((st = col_pass(c, COL_PTO1, JOB_AT * c->n))) return st;
   if ((st = row_pass(c, ROP_SGP_GRAD, false))) return st;
   if ((st = ctrl_pass(c, f ? (const void*)&k_ctrl_alpha<true> : (const void*)&k_ctrl_alpha<false>))) return st;
+  if (c->prm.constraint == 1 && (st = seq_flux(c))) return st;
   if ((st = row_pass(c, ROP_SGP_Y, false))) return st;
   if ((st = col_pass(c, COL_1TOP, JOB_A * c->n))) return st;
   if ((st = row_pass(c, ROP_SGP_AD, true))) return st;
@@ -339,6 +360,7 @@ sgp_status reset_ctrl(sgp_ctx* c) {
     z.stop_kind = STOP_FIXED; z.max_iter = 0;
     z.M_alpha = P.M_alpha; z.warmup = P.warmup_iters; z.max_backtracks = P.max_backtracks;
     z.fp64 = c->fp64; z.constraint = P.constraint;
+    z.flux_c = P.flux_c > 0.0 ? P.flux_c : c->c_const[i] * c->nS[i];
     z.alpha = P.alpha0; z.alpha_prev = P.alpha0; z.tau = P.tau1; z.lambda = 1.0;
     z.L1 = P.L1; z.L2 = P.L2;
     z.beta = P.beta; z.theta = P.theta; z.alpha0 = P.alpha0; z.tau1 = P.tau1;
@@ -360,6 +382,22 @@ sgp_status prepare(sgp_ctx* c, int mode) {
     if (!c->has_data[i]) return fail(SGP_ERR_STATE, "sgp_set_data was not called for every problem");
   sgp_status st;
   if ((st = reset_ctrl(c))) return st;
+  if (c->prm.constraint == 1 && mode == 1) {   // flux-constrained start: scale f0 to sum c
+    for (int i = 0; i < c->n; ++i) {
+      ImgDesc& d = c->L.d[i];
+      const double target = c->prm.flux_c > 0.0 ? c->prm.flux_c : c->c_const[i] * c->nS[i];
+      if (!(target > 0.0)) return fail(SGP_ERR_ARG, "flux constraint needs a positive flux");
+      if ((st = plane_stats(c->s, d.f[0], nullptr, nullptr, d.P, 1, 0, reinterpret_cast<double*>(d.Ad),
+                            c->L.scratch[i])))
+        return st;
+      float* f0 = d.f[0];
+      const double* sum = c->L.scratch[i];
+      size_t P = d.P;
+      double tg = target;
+      void* a[] = {(void*)&f0, (void*)&P, (void*)&sum, (void*)&tg};
+      if ((st = launch((const void*)&k_scale, grid_for(P), 256, 0, c->s, a))) return st;
+    }
+  }
   if ((st = row_pass(c, ROP_RL_UPDATE, false))) return st;       // R2C of f0 into plane 0
   if ((st = col_pass(c, COL_1TOP, JOB_A * c->n))) return st;
   if ((st = row_pass(c, ROP_RL_RATIO, true, 1))) return st;      // u = A f0, J_0, r spectra
@@ -408,7 +446,7 @@ sgp_status run_fixed(sgp_ctx* c, bool sgp, int n_iter) {
   const int launches = (n_iter + c->graph_units - 1) / c->graph_units;
   for (int l = 0; l < launches; ++l) {
     CU(cudaGraphLaunch(sgp ? c->g_sgp : c->g_rl, c->s));
-    c->launches += c->graph_units * (sgp ? 10 : 5);
+    c->launches += c->graph_units * (sgp ? (c->prm.constraint == 1 ? 24 : 10) : 5);
   }
   if (sgp && (st = seq_sgp_finalize(c))) return st;
   return SGP_OK;
@@ -429,7 +467,7 @@ sgp_status run_until(sgp_ctx* c, bool sgp, const sgp_stop_rule* rule, int* iters
   const int max_launches = rule->max_iter / c->graph_units + 2;
   CtrlState* slot[2] = {c->h_ctrl, c->h_ctrl + c->n};
   // keep one chunk in flight while the flags of the previous one are inspected
-  const int per_graph = c->graph_units * (sgp ? 10 : 5);
+  const int per_graph = c->graph_units * (sgp ? (c->prm.constraint == 1 ? 24 : 10) : 5);
   CU(cudaGraphLaunch(g, c->s));
   c->launches += per_graph;
   CU(cudaMemcpyAsync(slot[0], c->L.ctrl, sizeof(CtrlState) * c->n, cudaMemcpyDeviceToHost, c->s));
@@ -534,7 +572,7 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
   if (!(P.alpha_min > 0 && P.alpha_min < P.alpha_max)) return fail(SGP_ERR_ARG, "need 0 < alpha_min < alpha_max");
   if (!P.adaptive_L && !(P.L1 > 0 && P.L1 < P.L2)) return fail(SGP_ERR_ARG, "need 0 < L1 < L2");
   if (P.trace_cap < 1) P.trace_cap = 1;
-  if (P.constraint != 0) return fail(SGP_ERR_ARG, "flux constraint is not available in this build");
+  if (P.constraint != 0 && P.constraint != 1) return fail(SGP_ERR_ARG, "constraint must be 0 or 1");
 
   int dev = 0;
   CU(cudaGetDevice(&dev));

@@ -28,6 +28,8 @@ enum Slot {
   SLOT_PROJ = 42,     // flux projection search sums (up to 6)
 };
 constexpr int kArmExtra = 27;
+constexpr int kFluxCand = 16;       // candidate mu values per flux-search pass (slots SLOT_ARMX..)
+constexpr int kFluxPasses = 5;
 
 enum ColMode { COL_KHAT = 0, COL_1TOP = 1, COL_1TOP_CONJ = 2, COL_PTO1 = 3 };
 
@@ -69,6 +71,7 @@ struct ImgDesc {
   int H, W, p, boundary;
   int row_item0, n_row_items;   // this problem's items in the row-item list (image, row0)
   int rv_item0, n_rv_items;     // ... and in the row-view list (image, row0 | view << 16)
+  int rpi;                      // image rows per row item
   float w_scalar;               // periodic: 1/p (RL factor, SGP scaling factor)
   float a1_scalar;              // periodic: p (= sum_j A_j^T 1)
   float bs[kMaxViews];          // constant backgrounds (used when b == nullptr)

@@ -207,3 +207,20 @@ def test_starting_points(gpu):
     user = scenes.rng_for(1).random((32, 32)).astype(np.float32) - 0.2
     prob.set_start(0, gpu.START_USER, dev(user))
     np.testing.assert_allclose(host(prob.get_f()), np.maximum(user, 0), rtol=1e-6)
+
+
+def test_flux_constrained_sgp(gpu, galaxy128):
+    """SGP with the flux constraint sum f = c (projection onto {f >= 0, sum f = c} in the D^-1
+    metric): parity with the oracle's exact projection, and the constraint holds on the GPU."""
+    sc = galaxy128
+    orc = oracle_problem(sc)
+    c = float(orc.g.sum() - np.asarray(orc.b).sum())
+    ref = O.sgp(orc, P=O.SGPParams(flux=c), stop=O.StopRule("fixed", max_iter=15))
+    prob = gpu_problem(gpu, sc, gpu.default_params(constraint=1, flux_c=c))
+    prob.sgp_iterate(15)
+    f = host(prob.get_f())
+    assert np.all(f >= 0) and abs(f.sum() - c) <= 1e-4 * c
+    assert rel_l2(f, ref.f) <= 1e-3, rel_l2(f, ref.f)
+    assert abs(prob.kl_value() - ref.J) <= 1e-5 * ref.J
+    tr = prob.trace()
+    assert np.all(np.diff(tr[:, 1]) <= 0)
