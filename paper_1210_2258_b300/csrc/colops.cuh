@@ -59,8 +59,7 @@ __device__ __forceinline__ float2 col_product(const ColLayout<C>& x, int i, int 
 // One block per item (job, col0 | view << 16): runtime loops around the transforms make the
 // register allocator keep every stage's addresses live, so views are separate items where possible.
 template <int H, int MODE, int NV = 0>
-__global__ void __launch_bounds__(kColBlock) k_col(const ColJob* __restrict__ jobs, const int2* __restrict__ items,
-                                                  int n_items) {
+__device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int2* __restrict__ items, int n_items) {
   using G = ColGeo<H>;
   constexpr int C = G::C, T = G::T, E = G::E;
   extern __shared__ float2 smem[];
@@ -186,6 +185,13 @@ __global__ void __launch_bounds__(kColBlock) k_col(const ColJob* __restrict__ jo
       __syncthreads();
     }
   }
+}
+
+template <int H, int MODE, int NV = 0>
+__global__ void __launch_bounds__(kColBlock) k_col(const ColJob* __restrict__ jobs, const int2* __restrict__ items,
+                                                  int n_items) {
+  b_col<H, MODE, NV>(jobs, items, n_items);
+
 }
 
 }  // namespace sgp

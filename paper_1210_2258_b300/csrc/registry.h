@@ -26,11 +26,19 @@ struct Registry {
   const void* col[kColModes][kNumSides];      // [variant][side]
   size_t row_smem[kNumSides], col_smem[kNumSides];
   int row_rows[kNumSides], col_cols[kNumSides];
-  cudaError_t (*twiddle_init[3])(const float2*);
+  cudaError_t (*twiddle_init[5])(const float2*);
+  // multi-size kernels (one launch covers problems of different sides): row ops, and the column
+  // passes 1 -> p (index 0), p -> 1 for any p (index 1) and for p = 1 (index 2); dynamic shared
+  // memory = max over the sides
+  const void* row_multi[ROP_COUNT][2];
+  const void* col_multi[3];
+  size_t row_multi_smem, col_multi_smem;
 };
 
 void register_small(Registry&);
 void register_mid(Registry&);
 void register_large(Registry&);
+void register_multi_sgp(Registry&);
+void register_multi_rest(Registry&);
 
 }  // namespace sgp

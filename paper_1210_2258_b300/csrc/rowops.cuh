@@ -323,7 +323,7 @@ __device__ __forceinline__ int item_view(int2 item) { return item.y >> 16; }
 // SGP K1: apply the pending update f <- f + lambda d and A_j f <- A_j f + lambda A_j d (Alg. 1,
 // step 6), then r_j = g_j / (A_j f + b_j) -> R2C into planes 1..p, with the KL (and rho) partials.
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock) k_sgp_update_ratio(const ImgDesc* __restrict__ imgs,
+__device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ imgs,
                                                                const int2* __restrict__ items, int n_items) {
   using G = RowGeo<W>;
   extern __shared__ float2 smem[];
@@ -396,10 +396,15 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_update_ratio(const ImgDesc* _
     block_sum_store<2, FP64>(acc, partv_of(d, it) + SLOT_KL);
   }
 }
+template <int W, bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_sgp_update_ratio(const ImgDesc* __restrict__ imgs,
+                                                               const int2* __restrict__ items, int n_items) {
+  b_sgp_update_ratio<W, FP64>(imgs, items, n_items);
+}
 
 // SGP K3: C2R of plane 0 (= sum_j A_j^T r_j) -> gradient, and the four scaled-BB partial sums.
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock) k_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
+__device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
                                                           const int2* __restrict__ items, int n_items) {
   using G = RowGeo<W>;
   extern __shared__ float2 smem[];
@@ -451,10 +456,15 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_grad_bb(const ImgDesc* __rest
     block_sum_store<4, FP64>(acc, part_of(d, it) + SLOT_BB);
   }
 }
+template <int W, bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
+                                                          const int2* __restrict__ items, int n_items) {
+  b_sgp_grad_bb<W, FP64>(imgs, items, n_items);
+}
 
 // SGP K4: y = P(f - alpha D grad) (Alg. 1 step 2), d = y - f -> R2C into plane 0, grad'd partials.
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock) k_sgp_y(const ImgDesc* __restrict__ imgs,
+__device__ __forceinline__ void b_sgp_y(const ImgDesc* __restrict__ imgs,
                                                     const int2* __restrict__ items, int n_items) {
   using G = RowGeo<W>;
   extern __shared__ float2 smem[];
@@ -492,11 +502,16 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_y(const ImgDesc* __restrict__
     block_sum_store<1, FP64>(acc, part_of(d, it) + SLOT_GTD);
   }
 }
+template <int W, bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_sgp_y(const ImgDesc* __restrict__ imgs,
+                                                    const int2* __restrict__ items, int n_items) {
+  b_sgp_y<W, FP64>(imgs, items, n_items);
+}
 
 // SGP K6: per view, C2R of plane j+1 (= A_j d) -> stored A_j d (A(f + lam d) = A f + lam A d: no FFT
 // per backtrack) and the Armijo partial sums Delta J(theta^i), i = 0..3 (Alg. 1 step 5).
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock) k_sgp_ad_armijo(const ImgDesc* __restrict__ imgs,
+__device__ __forceinline__ void b_sgp_ad_armijo(const ImgDesc* __restrict__ imgs,
                                                             const int2* __restrict__ items, int n_items) {
   using G = RowGeo<W>;
   extern __shared__ float2 smem[];
@@ -535,10 +550,15 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_ad_armijo(const ImgDesc* __re
   }
   block_sum_store<4, FP64>(acc, partv_of(d, it) + SLOT_ARM);
 }
+template <int W, bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_sgp_ad_armijo(const ImgDesc* __restrict__ imgs,
+                                                            const int2* __restrict__ items, int n_items) {
+  b_sgp_ad_armijo<W, FP64>(imgs, items, n_items);
+}
 
 // SGP K7 (only when no lambda in {1, .., theta^3} was accepted): Delta J(theta^i), i = 4..30.
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock) k_sgp_armijo_extra(const ImgDesc* __restrict__ imgs,
+__device__ __forceinline__ void b_sgp_armijo_extra(const ImgDesc* __restrict__ imgs,
                                                                const int2* __restrict__ items, int n_items) {
   using G = RowGeo<W>;
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
@@ -576,11 +596,16 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_armijo_extra(const ImgDesc* _
     block_sum_store<kArmExtra, FP64>(acc, part_of(d, it) + SLOT_ARMX);
   }
 }
+template <int W, bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_sgp_armijo_extra(const ImgDesc* __restrict__ imgs,
+                                                               const int2* __restrict__ items, int n_items) {
+  b_sgp_armijo_extra<W, FP64>(imgs, items, n_items);
+}
 
 // RL K1: if plane 0 holds v = sum_j A_j^T r_j, f <- w f v (Eq. RL / multipleRL / boundaryRL);
 // then R2C of the current iterate into plane 0 (and the rho partial).
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock) k_rl_update(const ImgDesc* __restrict__ imgs,
+__device__ __forceinline__ void b_rl_update(const ImgDesc* __restrict__ imgs,
                                                         const int2* __restrict__ items, int n_items) {
   using G = RowGeo<W>;
   extern __shared__ float2 smem[];
@@ -625,11 +650,16 @@ __global__ void __launch_bounds__(kRowBlock) k_rl_update(const ImgDesc* __restri
     block_sum_store<1, FP64>(acc, part_of(d, it) + SLOT_RHO);
   }
 }
+template <int W, bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_rl_update(const ImgDesc* __restrict__ imgs,
+                                                        const int2* __restrict__ items, int n_items) {
+  b_rl_update<W, FP64>(imgs, items, n_items);
+}
 
 // RL K3 (also a set-up pass): per view, C2R of plane j+1 (= A_j f) -> KL partials and
 // r_j = g_j/(A_j f + b_j) -> R2C back into plane j+1; optionally stores A_j f into u.
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock) k_rl_ratio(const ImgDesc* __restrict__ imgs,
+__device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
                                                        const int2* __restrict__ items, int n_items, int write_u) {
   using G = RowGeo<W>;
   extern __shared__ float2 smem[];
@@ -664,10 +694,15 @@ __global__ void __launch_bounds__(kRowBlock) k_rl_ratio(const ImgDesc* __restric
   row_real_to_spec<W>(x, sp, t, act);
   block_sum_store<1, FP64>(acc, partv_of(d, it) + SLOT_KL);
 }
+template <int W, bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_rl_ratio(const ImgDesc* __restrict__ imgs,
+                                                       const int2* __restrict__ items, int n_items, int write_u) {
+  b_rl_ratio<W, FP64>(imgs, items, n_items, write_u);
+}
 
 // Set-up: y = w f v from plane 0 (one RL step from f^(0), Sect. 3.2); min over positive y and max y.
 template <int W>
-__global__ void __launch_bounds__(kRowBlock) k_rl_step_minmax(const ImgDesc* __restrict__ imgs,
+__device__ __forceinline__ void b_rl_step_minmax(const ImgDesc* __restrict__ imgs,
                                                              const int2* __restrict__ items, int n_items) {
   using G = RowGeo<W>;
   extern __shared__ float2 smem[];
@@ -697,6 +732,11 @@ __global__ void __launch_bounds__(kRowBlock) k_rl_step_minmax(const ImgDesc* __r
     }
     block_minmax_store(mn, mx, part_of(d, it) + SLOT_MIN);
   }
+}
+template <int W>
+__global__ void __launch_bounds__(kRowBlock) k_rl_step_minmax(const ImgDesc* __restrict__ imgs,
+                                                             const int2* __restrict__ items, int n_items) {
+  b_rl_step_minmax<W>(imgs, items, n_items);
 }
 
 }  // namespace sgp

@@ -43,6 +43,8 @@ sgp_status ensure_device_ready(int dev) {
     register_small(g_reg);
     register_mid(g_reg);
     register_large(g_reg);
+    register_multi_sgp(g_reg);
+    register_multi_rest(g_reg);
     g_reg_ready = true;
   }
   if (dev < 0 || dev >= 64) return fail(SGP_ERR_CUDA, "device index out of range");
@@ -57,7 +59,15 @@ sgp_status ensure_device_ready(int dev) {
       tab[off + q] = make_float2(float(cos(a)), float(sin(a)));
     }
   }
-  for (int i = 0; i < 3; ++i) CU(g_reg.twiddle_init[i](tab.data()));
+  for (int i = 0; i < 5; ++i) CU(g_reg.twiddle_init[i](tab.data()));
+  for (int op = 0; op < ROP_COUNT; ++op)
+    for (int f = 0; f < 2; ++f)
+      if (g_reg.row_multi[op][f])
+        CU(cudaFuncSetAttribute(g_reg.row_multi[op][f], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(g_reg.row_multi_smem)));
+  for (int m = 0; m < 3; ++m)
+    CU(cudaFuncSetAttribute(g_reg.col_multi[m], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            int(g_reg.col_multi_smem)));
   for (int s = 0; s < kNumSides; ++s) {
     for (int op = 0; op < ROP_COUNT; ++op)
       for (int f = 0; f < 2; ++f)
@@ -172,7 +182,8 @@ struct sgp_ctx {
   sgp_params prm;
   std::vector<sgp_shape> sh;
   Layout L;
-  int H = 0, W = 0, p = 0;         // common geometry (every problem of a context has the same H, W, p)
+  int H = 0, W = 0, p = 0;         // geometry of problem 0 (every problem has the same p)
+  bool mixed = false;              // problems of different sides: multi-size kernels
   int fp64 = 1;
   // host mirrors
   std::vector<int2> row, rv, colv, col, colk;
@@ -205,20 +216,26 @@ sgp_status launch(const void* fn, int grid, int block, size_t smem, cudaStream_t
 
 sgp_status row_pass(sgp_ctx* c, RowOp op, bool view_list, int extra = -1) {
   const int si = side_index(c->W);
-  const void* fn = g_reg.row[op][c->fp64][si];
+  const void* fn = c->mixed ? g_reg.row_multi[op][c->fp64] : g_reg.row[op][c->fp64][si];
+  const size_t smem = c->mixed ? g_reg.row_multi_smem : g_reg.row_smem[si];
   const ImgDesc* imgs = c->L.d_imgs;
   const int2* items = view_list ? c->L.d_rv : c->L.d_row;
   int n = view_list ? c->L.n_rv : c->L.n_row;
   void* args4[] = {(void*)&imgs, (void*)&items, (void*)&n, (void*)&extra};
-  return launch(fn, n, kRowBlock, g_reg.row_smem[si], c->s, args4);
+  return launch(fn, n, kRowBlock, smem, c->s, args4);
 }
 
 // variant: COL_1TOP (views list), COL_1TOP_CONJ, COL_PTO1; job_off selects A/AT/CONJ/raw jobs
 sgp_status col_pass(sgp_ctx* c, int variant, int job_off, int image = -1) {
-  const int si = side_index(c->H);
+  const int si = side_index(image >= 0 ? c->L.d[image].H : c->H);
   int v = variant;
   if (variant == COL_PTO1) v = c->p == 1 ? kColPto1P1 : (c->p == 3 ? kColPto1P3 : COL_PTO1);
   const void* fn = g_reg.col[v][si];
+  size_t smem = g_reg.col_smem[si];
+  if (c->mixed && image < 0) {
+    fn = variant == COL_PTO1 ? g_reg.col_multi[c->p == 1 ? 2 : 1] : g_reg.col_multi[0];
+    smem = g_reg.col_multi_smem;
+  }
   const bool views = variant != COL_PTO1;
   const int2* items = views ? c->L.d_colv : c->L.d_col;
   int n = views ? c->L.n_colv : c->L.n_col;
@@ -229,7 +246,7 @@ sgp_status col_pass(sgp_ctx* c, int variant, int job_off, int image = -1) {
   // the job index of an item is the problem index; job_off picks the job kind
   const ColJob* jobs = c->L.d_jobs + job_off;
   void* args[] = {(void*)&jobs, (void*)&items, (void*)&n};
-  return launch(fn, n, kColBlock, g_reg.col_smem[si], c->s, args);
+  return launch(fn, n, kColBlock, smem, c->s, args);
 }
 
 sgp_status ctrl_pass(sgp_ctx* c, const void* fn) {
@@ -526,8 +543,7 @@ static sgp_status validate_shapes(int n, const sgp_shape* sh) {
     if (sh[i].p < 1 || sh[i].p > kMaxViews) return fail(SGP_ERR_SIZE_UNSUPPORTED, "p must be 1..8");
     if (sh[i].psf_origin != SGP_PSF_CENTER && sh[i].psf_origin != SGP_PSF_CORNER)
       return fail(SGP_ERR_ARG, "psf_origin must be SGP_PSF_CENTER or SGP_PSF_CORNER");
-    if (sh[i].H != sh[0].H || sh[i].W != sh[0].W || sh[i].p != sh[0].p)
-      return fail(SGP_ERR_SIZE_UNSUPPORTED, "problems of one context must share H, W and p");
+    if (sh[i].p != sh[0].p) return fail(SGP_ERR_SIZE_UNSUPPORTED, "problems of one context must share p");
   }
   return SGP_OK;
 }
@@ -541,6 +557,8 @@ size_t sgp_workspace_bytes(int n, const sgp_shape* shapes, const sgp_params* par
     register_small(g_reg);
     register_mid(g_reg);
     register_large(g_reg);
+    register_multi_sgp(g_reg);
+    register_multi_rest(g_reg);
     g_reg_ready = true;
   }
   sgp_params P;
@@ -585,6 +603,7 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
   c->fp64 = P.reduce_fp64 ? 1 : 0;
   c->sh.assign(shapes, shapes + n);
   c->H = shapes[0].H; c->W = shapes[0].W; c->p = shapes[0].p;
+  for (int i = 1; i < n; ++i) c->mixed = c->mixed || shapes[i].H != c->H || shapes[i].W != c->W;
   c->user = reinterpret_cast<cudaStream_t>(stream);
   auto bail = [&](sgp_status s) { sgp_destroy(c); return s; };
   if (cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking) != cudaSuccess ||
@@ -605,12 +624,16 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
   Layout& L = c->L;
   if ((st = enter(c))) return bail(st);
 
-  // item lists (each problem's items contiguous) and per-problem descriptors
-  const int rpi = rows_per_item(c->W), cpi = cols_per_item(c->H), M = c->W / 2;
+  // item lists: each problem's items contiguous, problems ordered largest first (the work items of
+  // one launch then run longest-first across the SMs)
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return L.d[a].P > L.d[b].P; });
   int r0 = 0, rv0 = 0;
   c->colv_begin.resize(n); c->colv_count.resize(n); c->col_begin.resize(n); c->col_count.resize(n);
-  for (int i = 0; i < n; ++i) {
+  for (int i : order) {
     ImgDesc& d = L.d[i];
+    const int rpi = rows_per_item(d.W), cpi = cols_per_item(d.H), M = d.W / 2;
     d.row_item0 = r0; d.rv_item0 = rv0;
     for (int y = 0; y < d.H; y += rpi) c->row.push_back(make_int2(i, y));
     for (int j = 0; j < d.p; ++j)
@@ -660,9 +683,14 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
     }
   }
   // the column-item lists address job index = problem index; the spectrum set-up needs its own
-  for (int i = 0, jb = 5 * n; i < n; ++i)
+  std::vector<int> colk_begin(n), colk_count(n);
+  for (int i = 0, jb = 5 * n; i < n; ++i) {
+    colk_begin[i] = int(c->colk.size());
+    const int cpi = cols_per_item(L.d[i].H), M = L.d[i].W / 2;
     for (int j = 0; j < L.d[i].p; ++j, ++jb)
       for (int x = 0; x < M; x += cpi) c->colk.push_back(make_int2(jb, x));
+    colk_count[i] = int(c->colk.size()) - colk_begin[i];
+  }
   c->c_const.assign(n, 0.0);
   c->nS.assign(n, 0.0);
   c->has_data.assign(n, 0);
@@ -708,11 +736,11 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
       cudaMemcpyAsync(L.d_col, c->col.data(), sizeof(int2) * c->col.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
       cudaMemcpyAsync(L.d_colk, c->colk.data(), sizeof(int2) * c->colk.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess)
     return bail(fail(SGP_ERR_CUDA, "descriptor upload failed"));
-  {  // PSF spectra (forward column transforms, P/Q packing, scaling, origin shift)
-    const int si = side_index(c->H);
+  for (int i = 0; i < n; ++i) {  // PSF spectra (forward column transforms, P/Q packing, scaling, shift)
+    const int si = side_index(L.d[i].H);
     const ColJob* jobs = L.d_jobs;
-    const int2* items = L.d_colk;
-    int nk = L.n_colk;
+    const int2* items = L.d_colk + colk_begin[i];
+    int nk = colk_count[i];
     void* a[] = {(void*)&jobs, (void*)&items, (void*)&nk};
     if ((st = launch(g_reg.col[COL_KHAT][si], nk, kColBlock, g_reg.col_smem[si], c->s, a))) return bail(st);
   }

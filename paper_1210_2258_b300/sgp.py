@@ -153,10 +153,12 @@ class Problems:
         shapes = (Shape * n)()
         inputs = (Inputs * n)()
         self._keep = []
+        self.shapes = [tuple(int(v) for v in ps.shape[-2:]) for ps in psfs]
         for k in range(n):
             ps = psfs[k].contiguous()
             self._keep.append(ps)
-            shapes[k] = Shape(self.H, self.W, self.p, 1 if masks[k] is not None else 0, psf_origin)
+            Hk, Wk = self.shapes[k]
+            shapes[k] = Shape(Hk, Wk, self.p, 1 if masks[k] is not None else 0, psf_origin)
             inputs[k].psfs = ps.data_ptr()
             bk = b[k]
             if hasattr(bk, "data_ptr"):
@@ -230,7 +232,7 @@ class Problems:
     def get_f(self, image: int = 0, out=None):
         import torch
         if out is None:
-            out = torch.empty((self.H, self.W), dtype=torch.float32, device=self.device)
+            out = torch.empty(self.shapes[image], dtype=torch.float32, device=self.device)
         _check(load().sgp_get_f(self.ctx, image, out.data_ptr()))
         return out
 
@@ -246,7 +248,7 @@ class Problems:
         import torch
         f = f.contiguous()
         if out is None:
-            out = torch.empty((self.p, self.H, self.W), dtype=torch.float32, device=self.device)
+            out = torch.empty((self.p,) + self.shapes[image], dtype=torch.float32, device=self.device)
         _check(load().sgp_apply_A(self.ctx, image, f.data_ptr(), out.data_ptr()))
         return out
 
@@ -254,7 +256,7 @@ class Problems:
         import torch
         y = y.contiguous()
         if out is None:
-            out = torch.empty((self.H, self.W), dtype=torch.float32, device=self.device)
+            out = torch.empty(self.shapes[image], dtype=torch.float32, device=self.device)
         _check(load().sgp_apply_AT(self.ctx, image, y.data_ptr(), out.data_ptr()))
         return out
 
