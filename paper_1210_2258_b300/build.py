@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(LIBDIR, "libsgp_b300.so")
-UNITS = ["k_small.cu", "k_mid.cu", "k_large.cu", "k_multi_sgp.cu", "k_multi_rest.cu", "runtime.cu"]
+UNITS = ["k_small.cu", "k_mid.cu", "k_large.cu", "k_multi_sgp.cu", "k_multi_rest.cu", "runtime.cu", "warmstart.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-Wno-deprecated-gpu-targets"]
@@ -34,7 +34,7 @@ def nvcc() -> str:
 
 def _headers_mtime(unit: str) -> float:
     hs = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
-    if unit == "runtime.cu":
+    if unit in ("runtime.cu", "warmstart.cu"):
         hs += glob.glob(os.path.join(HERE, "..", "include", "*.h"))
     return max(os.path.getmtime(h) for h in hs)
 

@@ -99,9 +99,12 @@ def load() -> C.CDLL:
 
 
 def header_symbols() -> list[str]:
-    """Names of the entry points declared in include/sgp.h."""
-    txt = open(HEADER).read()
-    return re.findall(r"SGP_API\s+[\w\s\*]+?\b(\w+)\s*\(", txt)
+    """Names of the entry points declared in include/sgp.h and include/warmstart.h."""
+    names = []
+    for h, tag in ((HEADER, "SGP_API"), (os.path.join(os.path.dirname(HEADER), "warmstart.h"), "WS_API")):
+        txt = open(h).read()
+        names += re.findall(tag + r"\s+[\w\s\*]+?\b(\w+)\s*\(", txt)
+    return names
 
 
 class SGPError(RuntimeError):
