@@ -14,8 +14,9 @@
  *   s5 = up2(a4) + a2                                       ws_up2_add
  *   a5 = relu(conv(s5))                                     ws_conv32 mode 0
  *   z  = conv_out(a5)                 32 -> 1, linear       ws_conv_out
- *   f0 = s expm1(max(z, 0))                                 ws_start
- * Training target t = log(1 + max(f_SGP, 0)/s), loss mean (z - t)^2 (ws_loss).
+ *   f0 = s expm1(max(z + log(1 + max(x0, 0)), 0))           ws_start
+ * The network predicts a correction to the log-transformed data: training target
+ * t = log(1 + max(f_SGP, 0)/s) - log(1 + max(x0, 0)), loss mean (z - t)^2 (ws_loss).
  *
  * Layouts: conv32 weights bf16 [co][tap][ci] (tap = 3 dy + dx), conv_in weights fp32 [co][tap],
  * conv_out weights fp32 [tap][ci]; activations bf16 [b][y][x][c]; every 3x3 convolution uses zero
@@ -76,11 +77,16 @@ WS_API int ws_loss(const float* z, const float* t, float* dz, double* out, size_
 WS_API int ws_adam(float* p, float* m, float* v, const float* g, int n, float lr, float b1, float b2, float eps,
                    int step, void* stream);
 WS_API int ws_to_bf16(const float* x, void* y, int n, void* stream);
-/* x = (g - b)/s and (if f != NULL) t = log(1 + max(f, 0)/s); b and s per image (B values) */
+/* x = (g - b)/s and (if f != NULL) t = log(1 + max(f, 0)/s) - log(1 + max(x, 0)); b, s per image */
 WS_API int ws_prep(const float* g, const float* f, const float* b, const float* s, float* x, float* t, int B,
                    size_t P, void* stream);
-/* f0 = s expm1(max(z, 0)) */
-WS_API int ws_start(const float* z, const float* s, float* f0, int B, size_t P, void* stream);
+/* f0 = s expm1(max(z + log(1 + max(x, 0)), 0)) */
+WS_API int ws_start(const float* z, const float* x, const float* s, float* f0, int B, size_t P, void* stream);
+
+/* s[b] = 1 + mean over the image of max(g - b, 0): the per-image input scale */
+WS_API int ws_scale(const float* g, const float* b, float* s, int B, size_t P, void* stream);
+/* zero `bytes` bytes at p (gradient accumulators) */
+WS_API int ws_zero(void* p, size_t bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -409,23 +409,43 @@ __global__ void k_to_bf16(const float* __restrict__ x, bf16* __restrict__ y, int
   if (i < n) y[i] = __float2bfloat16(x[i]);
 }
 
-// input normalisation x = (g - b) / s and target t = log(1 + max(f, 0) / s), s per image
+// input normalisation x = (g - b) / s and target t = log(1 + max(f, 0) / s) - log(1 + max(x, 0)):
+// the network predicts a correction to the log-transformed data (s per image)
 __global__ void k_prep(const float* __restrict__ g, const float* __restrict__ f, const float* __restrict__ bvec,
                        const float* __restrict__ svec, float* __restrict__ x, float* __restrict__ t, int B, size_t P) {
   const size_t n = size_t(B) * P;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
     const size_t bb = i / P;
     const float s = svec[bb];
-    x[i] = (g[i] - bvec[bb]) / s;
-    if (f) t[i] = log1pf(fmaxf(f[i], 0.0f) / s);
+    const float xi = (g[i] - bvec[bb]) / s;
+    x[i] = xi;
+    if (f) t[i] = log1pf(fmaxf(f[i], 0.0f) / s) - log1pf(fmaxf(xi, 0.0f));
   }
 }
 
-// f0 = s expm1(max(z, 0)) (the inverse of the target transform)
-__global__ void k_start(const float* __restrict__ z, const float* __restrict__ svec, float* __restrict__ f0, int B, size_t P) {
+// f0 = s expm1(max(z + log(1 + max(x, 0)), 0)) (the inverse of the target transform)
+__global__ void k_start(const float* __restrict__ z, const float* __restrict__ x, const float* __restrict__ svec,
+                        float* __restrict__ f0, int B, size_t P) {
   const size_t n = size_t(B) * P;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
-    f0[i] = svec[i / P] * expm1f(fmaxf(z[i], 0.0f));
+    f0[i] = svec[i / P] * expm1f(fmaxf(z[i] + log1pf(fmaxf(x[i], 0.0f)), 0.0f));
+}
+
+// s[b] = 1 + mean over the image of max(g - b, 0) (input scale of the network), one block per image
+__global__ void __launch_bounds__(256) k_scale(const float* __restrict__ g, const float* __restrict__ bvec,
+                                              float* __restrict__ s, size_t P) {
+  const float* gb = g + size_t(blockIdx.x) * P;
+  const float bb = bvec[blockIdx.x];
+  double acc = 0.0;
+  for (size_t i = threadIdx.x; i < P; i += blockDim.x) acc += fmaxf(gb[i] - bb, 0.0f);
+  __shared__ double r[256];
+  r[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) r[threadIdx.x] += r[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) s[blockIdx.x] = float(1.0 + r[0] / double(P));
 }
 
 int grid1(size_t n) {
@@ -548,9 +568,18 @@ int ws_prep(const float* g, const float* f, const float* b, const float* s, floa
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
 }
 
-int ws_start(const float* z, const float* s, float* f0, int B, size_t P, void* stream) {
-  k_start<<<grid1(size_t(B) * P), 256, 0, static_cast<cudaStream_t>(stream)>>>(z, s, f0, B, P);
+int ws_start(const float* z, const float* x, const float* s, float* f0, int B, size_t P, void* stream) {
+  k_start<<<grid1(size_t(B) * P), 256, 0, static_cast<cudaStream_t>(stream)>>>(z, x, s, f0, B, P);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
+}
+
+int ws_scale(const float* g, const float* b, float* s, int B, size_t P, void* stream) {
+  k_scale<<<B, 256, 0, static_cast<cudaStream_t>(stream)>>>(g, b, s, P);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
+}
+
+int ws_zero(void* p, size_t bytes, void* stream) {
+  return cudaMemsetAsync(p, 0, bytes, static_cast<cudaStream_t>(stream)) == cudaSuccess ? 0 : 4;
 }
 
 }  // extern "C"

@@ -1,0 +1,315 @@
+"""Learned warm start for SGP: a small BF16 convolutional encoder-decoder that predicts f^(0) from g.
+
+Architecture, layouts and kernels: include/warmstart.h.  This module only allocates tensors
+(PyTorch supplies device memory), marshals arguments and sequences the library kernels; every
+numeric step (convolutions, their gradients, pooling, loss, Adam, normalisation, the SGP solves that
+produce the training targets) runs in the library.  SGP always refines the predicted start to the
+same stopping rule as the flat start.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import time
+
+import numpy as np
+
+from . import scenes
+from . import sgp as lib
+
+PARAMS = [("w1", 32 * 9), ("b1", 32)] + \
+    [(f"{k}{i}", n) for i in range(2, 6) for k, n in (("w", 32 * 9 * 32), ("b", 32))] + [("w6", 9 * 32), ("b6", 1)]
+CONV32 = ["w2", "w3", "w4", "w5"]
+
+_ws = None
+
+
+def _lib():
+    global _ws
+    if _ws is not None:
+        return _ws
+    L = lib.load()
+    vp, i, sz, f = C.c_void_p, C.c_int, C.c_size_t, C.c_float
+    sig = {
+        "ws_conv32": [vp, vp, vp, vp, vp, i, i, i, i, vp],
+        "ws_conv32_wgrad": [vp, vp, vp, i, i, i, vp],
+        "ws_flip_weights": [vp, vp, vp],
+        "ws_conv_in": [vp, vp, vp, vp, i, i, i, vp],
+        "ws_conv_out": [vp, vp, vp, vp, i, i, i, vp],
+        "ws_conv_out_dgrad": [vp, vp, vp, vp, i, i, i, vp],
+        "ws_small_wgrad": [vp, vp, vp, vp, i, i, i, i, vp],
+        "ws_bias_grad": [vp, vp, i, i, i, vp],
+        "ws_pool2": [vp, vp, i, i, i, vp],
+        "ws_up2_add": [vp, vp, vp, i, i, i, vp],
+        "ws_junction_bwd": [vp, vp, vp, vp, i, i, i, vp],
+        "ws_up2_bwd_mask": [vp, vp, vp, i, i, i, vp],
+        "ws_loss": [vp, vp, vp, vp, sz, vp],
+        "ws_adam": [vp, vp, vp, vp, i, f, f, f, f, i, vp],
+        "ws_to_bf16": [vp, vp, i, vp],
+        "ws_prep": [vp, vp, vp, vp, vp, vp, i, sz, vp],
+        "ws_start": [vp, vp, vp, vp, i, sz, vp],
+        "ws_scale": [vp, vp, vp, i, sz, vp],
+        "ws_zero": [vp, sz, vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.restype = C.c_int
+        fn.argtypes = args
+    _ws = L
+    return L
+
+
+def _ok(rc: int, what: str) -> None:
+    if rc != 0:
+        raise RuntimeError(f"{what} failed with code {rc}")
+
+
+def _p(t):
+    return None if t is None else t.data_ptr()
+
+
+class WarmStartNet:
+    """Parameters live in one FP32 buffer (master copy) with Adam moments and a gradient buffer;
+    the 32 -> 32 layers also keep bf16 working copies and their flipped (transposed) copies."""
+
+    def __init__(self, seed: int = 0, device: str = "cuda"):
+        import torch
+        self.torch = torch
+        self.dev = torch.device(device)
+        self.off = {}
+        o = 0
+        for name, n in PARAMS:
+            self.off[name] = (o, n)
+            o += n
+        self.n = o
+        rng = np.random.default_rng(seed)
+        host = np.zeros(o, np.float32)
+        for name, n in PARAMS:
+            a, _ = self.off[name]
+            if name.startswith("w"):
+                fan_in = 9 if name == "w1" else 288
+                std = math.sqrt(2.0 / fan_in) * (0.1 if name == "w6" else 1.0)
+                host[a:a + n] = rng.standard_normal(n) * std
+        self.p = torch.from_numpy(host).to(self.dev)
+        self.g = torch.zeros(o, dtype=torch.float32, device=self.dev)
+        self.m = torch.zeros_like(self.g)
+        self.v = torch.zeros_like(self.g)
+        self.wb = {k: torch.empty(32 * 9 * 32, dtype=torch.bfloat16, device=self.dev) for k in CONV32}
+        self.wt = {k: torch.empty(32 * 9 * 32, dtype=torch.bfloat16, device=self.dev) for k in CONV32}
+        self.t = 0
+        self._bufs = {}
+        self.sync_weights()
+
+    # ------------------------------------------------------------------ helpers
+    def stream(self):
+        return self.torch.cuda.current_stream().cuda_stream
+
+    def view(self, buf, name):
+        a, n = self.off[name]
+        return buf[a:a + n]
+
+    def set_params(self, params: dict) -> None:
+        """Load parameters given as numpy arrays in the layouts of include/warmstart.h."""
+        host = self.p.cpu().numpy()
+        for name, arr in params.items():
+            a, n = self.off[name]
+            host[a:a + n] = np.asarray(arr, np.float32).reshape(-1)
+        self.p.copy_(self.torch.from_numpy(host))
+        self.sync_weights()
+
+    def params(self) -> dict:
+        host = self.p.cpu().numpy()
+        return {name: host[a:a + n].copy() for name, (a, n) in self.off.items()}
+
+    def sync_weights(self) -> None:
+        L, s = _lib(), self.stream()
+        for k in CONV32:
+            _ok(L.ws_to_bf16(_p(self.view(self.p, k)), _p(self.wb[k]), 32 * 288, s), "to_bf16")
+            _ok(L.ws_flip_weights(_p(self.wb[k]), _p(self.wt[k]), s), "flip")
+
+    def buffers(self, B, H, W):
+        key = (B, H, W)
+        if key not in self._bufs:
+            t, d = self.torch, self.dev
+            full = (B, H, W, 32)
+            half = (B, H // 2, W // 2, 32)
+            bf = t.bfloat16
+            self._bufs[key] = dict(
+                x0=t.empty((B, H, W), dtype=t.float32, device=d), tgt=t.empty((B, H, W), dtype=t.float32, device=d),
+                s=t.empty(B, dtype=t.float32, device=d), b=t.empty(B, dtype=t.float32, device=d),
+                a1=t.empty(full, dtype=bf, device=d), a2=t.empty(full, dtype=bf, device=d),
+                p2=t.empty(half, dtype=bf, device=d), a3=t.empty(half, dtype=bf, device=d),
+                a4=t.empty(half, dtype=bf, device=d), s5=t.empty(full, dtype=bf, device=d),
+                a5=t.empty(full, dtype=bf, device=d), z=t.empty((B, H, W), dtype=t.float32, device=d),
+                dz=t.empty((B, H, W), dtype=t.float32, device=d), d5=t.empty(full, dtype=bf, device=d),
+                ds5=t.empty(full, dtype=bf, device=d), dz4=t.empty(half, dtype=bf, device=d),
+                dz3=t.empty(half, dtype=bf, device=d), dp2=t.empty(half, dtype=bf, device=d),
+                dz2=t.empty(full, dtype=bf, device=d), dz1=t.empty(full, dtype=bf, device=d),
+                loss=t.zeros(1, dtype=t.float64, device=d))
+        return self._bufs[key]
+
+    # ------------------------------------------------------------------ passes
+    def prepare(self, g, b, f=None):
+        """x0 = (g - b)/s and (with f) the training target; g, f (B, H, W) fp32 CUDA, b (B,) fp32 CUDA."""
+        L, s = _lib(), self.stream()
+        B, H, W = g.shape
+        bf = self.buffers(B, H, W)
+        bf["b"].copy_(b)
+        _ok(L.ws_scale(_p(g), _p(bf["b"]), _p(bf["s"]), B, H * W, s), "scale")
+        _ok(L.ws_prep(_p(g), _p(f), _p(bf["b"]), _p(bf["s"]), _p(bf["x0"]), _p(bf["tgt"]), B, H * W, s), "prep")
+        return bf
+
+    def forward(self, bf, B, H, W):
+        L, s, P = _lib(), self.stream(), self.p
+        v = lambda k: _p(self.view(P, k))
+        _ok(L.ws_conv_in(_p(bf["x0"]), v("w1"), v("b1"), _p(bf["a1"]), B, H, W, s), "conv_in")
+        _ok(L.ws_conv32(_p(bf["a1"]), _p(self.wb["w2"]), v("b2"), None, _p(bf["a2"]), B, H, W, 0, s), "conv2")
+        _ok(L.ws_pool2(_p(bf["a2"]), _p(bf["p2"]), B, H, W, s), "pool")
+        _ok(L.ws_conv32(_p(bf["p2"]), _p(self.wb["w3"]), v("b3"), None, _p(bf["a3"]), B, H // 2, W // 2, 0, s), "conv3")
+        _ok(L.ws_conv32(_p(bf["a3"]), _p(self.wb["w4"]), v("b4"), None, _p(bf["a4"]), B, H // 2, W // 2, 0, s), "conv4")
+        _ok(L.ws_up2_add(_p(bf["a4"]), _p(bf["a2"]), _p(bf["s5"]), B, H, W, s), "up")
+        _ok(L.ws_conv32(_p(bf["s5"]), _p(self.wb["w5"]), v("b5"), None, _p(bf["a5"]), B, H, W, 0, s), "conv5")
+        _ok(L.ws_conv_out(_p(bf["a5"]), v("w6"), v("b6"), _p(bf["z"]), B, H, W, s), "conv_out")
+        return bf["z"]
+
+    def backward(self, bf, B, H, W):
+        """Accumulate parameter gradients of the loss (dz in bf['dz']) into self.g."""
+        L, s, P, G = _lib(), self.stream(), self.p, self.g
+        v = lambda buf, k: _p(self.view(buf, k))
+        h, w = H // 2, W // 2
+        _ok(L.ws_small_wgrad(_p(bf["dz"]), _p(bf["a5"]), v(G, "w6"), v(G, "b6"), B, H, W, 1, s), "wgrad6")
+        _ok(L.ws_conv_out_dgrad(_p(bf["dz"]), v(P, "w6"), _p(bf["a5"]), _p(bf["d5"]), B, H, W, s), "dgrad6")
+        # layer 5: input s5, output gradient dz5 = d5
+        _ok(L.ws_conv32_wgrad(_p(bf["d5"]), _p(bf["s5"]), v(G, "w5"), B, H, W, s), "wgrad5")
+        _ok(L.ws_bias_grad(_p(bf["d5"]), v(G, "b5"), B, H, W, s), "bgrad5")
+        _ok(L.ws_conv32(_p(bf["d5"]), _p(self.wt["w5"]), None, None, _p(bf["ds5"]), B, H, W, 3, s), "dgrad5")
+        _ok(L.ws_up2_bwd_mask(_p(bf["ds5"]), _p(bf["a4"]), _p(bf["dz4"]), B, H, W, s), "upbwd")
+        # layer 4 (half resolution): input a3
+        _ok(L.ws_conv32_wgrad(_p(bf["dz4"]), _p(bf["a3"]), v(G, "w4"), B, h, w, s), "wgrad4")
+        _ok(L.ws_bias_grad(_p(bf["dz4"]), v(G, "b4"), B, h, w, s), "bgrad4")
+        _ok(L.ws_conv32(_p(bf["dz4"]), _p(self.wt["w4"]), None, _p(bf["a3"]), _p(bf["dz3"]), B, h, w, 2, s), "dgrad4")
+        # layer 3: input p2
+        _ok(L.ws_conv32_wgrad(_p(bf["dz3"]), _p(bf["p2"]), v(G, "w3"), B, h, w, s), "wgrad3")
+        _ok(L.ws_bias_grad(_p(bf["dz3"]), v(G, "b3"), B, h, w, s), "bgrad3")
+        _ok(L.ws_conv32(_p(bf["dz3"]), _p(self.wt["w3"]), None, None, _p(bf["dp2"]), B, h, w, 3, s), "dgrad3")
+        _ok(L.ws_junction_bwd(_p(bf["ds5"]), _p(bf["dp2"]), _p(bf["a2"]), _p(bf["dz2"]), B, H, W, s), "junction")
+        # layer 2: input a1
+        _ok(L.ws_conv32_wgrad(_p(bf["dz2"]), _p(bf["a1"]), v(G, "w2"), B, H, W, s), "wgrad2")
+        _ok(L.ws_bias_grad(_p(bf["dz2"]), v(G, "b2"), B, H, W, s), "bgrad2")
+        _ok(L.ws_conv32(_p(bf["dz2"]), _p(self.wt["w2"]), None, _p(bf["a1"]), _p(bf["dz1"]), B, H, W, 2, s), "dgrad2")
+        # layer 1: input x0
+        _ok(L.ws_small_wgrad(_p(bf["dz1"]), _p(bf["x0"]), v(G, "w1"), v(G, "b1"), B, H, W, 0, s), "wgrad1")
+
+    def loss_and_grad(self, bf, B, H, W) -> None:
+        L, s = _lib(), self.stream()
+        _ok(L.ws_zero(_p(self.g), self.n * 4, s), "zero")
+        _ok(L.ws_zero(_p(bf["loss"]), 8, s), "zero")
+        self.forward(bf, B, H, W)
+        _ok(L.ws_loss(_p(bf["z"]), _p(bf["tgt"]), _p(bf["dz"]), _p(bf["loss"]), B * H * W, s), "loss")
+        self.backward(bf, B, H, W)
+
+    def adam(self, lr: float) -> None:
+        self.t += 1
+        _ok(_lib().ws_adam(_p(self.p), _p(self.m), _p(self.v), _p(self.g), self.n, lr, 0.9, 0.999, 1e-8, self.t,
+                           self.stream()), "adam")
+        self.sync_weights()
+
+    def predict(self, g, b):
+        """f0 (B, H, W) fp32 for detected images g (B, H, W) with backgrounds b (B,)."""
+        B, H, W = g.shape
+        bf = self.prepare(g, b)
+        self.forward(bf, B, H, W)
+        f0 = self.torch.empty_like(g)
+        _ok(_lib().ws_start(_p(bf["z"]), _p(bf["x0"]), _p(bf["s"]), _p(f0), B, H * W, self.stream()), "start")
+        return f0
+
+
+# ---------------------------------------------------------------------- data, training, evaluation
+def make_scenes(n: int, N: int, seed: int):
+    rng = scenes.rng_for(seed)
+    return [scenes.warmstart_scene(rng, N) for _ in range(n)]
+
+
+def sgp_solutions(scs, max_iter: int = 400, batch: int = 64):
+    """SGP from the flat start to the discrepancy stop for every scene (batched GPU solves).
+    Returns (g, f, b, iterations) as CUDA tensors / numpy."""
+    import torch
+    Hs = scs[0].g.shape[1]
+    g_all = torch.empty((len(scs), Hs, Hs), dtype=torch.float32, device="cuda")
+    f_all = torch.empty_like(g_all)
+    b_all = torch.tensor([float(s.b[0]) for s in scs], dtype=torch.float32, device="cuda")
+    its = np.zeros(len(scs), np.int64)
+    for a in range(0, len(scs), batch):
+        part = scs[a:a + batch]
+        probs = lib.Problems([torch.from_numpy(s.psfs.astype(np.float32)).cuda() for s in part],
+                             [[float(s.b[0])] for s in part])
+        for i, s in enumerate(part):
+            g = torch.from_numpy(s.g.astype(np.float32)).cuda()
+            probs.set_data(i, g)
+            g_all[a + i].copy_(g[0])
+        it = probs.solve_until(lib.STOP_DISCREPANCY, max_iter=max_iter, eta=1.0, raise_on_error=False)
+        for i in range(len(part)):
+            probs.get_f(i, out=f_all[a + i])
+        its[a:a + len(part)] = it
+        probs.close()
+    return g_all, f_all, b_all, its
+
+
+def train(net: WarmStartNet, g, f, b, epochs: int = 3, batch: int = 32, lr: float = 2e-3, seed: int = 0,
+          log=None) -> list[float]:
+    """Adam on the squared error of the log-domain correction; batches are contiguous slices of the
+    (pre-shuffled) data visited in a random order each epoch."""
+    import torch
+    n, H, W = g.shape
+    rng = np.random.default_rng(seed)
+    nb = n // batch
+    losses = []
+    for ep in range(epochs):
+        tot = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for k in rng.permutation(nb):
+            sl = slice(k * batch, (k + 1) * batch)
+            bf = net.prepare(g[sl], b[sl], f[sl])
+            net.loss_and_grad(bf, batch, H, W)
+            net.adam(lr * (0.5 ** ep))
+            tot += bf["loss"]
+        losses.append(float(tot.item()) / (nb * batch * H * W))
+        if log:
+            log(f"epoch {ep}: loss {losses[-1]:.4e}")
+    return losses
+
+
+def evaluate(net: WarmStartNet, scs, max_iter: int = 2000, batch: int = 50):
+    """Flat-start vs warm-start SGP to the same discrepancy stop: iterations, GPU time, final KL."""
+    import torch
+    out = {"flat_iters": [], "warm_iters": [], "flat_kl": [], "warm_kl": [], "flat_ms": 0.0, "warm_ms": 0.0,
+           "net_ms": 0.0}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for a in range(0, len(scs), batch):
+        part = scs[a:a + batch]
+        psf = [torch.from_numpy(s.psfs.astype(np.float32)).cuda() for s in part]
+        bc = [[float(s.b[0])] for s in part]
+        g = torch.stack([torch.from_numpy(s.g[0].astype(np.float32)) for s in part]).cuda()
+        bvec = torch.tensor([float(s.b[0]) for s in part], dtype=torch.float32, device="cuda")
+        for mode in ("flat", "warm"):
+            probs = lib.Problems(psf, bc)
+            for i in range(len(part)):
+                probs.set_data(i, g[i:i + 1])
+            torch.cuda.synchronize()
+            ev[0].record()
+            if mode == "warm":
+                f0 = net.predict(g, bvec)
+                ev[2].record()
+                for i in range(len(part)):
+                    probs.set_start(i, lib.START_USER, f0[i])
+            it = probs.solve_until(lib.STOP_DISCREPANCY, max_iter=max_iter, eta=1.0, raise_on_error=False)
+            ev[1].record()
+            torch.cuda.synchronize()
+            out[f"{mode}_ms"] += ev[0].elapsed_time(ev[1])
+            if mode == "warm":
+                out["net_ms"] += ev[0].elapsed_time(ev[2])
+            out[f"{mode}_iters"] += list(it)
+            out[f"{mode}_kl"] += [probs.info(i).J for i in range(len(part))]
+            probs.close()
+    for k in ("flat_iters", "warm_iters", "flat_kl", "warm_kl"):
+        out[k] = np.asarray(out[k])
+    return out
