@@ -313,3 +313,92 @@ def evaluate(net: WarmStartNet, scs, max_iter: int = 2000, batch: int = 50):
     for k in ("flat_iters", "warm_iters", "flat_kl", "warm_kl"):
         out[k] = np.asarray(out[k])
     return out
+
+
+def _scene_chunk(args):
+    n, N, seed = args
+    sc = make_scenes(n, N, seed)
+    return [(s.psfs.astype(np.float32), s.g.astype(np.float32), float(s.b[0])) for s in sc]
+
+
+def _light(items):
+    out = []
+    for psf, g, b in items:
+        out.append(scenes.Scene(psfs=psf, g=g, b=np.array([b]), f_true=None))
+    return out
+
+
+def generate(n: int, N: int, seed: int, workers: int = 0):
+    """n seeded scenes of side N, generated in parallel worker processes (spawned, before any GPU
+    work in them)."""
+    import multiprocessing as mp
+    import os
+    workers = workers or min(16, os.cpu_count() or 1)
+    chunk = max(1, n // (4 * workers))
+    jobs = [(min(chunk, n - a), N, seed * 100003 + a) for a in range(0, n, chunk)]
+    if workers <= 1:
+        res = [_scene_chunk(j) for j in jobs]
+    else:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            res = pool.map(_scene_chunk, jobs)
+    return _light([x for r in res for x in r])
+
+
+def main(argv=None) -> int:
+    """Train the warm start on SGP solutions and compare warm vs flat starts on held-out images.
+
+    python -m paper_1210_2258_b300.warmstart --train 20000 --train-side 256 --eval 1000 --eval-side 512
+    """
+    import argparse
+    import json
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=20000)
+    ap.add_argument("--train-side", type=int, default=256)
+    ap.add_argument("--eval", type=int, default=1000)
+    ap.add_argument("--eval-side", type=int, default=512)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--max-iter", type=int, default=400)
+    ap.add_argument("--save", default="")
+    a = ap.parse_args(argv)
+    log = lambda m: print(m, flush=True)
+    t0 = time.perf_counter()
+    tr = generate(a.train, a.train_side, seed=1)
+    ev_scenes = generate(a.eval, a.eval_side, seed=2)
+    t1 = time.perf_counter()
+    log(f"scenes: {len(tr)} train {a.train_side}^2, {len(ev_scenes)} eval {a.eval_side}^2 in {t1 - t0:.1f} s")
+    torch.cuda.synchronize()
+    g, f, b, its = sgp_solutions(tr, max_iter=a.max_iter)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    log(f"training targets: {len(tr)} SGP solves in {t2 - t1:.1f} s, mean iterations {its.mean():.1f}, "
+        f"stopped {np.mean(its < a.max_iter) * 100:.1f}%")
+    net = WarmStartNet(seed=0)
+    losses = train(net, g, f, b, epochs=a.epochs, batch=a.batch, lr=a.lr, log=log)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    res = evaluate(net, ev_scenes)
+    t4 = time.perf_counter()
+    done = (res["flat_iters"] < 2000) & (res["warm_iters"] < 2000)
+    kl_rel = np.abs(res["warm_kl"] - res["flat_kl"]) / res["flat_kl"]
+    summary = {
+        "train_pairs": len(tr), "train_side": a.train_side, "eval_images": len(ev_scenes), "eval_side": a.eval_side,
+        "target_solves_s": t2 - t1, "target_mean_iters": float(its.mean()), "train_s": t3 - t2,
+        "train_loss_first_last": [losses[0], losses[-1]],
+        "both_stopped": int(done.sum()),
+        "flat_mean_iters": float(res["flat_iters"][done].mean()), "warm_mean_iters": float(res["warm_iters"][done].mean()),
+        "flat_gpu_ms_total": res["flat_ms"], "warm_gpu_ms_total": res["warm_ms"], "net_ms_total": res["net_ms"],
+        "final_kl_rel_diff_median": float(np.median(kl_rel[done])), "final_kl_rel_diff_max": float(np.max(kl_rel[done])),
+        "eval_s": t4 - t3,
+    }
+    log(json.dumps(summary))
+    if a.save:
+        np.savez(a.save, **net.params())
+    return 0
+
+
+if __name__ == "__main__":
+    import sys
+    sys.exit(main())
