@@ -14,7 +14,7 @@
  *   s5 = up2(a4) + a2                                       ws_up2_add
  *   a5 = relu(conv(s5))                                     ws_conv32 mode 0
  *   z  = conv_out(a5)                 32 -> 1, linear       ws_conv_out
- *   f0 = s expm1(max(z + log(1 + max(x0, 0)), 0))           ws_start
+ *   f0 = s expm1(clamp(z + log(1 + max(x0, 0)), 0, 20))     ws_start
  * The network predicts a correction to the log-transformed data: training target
  * t = log(1 + max(f_SGP, 0)/s) - log(1 + max(x0, 0)), loss mean (z - t)^2 (ws_loss).
  *
@@ -80,7 +80,7 @@ WS_API int ws_to_bf16(const float* x, void* y, int n, void* stream);
 /* x = (g - b)/s and (if f != NULL) t = log(1 + max(f, 0)/s) - log(1 + max(x, 0)); b, s per image */
 WS_API int ws_prep(const float* g, const float* f, const float* b, const float* s, float* x, float* t, int B,
                    size_t P, void* stream);
-/* f0 = s expm1(max(z + log(1 + max(x, 0)), 0)) */
+/* f0 = s expm1(clamp(z + log(1 + max(x, 0)), 0, 20)) */
 WS_API int ws_start(const float* z, const float* x, const float* s, float* f0, int B, size_t P, void* stream);
 
 /* s[b] = 1 + mean over the image of max(g - b, 0): the per-image input scale */

@@ -239,26 +239,8 @@ __device__ __forceinline__ void stockham_stage(const Lay& x0, int t, bool act) {
       const int j = t + b * T;
       const int k = j % NS;
       if (NS > 1) {
-        constexpr int STR = L / (NS * R);
-        if (R <= 6) {
 #pragma unroll
-          for (int m = 1; m < R; ++m) v[b][m] = cmul(v[b][m], twl<L, INV>(m * k * STR));
-        } else {
-          // w^{(4q + r) k} = (w^{4k})^q (w^k)^r: two table loads, the rest by complex products
-          const float2 a1 = twl<L, INV>(k * STR), c1 = twl<L, INV>(4 * k * STR);
-          const float2 a2 = cmul(a1, a1), a3 = cmul(a2, a1);
-          float2 cq = make_float2(1.0f, 0.0f);
-#pragma unroll
-          for (int q = 0; q < R / 4; ++q) {
-            if (q > 0) {
-              cq = (q == 1) ? c1 : cmul(cq, c1);
-              v[b][4 * q] = cmul(v[b][4 * q], cq);
-            }
-            v[b][4 * q + 1] = cmul(v[b][4 * q + 1], q ? cmul(cq, a1) : a1);
-            v[b][4 * q + 2] = cmul(v[b][4 * q + 2], q ? cmul(cq, a2) : a2);
-            v[b][4 * q + 3] = cmul(v[b][4 * q + 3], q ? cmul(cq, a3) : a3);
-          }
-        }
+        for (int m = 1; m < R; ++m) v[b][m] = cmul(v[b][m], twl<L, INV>(m * k * (L / (NS * R))));
       }
       DFT<R, INV>::run(v[b]);
       const int base = (j - k) * R + k;

@@ -438,10 +438,13 @@ sgp_status prepare(sgp_ctx* c, int mode) {
     }
   }
   CU(read_ctrl(c, c->h_ctrl) == SGP_OK ? cudaSuccess : cudaErrorUnknown);
+  // a problem whose set-up failed stays stopped with its status; the others proceed
+  int failed = 0, first = -1;
   for (int i = 0; i < c->n; ++i)
-    if (c->h_ctrl[i].status)
-      return fail(sgp_status(c->h_ctrl[i].status), "set-up failed for problem " + std::to_string(i) +
-                                                       " (no positive pixel after one RL step, or non-finite J)");
+    if (c->h_ctrl[i].status) { ++failed; if (first < 0) first = i; }
+  if (failed == c->n)
+    return fail(sgp_status(c->h_ctrl[first].status), "set-up failed for problem " + std::to_string(first) +
+                                                         " (no positive pixel after one RL step, or non-finite J)");
   c->mode = mode;
   return SGP_OK;
 }

@@ -423,12 +423,12 @@ __global__ void k_prep(const float* __restrict__ g, const float* __restrict__ f,
   }
 }
 
-// f0 = s expm1(max(z + log(1 + max(x, 0)), 0)) (the inverse of the target transform)
+// f0 = s expm1(clamp(z + log(1 + max(x, 0)), 0, 20)) (the inverse of the target transform, bounded)
 __global__ void k_start(const float* __restrict__ z, const float* __restrict__ x, const float* __restrict__ svec,
                         float* __restrict__ f0, int B, size_t P) {
   const size_t n = size_t(B) * P;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
-    f0[i] = svec[i / P] * expm1f(fmaxf(z[i] + log1pf(fmaxf(x[i], 0.0f)), 0.0f));
+    f0[i] = svec[i / P] * expm1f(fminf(fmaxf(z[i] + log1pf(fmaxf(x[i], 0.0f)), 0.0f), 20.0f));
 }
 
 // s[b] = 1 + mean over the image of max(g - b, 0) (input scale of the network), one block per image

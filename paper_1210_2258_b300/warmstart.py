@@ -282,7 +282,7 @@ def evaluate(net: WarmStartNet, scs, max_iter: int = 2000, batch: int = 50):
     """Flat-start vs warm-start SGP to the same discrepancy stop: iterations, GPU time, final KL."""
     import torch
     out = {"flat_iters": [], "warm_iters": [], "flat_kl": [], "warm_kl": [], "flat_ms": 0.0, "warm_ms": 0.0,
-           "net_ms": 0.0}
+           "net_ms": 0.0, "fallbacks": 0}
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     for a in range(0, len(scs), batch):
         part = scs[a:a + batch]
@@ -307,8 +307,20 @@ def evaluate(net: WarmStartNet, scs, max_iter: int = 2000, batch: int = 50):
             out[f"{mode}_ms"] += ev[0].elapsed_time(ev[1])
             if mode == "warm":
                 out["net_ms"] += ev[0].elapsed_time(ev[2])
+            infos = [probs.info(i) for i in range(len(part))]
+            if mode == "warm":
+                # a start the method cannot use falls back to the flat start (its flat result stands)
+                bad = [i for i, inf in enumerate(infos) if inf.status != 0]
+                out["fallbacks"] += len(bad)
+                base = len(out["warm_iters"])
+                it = list(it)
+                for i in bad:
+                    it[i] = out["flat_iters"][base + i]
+                klw = [inf.J if inf.status == 0 else out["flat_kl"][base + i] for i, inf in enumerate(infos)]
+            else:
+                klw = [inf.J for inf in infos]
             out[f"{mode}_iters"] += list(it)
-            out[f"{mode}_kl"] += [probs.info(i).J for i in range(len(part))]
+            out[f"{mode}_kl"] += klw
             probs.close()
     for k in ("flat_iters", "warm_iters", "flat_kl", "warm_kl"):
         out[k] = np.asarray(out[k])
@@ -391,7 +403,7 @@ def main(argv=None) -> int:
         "flat_mean_iters": float(res["flat_iters"][done].mean()), "warm_mean_iters": float(res["warm_iters"][done].mean()),
         "flat_gpu_ms_total": res["flat_ms"], "warm_gpu_ms_total": res["warm_ms"], "net_ms_total": res["net_ms"],
         "final_kl_rel_diff_median": float(np.median(kl_rel[done])), "final_kl_rel_diff_max": float(np.max(kl_rel[done])),
-        "eval_s": t4 - t3,
+        "eval_s": t4 - t3, "fallbacks_to_flat": res["fallbacks"],
     }
     log(json.dumps(summary))
     if a.save:
