@@ -33,10 +33,11 @@ FALLBACK_HBM_GBS = 6400.0
 # plane (single view): K1 reads f, grad, A f, A d, g and writes f, A f, the ratio spectrum; the
 # column passes read a spectrum and the PSF spectrum and write a spectrum; K3 reads the spectrum,
 # f, f_prev, grad_prev and writes grad; K4 reads f, grad and writes a spectrum; K6 reads the
-# spectrum, A f, g and writes A d.  Controllers move O(1) bytes.
-PASS_NAMES = ["update_ratio", "col_AT", "grad_bb", "ctrl_alpha", "proj_y", "col_A", "ad_armijo",
-              "ctrl_lambda", "armijo_extra", "ctrl_extra"]
-PASS_PLANES = [8, 3, 5, 0, 3, 3, 4, 0, 0, 0]
+# spectrum, A f, g and writes A d.  The controllers run in the last block of K1, K3, K6 and the
+# extra Armijo pass and move O(1) bytes; the extra pass returns at once unless no step length of
+# the main pass was accepted (it then reads A f, A d, g), so it is counted as 0.
+PASS_NAMES = ["update_ratio", "col_AT", "grad_bb", "proj_y", "col_A", "ad_armijo", "armijo_extra"]
+PASS_PLANES = [8, 3, 5, 3, 3, 4, 0]
 
 
 def parse():

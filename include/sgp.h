@@ -192,10 +192,12 @@ SGP_API sgp_status sgp_apply_A(sgp_ctx* ctx, int image, const float* f, float* o
 SGP_API sgp_status sgp_apply_AT(sgp_ctx* ctx, int image, const float* y, float* out);
 
 /* Measurement aid: run `iters` SGP iterations launching each pass separately, bracketed by CUDA
- * events on the library's stream, and return the mean duration in ms of the 10 passes of an
- * iteration in ms_out[0..9]: K1 update+ratio, column A^T, K3 gradient+BB, step-length controller,
- * K4 projection, column A, K6 A d + Armijo, line-search controller, extra Armijo, extra controller.
- * The iterations advance the state; the next solve restarts from the current iterate. */
+ * events on the library's stream, and return the mean duration in ms of the 7 passes of an
+ * iteration in ms_out[0..6]: K1 update + ratio (+ iteration controller), column A^T, K3 gradient +
+ * BB sums (+ step-length controller), K4 projection, column A, K6 A d + Armijo (+ line-search
+ * controller), extra Armijo (+ its controller; returns at once unless needed).  n_out >= 7;
+ * SGP_ERR_ARG for a flux-constrained context.  The iterations advance the state; the next solve
+ * restarts from the current iterate. */
 SGP_API sgp_status sgp_time_passes(sgp_ctx* ctx, int iters, double* ms_out, int n_out);
 
 /* Number of kernels this context has enqueued so far (graph launches count their nodes). */

@@ -19,7 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(LIBDIR, "libsgp_b300.so")
-UNITS = ["k_small.cu", "k_mid.cu", "k_large.cu", "k_multi_sgp.cu", "k_multi_rest.cu", "runtime.cu", "warmstart.cu"]
+UNITS = ["k_small.cu", "k_mid.cu", "k_large.cu", "k_multi_sgp_a.cu", "k_multi_sgp_b.cu", "k_multi_rest.cu", "runtime.cu",
+         "warmstart.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-Wno-deprecated-gpu-targets"]

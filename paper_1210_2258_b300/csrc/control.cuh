@@ -1,0 +1,225 @@
+// Scalar decisions of the methods, taken on the device by the block that finishes a row pass last
+// (see arrive_last), so an iteration never waits on the host and needs no controller launch.
+// Every function is called by all threads of that block; thread 0 takes the decisions.
+//   ctrl_sgp_begin         after K1: k <- k+1 once the pending update is applied, J_0 (Eq. KL),
+//                          min-error rule, completion of a decided stop
+//   ctrl_sgp_alpha         after K3: step 1 of Alg. 1, scaled BB values (Eq. BB1, BB2), the
+//                          safeguards, the alternation of Eq. (alphadef) with the M_alpha window
+//                          and tau, warm-up rule
+//   ctrl_sgp_lambda        after K6: step 5 of Alg. 1, first lambda in {1, theta, theta^2,
+//                          theta^3} with J(f + lambda d) <= J(f) + beta lambda grad'd; stop rules
+//                          of Sect. 3.3
+//   ctrl_sgp_lambda_extra  after K7: theta^4 .. theta^30 when needed
+//   ctrl_rl                after the RL ratio pass: Richardson-Lucy bookkeeping (J, trace, stops)
+#pragma once
+#include <math.h>
+#include "reduce.cuh"
+#include "state.cuh"
+
+namespace sgp {
+
+__device__ inline void trace_push(const ImgDesc& d, CtrlState* c, double k, double J, double alpha,
+                                  double lam, int bt, int branch, double gTd) {
+  if (c->trace_n < c->trace_cap) {
+    double* r = d.trace + size_t(c->trace_n) * kTraceStride;
+    r[0] = k; r[1] = J; r[2] = 2.0 * J * c->inv_pS; r[3] = alpha; r[4] = lam;
+    r[5] = bt; r[6] = branch; r[7] = gTd;
+  }
+  c->trace_n += 1;
+}
+
+// Step 1 of Alg. 1 for k >= 1 (V = double, or float for the plain-FP32 variant).
+template <class V>
+__device__ inline double bb_alpha(CtrlState* c, V n1, V d1, V n2, V d2, int k) {
+  const V amin = V(c->alpha_min), amax = V(c->alpha_max), aprev = V(c->alpha);
+  V a1, a2;
+  if (d1 <= V(0)) a1 = fmin(V(10) * aprev, amax);
+  else a1 = fmin(amax, fmax(amin, n1 / d1));
+  if (n2 <= V(0)) a2 = fmin(V(10) * aprev, amax);
+  else a2 = fmin(amax, fmax(amin, n2 / d2));
+  // window of the last M_alpha values of alpha^(2), Eq. (alphadef)
+  if (c->hist_n < c->M_alpha) c->hist[c->hist_n++] = double(a2);
+  else {
+    for (int i = 1; i < c->M_alpha; ++i) c->hist[i - 1] = c->hist[i];
+    c->hist[c->M_alpha - 1] = double(a2);
+  }
+  V wmin = V(c->hist[0]);
+  for (int i = 1; i < c->hist_n; ++i) wmin = fmin(wmin, V(c->hist[i]));
+  V alpha;
+  if (k <= c->warmup) { alpha = wmin; c->branch = 2; }
+  else if (a2 / a1 <= V(c->tau)) { alpha = wmin; c->tau *= 0.9; c->branch = 2; }
+  else { alpha = a1; c->tau *= 1.1; c->branch = 1; }
+  return double(alpha);
+}
+
+// The controller's working copy of the state: every thread loads one 8-byte word of it (in flight
+// while the partial sums are read), thread 0 decides on the shared copy, the block writes it back.
+constexpr int kCtrlWords = int(sizeof(CtrlState) / 8);
+static_assert(sizeof(CtrlState) % 8 == 0 && kCtrlWords <= kCtrlBlock && kCtrlWords <= kRowBlock,
+              "controller state must fit one word per thread");
+struct CtrlCopy {
+  unsigned long long w = 0ull;
+  __device__ __forceinline__ explicit CtrlCopy(const CtrlState* c) {
+    if (threadIdx.x < kCtrlWords) w = __ldcg(reinterpret_cast<const unsigned long long*>(c) + threadIdx.x);
+  }
+  __device__ __forceinline__ void to_shared(CtrlState& s) const {
+    if (threadIdx.x < kCtrlWords) reinterpret_cast<unsigned long long*>(&s)[threadIdx.x] = w;
+    __syncthreads();
+  }
+  __device__ __forceinline__ static void write_back(const CtrlState& s, CtrlState* c) {
+    __syncthreads();
+    if (threadIdx.x < kCtrlWords)
+      reinterpret_cast<unsigned long long*>(c)[threadIdx.x] = reinterpret_cast<const unsigned long long*>(&s)[threadIdx.x];
+  }
+};
+
+template <bool FP64>
+__device__ void sgp_begin_decide(CtrlState* c, const double (&kl)[2]) {
+  const int done = c->done;
+  if (!c->fresh) { c->k += 1; c->fresh = 1; }
+  if (done == 1) { c->done = 2; c->J = c->J_pred; return; }
+  if (!isfinite(kl[0])) { c->status = 8; c->done = 2; return; }
+  c->J = kl[0];
+  if (c->stop_kind == STOP_MIN_ERROR && c->ftrue_norm2 > 0.0) {
+    const double rho = sqrt(kl[1] / c->ftrue_norm2);
+    c->rho = rho;
+    if (c->k >= 1 && rho > c->rho_prev) { c->done = 2; c->result_prev = 1; return; }
+    c->rho_prev = rho;
+  }
+}
+// (with done == 1 the KL partials were not written by this pass: the sums are not used)
+template <bool FP64>
+__device__ void ctrl_sgp_begin(const ImgDesc& d) {
+  __shared__ CtrlState s;
+  const CtrlCopy cp(d.ctrl);
+  double kl[2];
+  ctrl_sum<2, FP64>(d, SLOT_KL, kl, true);
+  cp.to_shared(s);
+  if (threadIdx.x == 0) sgp_begin_decide<FP64>(&s, kl);
+  CtrlCopy::write_back(s, d.ctrl);
+}
+
+template <bool FP64>
+__device__ void sgp_alpha_decide(CtrlState* c, const double (&bb)[4]) {
+  double alpha;
+  if (c->k == 0) {
+    alpha = c->alpha0;
+    c->branch = 0;
+  } else if (FP64) {
+    alpha = bb_alpha<double>(c, bb[0], bb[1], bb[2], bb[3], c->k);
+  } else {
+    alpha = bb_alpha<float>(c, float(bb[0]), float(bb[1]), float(bb[2]), float(bb[3]), c->k);
+  }
+  c->alpha = alpha;
+}
+template <bool FP64>
+__device__ void ctrl_sgp_alpha(const ImgDesc& d) {
+  __shared__ CtrlState s;
+  const CtrlCopy cp(d.ctrl);
+  double bb[4];
+  ctrl_sum<4, FP64>(d, SLOT_BB, bb, false);
+  cp.to_shared(s);
+  if (threadIdx.x == 0) sgp_alpha_decide<FP64>(&s, bb);
+  CtrlCopy::write_back(s, d.ctrl);
+}
+
+__device__ inline void sgp_accept(const ImgDesc& d, CtrlState* c, int nb, double lam, double dJ) {
+  c->lambda = lam;
+  c->backtracks = nb;
+  c->dJ = dJ;
+  c->J_pred = c->J + dJ;
+  c->fresh = 0;                       // f^(k+1) = f^(k) + lambda d is applied by the next K1
+  c->need_more = 0;
+  const int kn = c->k + 1;
+  trace_push(d, c, kn, c->J_pred, c->alpha, lam, nb, c->branch, c->gTd);
+  bool stop = kn >= c->max_iter;
+  if (c->stop_kind == STOP_CONVERGENCE && fabs(c->J_pred - c->J) <= c->tol * c->J) stop = true;
+  if (c->stop_kind == STOP_DISCREPANCY && 2.0 * c->J_pred * c->inv_pS <= c->eta) stop = true;
+  if (stop) c->done = 1;
+}
+
+template <bool FP64>
+__device__ void sgp_lambda_decide(const ImgDesc& d, CtrlState* c, double gTd, const double (&arm)[kArmMain]) {
+  c->gTd = gTd;
+  if (!isfinite(gTd)) { c->status = 8; c->done = 2; return; }
+  double lam = 1.0;
+  for (int i = 0; i < kArmMain && i <= c->max_backtracks; ++i) {
+    const bool ok = FP64 ? (arm[i] <= c->beta * lam * gTd)
+                         : (float(arm[i]) <= float(c->beta) * float(lam) * float(gTd));
+    if (ok) { sgp_accept(d, c, i, lam, arm[i]); return; }
+    lam *= c->theta;
+  }
+  c->need_more = 1;
+}
+template <bool FP64>
+__device__ void ctrl_sgp_lambda(const ImgDesc& d) {
+  __shared__ CtrlState s;
+  const CtrlCopy cp(d.ctrl);
+  double g[1], arm[kArmMain];
+  ctrl_sum<1, FP64>(d, SLOT_GTD, g, false);
+  ctrl_sum<kArmMain, FP64>(d, SLOT_ARM, arm, true);
+  cp.to_shared(s);
+  if (threadIdx.x == 0) sgp_lambda_decide<FP64>(d, &s, g[0], arm);
+  CtrlCopy::write_back(s, d.ctrl);
+}
+
+template <bool FP64>
+__device__ void sgp_lambda_extra_decide(const ImgDesc& d, CtrlState* c, const double (&arm)[kArmExtra]) {
+  double lam = 1.0;
+  for (int i = 0; i < kArmMain; ++i) lam *= c->theta;
+  const double gTd = c->gTd;
+  for (int i = 0; i < kArmExtra && kArmMain + i <= c->max_backtracks; ++i) {
+    const bool ok = FP64 ? (arm[i] <= c->beta * lam * gTd)
+                         : (float(arm[i]) <= float(c->beta) * float(lam) * float(gTd));
+    if (ok) { sgp_accept(d, c, kArmMain + i, lam, arm[i]); return; }
+    lam *= c->theta;
+  }
+  c->need_more = 0;
+  c->status = 6;                      // line search failed: stop at f^(k)
+  c->done = 2;
+}
+template <bool FP64>
+__device__ void ctrl_sgp_lambda_extra(const ImgDesc& d) {
+  __shared__ CtrlState s;
+  const CtrlCopy cp(d.ctrl);
+  double arm[kArmExtra];
+  ctrl_sum<kArmExtra, FP64>(d, SLOT_ARMX, arm, false);
+  cp.to_shared(s);
+  if (threadIdx.x == 0) sgp_lambda_extra_decide<FP64>(d, &s, arm);
+  CtrlCopy::write_back(s, d.ctrl);
+}
+
+template <bool FP64>
+__device__ void rl_decide(const ImgDesc& d, CtrlState* c, double kl, double rr) {
+  const bool updated = c->have_v;
+  if (updated) c->k += 1;
+  c->have_v = 1;
+  // a stop skips the adjoint pass that follows, so v is not available to a resumed run
+  if (!isfinite(kl)) { c->status = 8; c->done = 2; c->have_v = 0; return; }
+  c->J_prev = c->J;
+  c->J = kl;
+  if (updated) trace_push(d, c, c->k, c->J, 0.0, 1.0, 0, 0, 0.0);
+  if (c->stop_kind == STOP_MIN_ERROR && c->ftrue_norm2 > 0.0) {
+    const double rho = sqrt(rr / c->ftrue_norm2);
+    c->rho = rho;
+    if (c->k >= 1 && rho > c->rho_prev) { c->done = 2; c->result_prev = 1; c->have_v = 0; return; }
+    c->rho_prev = rho;
+  }
+  bool stop = c->k >= c->max_iter;
+  if (updated && c->stop_kind == STOP_CONVERGENCE && fabs(c->J - c->J_prev) <= c->tol * c->J_prev) stop = true;
+  if (c->stop_kind == STOP_DISCREPANCY && 2.0 * c->J * c->inv_pS <= c->eta) stop = true;
+  if (stop) { c->done = 2; c->have_v = 0; }
+}
+template <bool FP64>
+__device__ void ctrl_rl(const ImgDesc& d) {
+  __shared__ CtrlState s;
+  const CtrlCopy cp(d.ctrl);
+  double kl[1], rr[1];
+  ctrl_sum<1, FP64>(d, SLOT_KL, kl, true);
+  ctrl_sum<1, FP64>(d, SLOT_RHO, rr, false);
+  cp.to_shared(s);
+  if (threadIdx.x == 0) rl_decide<FP64>(d, &s, kl[0], rr[0]);
+  CtrlCopy::write_back(s, d.ctrl);
+}
+
+}  // namespace sgp

@@ -1,221 +1,14 @@
-// Device-side controllers (one block per problem): they turn the partial sums of the row passes
-// into the scalar decisions of the methods, so an iteration never waits on the host.
-//   k_ctrl_alpha   step 1 of Alg. 1: scaled BB values (Eq. BB1, BB2), the safeguards, the
-//                  alternation of Eq. (alphadef) with the M_alpha window and tau, warm-up rule
-//   k_ctrl_lambda  step 5 of Alg. 1: first lambda in {1, theta, theta^2, theta^3} with
-//                  J(f + lambda d) <= J(f) + beta lambda grad'd; stop rules of Sect. 3.3
-//   k_ctrl_lambda_extra  lambda = theta^4 .. theta^30 when needed
-//   k_ctrl_rl      Richardson-Lucy bookkeeping (J, trace, stop rules)
+// Controller kernels outside the iteration (one block per problem) and the set-up and flux kernels.
+// The per-iteration controllers run inside the row passes (control.cuh).
 //   k_ctrl_setup   J_0 and the adaptive bounds L1, L2 of Sect. 3.2
+//   k_ctrl_arm     (re)arms the stop rule of every problem
+//   k_flux_pass / k_ctrl_flux  flux-constrained projection
 #pragma once
 #include <math.h>
 #include "rowops.cuh"
 #include "state.cuh"
 
 namespace sgp {
-
-// Sum NS slots over this problem's items (row list or row-view list); result on every thread.
-template <int NS, bool FP64>
-__device__ void ctrl_sum(const ImgDesc& d, int slot, double (&res)[NS], bool view_list) {
-  using V = typename Acc<FP64>::T;
-  __shared__ V red[NS][kCtrlBlock / 32];
-  V loc[NS];
-#pragma unroll
-  for (int s = 0; s < NS; ++s) loc[s] = V(0);
-  const int n = view_list ? d.n_rv_items : d.n_row_items;
-  const double* base = view_list ? d.partv : d.part;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double* p = base + size_t(i) * kPartStride + slot;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) loc[s] += V(p[s]);
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    const V v = warp_sum<V>(loc[s]);
-    if (lane == 0) red[s][wid] = v;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    V v = V(0);
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) v += red[s][w];   // fixed order: deterministic
-    res[s] = double(v);
-  }
-  __syncthreads();
-}
-
-__device__ inline void ctrl_minmax(const ImgDesc& d, double& mn, double& mx) {
-  __shared__ double rmn[kCtrlBlock / 32], rmx[kCtrlBlock / 32];
-  double a = INFINITY, b = 0.0;
-  for (int i = threadIdx.x; i < d.n_row_items; i += blockDim.x) {
-    const double* p = d.part + size_t(i) * kPartStride;
-    a = fmin(a, p[SLOT_MIN]);
-    b = fmax(b, p[SLOT_MAX]);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
-    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) { rmn[wid] = a; rmx[wid] = b; }
-  __syncthreads();
-  mn = INFINITY; mx = 0.0;
-  for (int w = 0; w < int(blockDim.x >> 5); ++w) { mn = fmin(mn, rmn[w]); mx = fmax(mx, rmx[w]); }
-  __syncthreads();
-}
-
-__device__ inline void trace_push(const ImgDesc& d, CtrlState* c, double k, double J, double alpha,
-                                  double lam, int bt, int branch, double gTd) {
-  if (c->trace_n < c->trace_cap) {
-    double* r = d.trace + size_t(c->trace_n) * kTraceStride;
-    r[0] = k; r[1] = J; r[2] = 2.0 * J * c->inv_pS; r[3] = alpha; r[4] = lam;
-    r[5] = bt; r[6] = branch; r[7] = gTd;
-  }
-  c->trace_n += 1;
-}
-
-// Step 1 of Alg. 1 for k >= 1 (V = double, or float for the plain-FP32 variant).
-template <class V>
-__device__ inline double bb_alpha(CtrlState* c, V n1, V d1, V n2, V d2, int k) {
-  const V amin = V(c->alpha_min), amax = V(c->alpha_max), aprev = V(c->alpha);
-  V a1, a2;
-  if (d1 <= V(0)) a1 = fmin(V(10) * aprev, amax);
-  else a1 = fmin(amax, fmax(amin, n1 / d1));
-  if (n2 <= V(0)) a2 = fmin(V(10) * aprev, amax);
-  else a2 = fmin(amax, fmax(amin, n2 / d2));
-  // window of the last M_alpha values of alpha^(2), Eq. (alphadef)
-  if (c->hist_n < c->M_alpha) c->hist[c->hist_n++] = double(a2);
-  else {
-    for (int i = 1; i < c->M_alpha; ++i) c->hist[i - 1] = c->hist[i];
-    c->hist[c->M_alpha - 1] = double(a2);
-  }
-  V wmin = V(c->hist[0]);
-  for (int i = 1; i < c->hist_n; ++i) wmin = fmin(wmin, V(c->hist[i]));
-  V alpha;
-  if (k <= c->warmup) { alpha = wmin; c->branch = 2; }
-  else if (a2 / a1 <= V(c->tau)) { alpha = wmin; c->tau *= 0.9; c->branch = 2; }
-  else { alpha = a1; c->tau *= 1.1; c->branch = 1; }
-  return double(alpha);
-}
-
-template <bool FP64>
-__global__ void __launch_bounds__(kCtrlBlock) k_ctrl_alpha(const ImgDesc* __restrict__ imgs) {
-  const ImgDesc& d = imgs[blockIdx.x];
-  CtrlState* c = d.ctrl;
-  if (c->done >= 2) return;
-  double kl[2], bb[4];
-  ctrl_sum<2, FP64>(d, SLOT_KL, kl, true);
-  ctrl_sum<4, FP64>(d, SLOT_BB, bb, false);
-  if (threadIdx.x != 0) return;
-  if (!c->fresh) { c->k += 1; c->fresh = 1; }
-  if (c->done == 1) { c->done = 2; c->J = c->J_pred; return; }
-  if (!isfinite(kl[0])) { c->status = 8; c->done = 2; return; }
-  c->J = kl[0];
-  if (c->stop_kind == STOP_MIN_ERROR && c->ftrue_norm2 > 0.0) {
-    const double rho = sqrt(kl[1] / c->ftrue_norm2);
-    c->rho = rho;
-    if (c->k >= 1 && rho > c->rho_prev) { c->done = 2; c->result_prev = 1; return; }
-    c->rho_prev = rho;
-  }
-  double alpha;
-  if (c->k == 0) {
-    alpha = c->alpha0;
-    c->branch = 0;
-  } else if (FP64) {
-    alpha = bb_alpha<double>(c, bb[0], bb[1], bb[2], bb[3], c->k);
-  } else {
-    alpha = bb_alpha<float>(c, float(bb[0]), float(bb[1]), float(bb[2]), float(bb[3]), c->k);
-  }
-  c->alpha = alpha;
-}
-
-__device__ inline void sgp_accept(const ImgDesc& d, CtrlState* c, int nb, double lam, double dJ) {
-  c->lambda = lam;
-  c->backtracks = nb;
-  c->dJ = dJ;
-  c->J_pred = c->J + dJ;
-  c->fresh = 0;                       // f^(k+1) = f^(k) + lambda d is applied by the next K1
-  c->need_more = 0;
-  const int kn = c->k + 1;
-  trace_push(d, c, kn, c->J_pred, c->alpha, lam, nb, c->branch, c->gTd);
-  bool stop = kn >= c->max_iter;
-  if (c->stop_kind == STOP_CONVERGENCE && fabs(c->J_pred - c->J) <= c->tol * c->J) stop = true;
-  if (c->stop_kind == STOP_DISCREPANCY && 2.0 * c->J_pred * c->inv_pS <= c->eta) stop = true;
-  if (stop) c->done = 1;
-}
-
-template <bool FP64>
-__global__ void __launch_bounds__(kCtrlBlock) k_ctrl_lambda(const ImgDesc* __restrict__ imgs) {
-  const ImgDesc& d = imgs[blockIdx.x];
-  CtrlState* c = d.ctrl;
-  if (c->done >= 1) return;
-  double s[1], arm[4];
-  ctrl_sum<1, FP64>(d, SLOT_GTD, s, false);
-  ctrl_sum<4, FP64>(d, SLOT_ARM, arm, true);
-  if (threadIdx.x != 0) return;
-  const double gTd = s[0];
-  c->gTd = gTd;
-  if (!isfinite(gTd)) { c->status = 8; c->done = 2; return; }
-  double lam = 1.0;
-  for (int i = 0; i < 4 && i <= c->max_backtracks; ++i) {
-    const bool ok = FP64 ? (arm[i] <= c->beta * lam * gTd)
-                         : (float(arm[i]) <= float(c->beta) * float(lam) * float(gTd));
-    if (ok) { sgp_accept(d, c, i, lam, arm[i]); return; }
-    lam *= c->theta;
-  }
-  c->need_more = 1;
-}
-
-template <bool FP64>
-__global__ void __launch_bounds__(kCtrlBlock) k_ctrl_lambda_extra(const ImgDesc* __restrict__ imgs) {
-  const ImgDesc& d = imgs[blockIdx.x];
-  CtrlState* c = d.ctrl;
-  if (c->done >= 1 || !c->need_more) return;
-  double arm[kArmExtra];
-  ctrl_sum<kArmExtra, FP64>(d, SLOT_ARMX, arm, false);
-  if (threadIdx.x != 0) return;
-  double lam = c->theta * c->theta * c->theta * c->theta;
-  const double gTd = c->gTd;
-  for (int i = 0; i < kArmExtra && 4 + i <= c->max_backtracks; ++i) {
-    const bool ok = FP64 ? (arm[i] <= c->beta * lam * gTd)
-                         : (float(arm[i]) <= float(c->beta) * float(lam) * float(gTd));
-    if (ok) { sgp_accept(d, c, 4 + i, lam, arm[i]); return; }
-    lam *= c->theta;
-  }
-  c->need_more = 0;
-  c->status = 6;                      // line search failed: stop at f^(k)
-  c->done = 2;
-}
-
-template <bool FP64>
-__global__ void __launch_bounds__(kCtrlBlock) k_ctrl_rl(const ImgDesc* __restrict__ imgs) {
-  const ImgDesc& d = imgs[blockIdx.x];
-  CtrlState* c = d.ctrl;
-  if (c->done >= 2) return;
-  double kl[1], rr[1];
-  ctrl_sum<1, FP64>(d, SLOT_KL, kl, true);
-  ctrl_sum<1, FP64>(d, SLOT_RHO, rr, false);
-  if (threadIdx.x != 0) return;
-  const bool updated = c->have_v;
-  if (updated) c->k += 1;
-  c->have_v = 1;
-  if (!isfinite(kl[0])) { c->status = 8; c->done = 2; return; }
-  c->J_prev = c->J;
-  c->J = kl[0];
-  if (updated) trace_push(d, c, c->k, c->J, 0.0, 1.0, 0, 0, 0.0);
-  if (c->stop_kind == STOP_MIN_ERROR && c->ftrue_norm2 > 0.0) {
-    const double rho = sqrt(rr[0] / c->ftrue_norm2);
-    c->rho = rho;
-    if (c->k >= 1 && rho > c->rho_prev) { c->done = 2; c->result_prev = 1; return; }
-    c->rho_prev = rho;
-  }
-  bool stop = c->k >= c->max_iter;
-  if (updated && c->stop_kind == STOP_CONVERGENCE && fabs(c->J - c->J_prev) <= c->tol * c->J_prev) stop = true;
-  if (c->stop_kind == STOP_DISCREPANCY && 2.0 * c->J * c->inv_pS <= c->eta) stop = true;
-  if (stop) c->done = 2;
-}
 
 // After the set-up passes: J_0 (from the ratio pass) and L1/L2 (Sect. 3.2) from one RL step.
 template <bool FP64>

@@ -1,5 +1,6 @@
-// Multi-size passes: one launch covers problems of different sides; every block reads the side of
-// its work item's problem and runs the body instantiated for that side.
+// Shared pieces of the multi-size passes: one launch covers problems of different sides; every
+// block reads the side of its work item's problem and runs the body instantiated for that side.
+#pragma once
 #include "kernels_inst.cuh"
 
 namespace sgp {
@@ -34,30 +35,5 @@ constexpr size_t max_col_smem() {
     (void)extra;                                                                                          \
     SGP_SWITCH_SIDE(W, BODY)                                                                              \
   }
-
-#define B1(N) b_sgp_update_ratio<N, FP64>(imgs, items, n_items)
-SGP_MULTI_ROW(km_sgp_update_ratio, B1)
-#define B2(N) b_sgp_grad_bb<N, FP64>(imgs, items, n_items)
-SGP_MULTI_ROW(km_sgp_grad_bb, B2)
-#define B3(N) b_sgp_y<N, FP64>(imgs, items, n_items)
-SGP_MULTI_ROW(km_sgp_y, B3)
-#define B4(N) b_sgp_ad_armijo<N, FP64>(imgs, items, n_items)
-SGP_MULTI_ROW(km_sgp_ad_armijo, B4)
-#define B5(N) b_sgp_armijo_extra<N, FP64>(imgs, items, n_items)
-SGP_MULTI_ROW(km_sgp_armijo_extra, B5)
-
-static SGP_DEFINE_TWIDDLE_INIT(twiddle_init_multi_sgp)
-
-void register_multi_sgp(Registry& R) {
-#define REG(OP, K) R.row_multi[OP][0] = (const void*)&K<false>; R.row_multi[OP][1] = (const void*)&K<true>;
-  REG(ROP_SGP_UPDATE, km_sgp_update_ratio)
-  REG(ROP_SGP_GRAD, km_sgp_grad_bb)
-  REG(ROP_SGP_Y, km_sgp_y)
-  REG(ROP_SGP_AD, km_sgp_ad_armijo)
-  REG(ROP_SGP_ARMX, km_sgp_armijo_extra)
-#undef REG
-  R.row_multi_smem = max_row_smem();
-  R.twiddle_init[3] = &twiddle_init_multi_sgp;
-}
 
 }  // namespace sgp

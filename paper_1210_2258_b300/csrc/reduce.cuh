@@ -1,0 +1,171 @@
+// Reductions of the row passes and of the controllers.
+//
+// Per thread: compensated FP32 (Kahan) accumulation over the thread's pixels.  Above the thread,
+// the "mixed" variant carries every sum as an unevaluated pair of FP32 values (hi + lo, combined
+// with the error-free two-sum of Knuth), i.e. about 48 significand bits, and converts to FP64
+// only for the controller's scalar logic: FP64 arithmetic is slow on this part, FP32 is not.
+// The plain-FP32 variant sums single FP32 values throughout.
+//
+// A block stores its NS sums as float2 (hi, lo) in consecutive 8-byte slots of its item's
+// partial-sum record; the controller of a problem adds the records of all its items in a fixed
+// order (deterministic, no atomics on values).  The controller runs at the end of a row pass in
+// the block that finishes last (arrive_last), so no separate launch is needed for it.
+#pragma once
+#include <math.h>
+#include "state.cuh"
+
+namespace sgp {
+
+struct KSum {
+  float s = 0.0f, c = 0.0f;   // value = s - c
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+// value hi + lo with |lo| <= ulp(hi)/2 after ff_add
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;                       // two-sum: s + e = a.hi + b.hi exactly
+  const float bv = s - a.hi;
+  const float e = (a.hi - (s - bv)) + (b.hi - bv);
+  const float lo = e + (a.lo + b.lo);
+  const float hi = s + lo;                           // fast two-sum renormalisation
+  return FF{hi, lo - (hi - s)};
+}
+__device__ __forceinline__ FF ff_shfl_xor(FF a, int o) {
+  return FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ FF ff_warp_sum(FF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = ff_add(v, ff_shfl_xor(v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double ff_value(FF a) { return double(a.hi) + double(a.lo); }
+
+// a partial-sum slot holds one float2 (hi, lo)
+__device__ __forceinline__ void slot_store(double* slot, FF v) {
+  *reinterpret_cast<float2*>(slot) = make_float2(v.hi, v.lo);
+}
+__device__ __forceinline__ FF slot_load(const double* slot) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(slot));   // L2: written by other blocks
+  return FF{v.x, v.y};
+}
+
+// Sum NS per-thread values over the block; thread 0 stores them to out[0..NS).
+template <int NS, bool FP64>
+__device__ __forceinline__ void block_sum_store(const KSum (&loc)[NS], double* out) {
+  __shared__ FF red[NS][kRowBlock / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    FF v;
+    if (FP64) v = ff_warp_sum(FF{loc[s].s, -loc[s].c});
+    else v = FF{warp_sum(loc[s].s - loc[s].c), 0.0f};
+    if (lane == 0) red[s][wid] = v;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      FF v = lane < (int)(blockDim.x >> 5) ? red[s][lane] : FF{0.0f, 0.0f};
+      if (FP64) v = ff_warp_sum(v);
+      else v = FF{warp_sum(v.hi), 0.0f};
+      if (lane == 0) slot_store(out + s, v);
+    }
+  }
+  __syncthreads();
+}
+
+// Sum NS slots over this problem's items (row list or row-view list) in a fixed order; the
+// result is on every thread of the block.
+template <int NS, bool FP64>
+__device__ void ctrl_sum(const ImgDesc& d, int slot, double (&res)[NS], bool view_list) {
+  __shared__ FF red[NS][kCtrlBlock / 32];
+  FF loc[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) loc[s] = FF{0.0f, 0.0f};
+  const int n = view_list ? d.n_rv_items : d.n_row_items;
+  const double* base = view_list ? d.partv : d.part;
+#pragma unroll 4
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double* p = base + size_t(i) * kPartStride + slot;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const FF v = slot_load(p + s);
+      if (FP64) loc[s] = ff_add(loc[s], v);
+      else loc[s].hi += v.hi;
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const FF v = FP64 ? ff_warp_sum(loc[s]) : FF{warp_sum(loc[s].hi), 0.0f};
+    if (lane == 0) red[s][wid] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    FF v = red[s][0];
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) {   // fixed order: deterministic
+      if (FP64) v = ff_add(v, red[s][w]);
+      else v.hi += red[s][w].hi;
+    }
+    res[s] = FP64 ? ff_value(v) : double(v.hi);
+  }
+  __syncthreads();
+}
+
+// min over SLOT_MIN and max over SLOT_MAX (plain doubles) of this problem's row items
+__device__ inline void ctrl_minmax(const ImgDesc& d, double& mn, double& mx) {
+  __shared__ double rmn[kCtrlBlock / 32], rmx[kCtrlBlock / 32];
+  double a = INFINITY, b = 0.0;
+  for (int i = threadIdx.x; i < d.n_row_items; i += blockDim.x) {
+    const double* p = d.part + size_t(i) * kPartStride;
+    a = fmin(a, __ldcg(p + SLOT_MIN));
+    b = fmax(b, __ldcg(p + SLOT_MAX));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { rmn[wid] = a; rmx[wid] = b; }
+  __syncthreads();
+  mn = INFINITY; mx = 0.0;
+  for (int w = 0; w < int(blockDim.x >> 5); ++w) { mn = fmin(mn, rmn[w]); mx = fmax(mx, rmx[w]); }
+  __syncthreads();
+}
+
+// Called once by every block of a problem in a pass, after the block's partial sums are stored
+// (by its thread 0).  True in the block that arrives last: it then sees every block's partials.
+// The last block resets the counter, so the next pass starts from zero.  Nothing waits.
+__device__ __forceinline__ bool arrive_last(CtrlState* c, int n_blocks) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();                                   // release this block's partials
+    const unsigned prev = atomicAdd(&c->arrive, 1u);
+    const int last = prev == unsigned(n_blocks - 1);
+    if (last) {
+      c->arrive = 0u;
+      __threadfence();                                 // acquire the other blocks' partials
+    }
+    s_last = last;
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
+}  // namespace sgp

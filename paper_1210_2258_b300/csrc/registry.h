@@ -21,12 +21,14 @@ enum RowOp {
 constexpr int kColModes = 6;
 constexpr int kColPto1P1 = 4, kColPto1P3 = 5;
 
+constexpr int kTwiddleUnits = 6;   // translation units with their own twiddle table
+
 struct Registry {
   const void* row[ROP_COUNT][2][kNumSides];   // [op][fp64][side]
   const void* col[kColModes][kNumSides];      // [variant][side]
   size_t row_smem[kNumSides], col_smem[kNumSides];
   int row_rows[kNumSides], col_cols[kNumSides];
-  cudaError_t (*twiddle_init[5])(const float2*);
+  cudaError_t (*twiddle_init[kTwiddleUnits])(const float2*);
   // multi-size kernels (one launch covers problems of different sides): row ops, and the column
   // passes 1 -> p (index 0), p -> 1 for any p (index 1) and for p = 1 (index 2); dynamic shared
   // memory = max over the sides
@@ -38,7 +40,8 @@ struct Registry {
 void register_small(Registry&);
 void register_mid(Registry&);
 void register_large(Registry&);
-void register_multi_sgp(Registry&);
+void register_multi_sgp_a(Registry&);
+void register_multi_sgp_b(Registry&);
 void register_multi_rest(Registry&);
 
 }  // namespace sgp

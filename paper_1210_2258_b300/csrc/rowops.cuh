@@ -15,6 +15,7 @@
 //              the row passes transform r - 1, so no 1 - A^T r cancellation
 //   step       y = P_+(f - alpha D grad), d = y - f, Eq. (diry); flux mode y = max(0, x - mu D)
 #pragma once
+#include "control.cuh"
 #include "fft.cuh"
 #include "state.cuh"
 
@@ -58,13 +59,46 @@ __device__ __forceinline__ float kl_term(float g, float u0) {
   if (u0 <= 0.0f) return f_inf();
   return g * phi_t((u0 - g) / g);
 }
-// Armijo pixel term J(f + lam d) - J(f) with dl = lam * A d, u0 = A f + b
-__device__ __forceinline__ float armijo_term(float g, float u0, float dl) {
-  if (g < 0.0f) return 0.0f;
-  if (g == 0.0f) return dl;
-  if (u0 + dl <= 0.0f || u0 <= 0.0f) return f_inf();
-  const float q = dl / u0;
-  return fmaf(u0 - g, q, g * phi_t(q));
+// Armijo pixel terms J(f + lam d) - J(f) for the step lengths lam[0..N) at one pixel, u0 = A f + b,
+// ad = A d; q = lam ad / u0 shares one division over the step lengths
+template <int N>
+__device__ __forceinline__ void armijo_add(KSum (&acc)[N], const float (&lam)[N], float g, float u0, float ad) {
+  if (g < 0.0f) return;                       // outside S
+  if (g == 0.0f) {
+#pragma unroll
+    for (int l = 0; l < N; ++l) acc[l].add(lam[l] * ad);
+    return;
+  }
+  if (u0 <= 0.0f) {
+#pragma unroll
+    for (int l = 0; l < N; ++l) acc[l].add(f_inf());
+    return;
+  }
+  const float qb = ad / u0, gm = u0 - g;
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    const float q = lam[l] * qb;              // u0 + lam ad <= 0  <=>  q <= -1
+    acc[l].add(q <= -1.0f ? f_inf() : fmaf(gm, q, g * phi_t(q)));
+  }
+}
+// the same for the step lengths lam0 th^l, l = 0..N-1 (running products: few registers)
+template <int N>
+__device__ __forceinline__ void armijo_add_geom(KSum (&acc)[N], float lam0, float th, float g, float u0, float ad) {
+  if (g < 0.0f) return;
+  float q, gm = 0.0f;
+  if (g == 0.0f) q = lam0 * ad;
+  else if (u0 > 0.0f) { q = lam0 * (ad / u0); gm = u0 - g; }
+  else {
+#pragma unroll
+    for (int l = 0; l < N; ++l) acc[l].add(f_inf());
+    return;
+  }
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    if (g == 0.0f) acc[l].add(q);             // q = lam A d here
+    else acc[l].add(q <= -1.0f ? f_inf() : fmaf(gm, q, g * phi_t(q)));
+    q *= th;
+  }
 }
 __device__ __forceinline__ float ratio_term(float g, float u0) {
   return (g > 0.0f && u0 > 0.0f) ? g / u0 : 0.0f;
@@ -78,50 +112,6 @@ __device__ __forceinline__ float ratio_m1(float g, float u0) {
 }
 
 // ------------------------------------------------------------------------------ reductions
-// Per-thread compensated FP32 accumulation over the thread's few pixels, FP64 from the warp
-// level up (FP32 throughout for the plain-FP32 variant).
-struct KSum {
-  float s = 0.0f, c = 0.0f;
-  __device__ __forceinline__ void add(float x) {
-    const float y = x - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-};
-
-template <bool FP64> struct Acc { using T = float; };
-template <> struct Acc<true> { using T = double; };
-
-template <class V> __device__ __forceinline__ V warp_sum(V v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Sum NS per-thread values over the block; thread 0 writes them (as doubles) to out[0..NS).
-template <int NS, bool FP64>
-__device__ __forceinline__ void block_sum_store(const KSum (&loc)[NS], double* out) {
-  using V = typename Acc<FP64>::T;
-  __shared__ V red[NS][kRowBlock / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    V v = warp_sum<V>(V(loc[s].s) - V(loc[s].c));
-    if (lane == 0) red[s][wid] = v;
-  }
-  __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      V v = lane < (int)(blockDim.x >> 5) ? red[s][lane] : V(0);
-      v = warp_sum<V>(v);
-      if (lane == 0) out[s] = double(v);
-    }
-  }
-  __syncthreads();
-}
-
 // min over strictly positive values and max, stored to out[0], out[1]
 __device__ __forceinline__ void block_minmax_store(float mn, float mx, double* out) {
   __shared__ float rmn[kRowBlock / 32], rmx[kRowBlock / 32];
@@ -395,6 +385,7 @@ __device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ i
     row_real_to_spec<W>(x, spec_plane(d, j + 1) + off, t, act);
     block_sum_store<2, FP64>(acc, partv_of(d, it) + SLOT_KL);
   }
+  if (arrive_last(d.ctrl, d.n_rv_items)) ctrl_sgp_begin<FP64>(d);
 }
 template <int W, bool FP64>
 __global__ void __launch_bounds__(kRowBlock) k_sgp_update_ratio(const ImgDesc* __restrict__ imgs,
@@ -454,6 +445,7 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
       }
     }
     block_sum_store<4, FP64>(acc, part_of(d, it) + SLOT_BB);
+    if (arrive_last(d.ctrl, d.n_row_items)) ctrl_sgp_alpha<FP64>(d);
   }
 }
 template <int W, bool FP64>
@@ -528,8 +520,11 @@ __device__ __forceinline__ void b_sgp_ad_armijo(const ImgDesc* __restrict__ imgs
   const bool act = row < d.H;
   const size_t off = size_t(row) * G::M;
   const float th = float(c->theta);
-  const float lam[4] = {1.0f, th, th * th, th * th * th};
-  KSum acc[4];
+  float lam[kArmMain];
+  lam[0] = 1.0f;
+#pragma unroll
+  for (int l = 1; l < kArmMain; ++l) lam[l] = lam[l - 1] * th;
+  KSum acc[kArmMain];
   row_spec_to_real<W>(x, spec_plane(d, j + 1) + off, t, act);
   if (act) {
     const float* uj = d.u + size_t(j) * d.P;
@@ -541,14 +536,12 @@ __device__ __forceinline__ void b_sgp_ad_armijo(const ImgDesc* __restrict__ imgs
       const float2 ad = x(t + q * G::T), u = ld2(uj, i), g = ld2(gj, i), b = b_pair(d, j, i);
       st2(adj, i, ad);
       const float u0x = u.x + b.x, u0y = u.y + b.y;
-#pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        acc[l].add(armijo_term(g.x, u0x, lam[l] * ad.x));
-        acc[l].add(armijo_term(g.y, u0y, lam[l] * ad.y));
-      }
+      armijo_add<kArmMain>(acc, lam, g.x, u0x, ad.x);
+      armijo_add<kArmMain>(acc, lam, g.y, u0y, ad.y);
     }
   }
-  block_sum_store<4, FP64>(acc, partv_of(d, it) + SLOT_ARM);
+  block_sum_store<kArmMain, FP64>(acc, partv_of(d, it) + SLOT_ARM);
+  if (arrive_last(d.ctrl, d.n_rv_items)) ctrl_sgp_lambda<FP64>(d);
 }
 template <int W, bool FP64>
 __global__ void __launch_bounds__(kRowBlock) k_sgp_ad_armijo(const ImgDesc* __restrict__ imgs,
@@ -556,7 +549,7 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_ad_armijo(const ImgDesc* __re
   b_sgp_ad_armijo<W, FP64>(imgs, items, n_items);
 }
 
-// SGP K7 (only when no lambda in {1, .., theta^3} was accepted): Delta J(theta^i), i = 4..30.
+// SGP K7 (only when no lambda of the main pass was accepted): Delta J(theta^i), i = kArmMain..30.
 template <int W, bool FP64>
 __device__ __forceinline__ void b_sgp_armijo_extra(const ImgDesc* __restrict__ imgs,
                                                                const int2* __restrict__ items, int n_items) {
@@ -573,6 +566,9 @@ __device__ __forceinline__ void b_sgp_armijo_extra(const ImgDesc* __restrict__ i
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
     const float th = float(c->theta);
+    float lam0 = 1.0f;
+#pragma unroll
+    for (int l = 0; l < kArmMain; ++l) lam0 *= th;
     KSum acc[kArmExtra];
     if (act) {
       for (int j = 0; j < d.p; ++j) {
@@ -582,18 +578,13 @@ __device__ __forceinline__ void b_sgp_armijo_extra(const ImgDesc* __restrict__ i
         for (int q = 0; q < G::E; ++q) {
           const size_t i = off + t + q * G::T;
           const float2 u = ld2(uj, i), ad = ld2(adj, i), g = ld2(gj, i), b = b_pair(d, j, i);
-          const float u0x = u.x + b.x, u0y = u.y + b.y;
-          float lam = th * th * th * th;
-#pragma unroll
-          for (int l = 0; l < kArmExtra; ++l) {
-            acc[l].add(armijo_term(g.x, u0x, lam * ad.x));
-            acc[l].add(armijo_term(g.y, u0y, lam * ad.y));
-            lam *= th;
-          }
+          armijo_add_geom<kArmExtra>(acc, lam0, th, g.x, u.x + b.x, ad.x);
+          armijo_add_geom<kArmExtra>(acc, lam0, th, g.y, u.y + b.y, ad.y);
         }
       }
     }
     block_sum_store<kArmExtra, FP64>(acc, part_of(d, it) + SLOT_ARMX);
+    if (arrive_last(d.ctrl, d.n_row_items)) ctrl_sgp_lambda_extra<FP64>(d);
   }
 }
 template <int W, bool FP64>
@@ -693,6 +684,7 @@ __device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
   }
   row_real_to_spec<W>(x, sp, t, act);
   block_sum_store<1, FP64>(acc, partv_of(d, it) + SLOT_KL);
+  if (!write_u && arrive_last(d.ctrl, d.n_rv_items)) ctrl_rl<FP64>(d);   // RL iteration (not set-up)
 }
 template <int W, bool FP64>
 __global__ void __launch_bounds__(kRowBlock) k_rl_ratio(const ImgDesc* __restrict__ imgs,

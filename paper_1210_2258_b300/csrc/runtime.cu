@@ -43,7 +43,8 @@ sgp_status ensure_device_ready(int dev) {
     register_small(g_reg);
     register_mid(g_reg);
     register_large(g_reg);
-    register_multi_sgp(g_reg);
+    register_multi_sgp_a(g_reg);
+    register_multi_sgp_b(g_reg);
     register_multi_rest(g_reg);
     g_reg_ready = true;
   }
@@ -59,7 +60,7 @@ sgp_status ensure_device_ready(int dev) {
       tab[off + q] = make_float2(float(cos(a)), float(sin(a)));
     }
   }
-  for (int i = 0; i < 5; ++i) CU(g_reg.twiddle_init[i](tab.data()));
+  for (int i = 0; i < kTwiddleUnits; ++i) CU(g_reg.twiddle_init[i](tab.data()));
   for (int op = 0; op < ROP_COUNT; ++op)
     for (int f = 0; f < 2; ++f)
       if (g_reg.row_multi[op][f])
@@ -291,13 +292,15 @@ sgp_status plane_stats(cudaStream_t s, const float* x, const float* b, const flo
 }
 
 // ---- iteration sequences --------------------------------------------------------------------------
+// kernel launches of one iteration (the launch counter counts graph nodes)
+constexpr int kSgpLaunches = 7, kRlLaunches = 4, kFluxLaunches = 2 * (kFluxPasses + 2);
+
 sgp_status seq_rl_unit(sgp_ctx* c) {
   sgp_status st;
   if ((st = row_pass(c, ROP_RL_UPDATE, false))) return st;
   if ((st = col_pass(c, COL_1TOP, JOB_A * c->n))) return st;
-  if ((st = row_pass(c, ROP_RL_RATIO, true, 0))) return st;
-  if ((st = col_pass(c, COL_PTO1, JOB_AT * c->n))) return st;
-  return ctrl_pass(c, c->fp64 ? (const void*)&k_ctrl_rl<true> : (const void*)&k_ctrl_rl<false>);
+  if ((st = row_pass(c, ROP_RL_RATIO, true, 0))) return st;     // + RL controller
+  return col_pass(c, COL_PTO1, JOB_AT * c->n);
 }
 
 // flux-constrained projection: bracket, kFluxPasses candidate passes, exact final solve
@@ -321,25 +324,18 @@ sgp_status seq_flux(sgp_ctx* c) {
 
 sgp_status seq_sgp_unit(sgp_ctx* c) {
   sgp_status st;
-  const bool f = c->fp64;
-  if ((st = row_pass(c, ROP_SGP_UPDATE, true))) return st;
+  if ((st = row_pass(c, ROP_SGP_UPDATE, true))) return st;     // + iteration controller
   if ((st = col_pass(c, COL_PTO1, JOB_AT * c->n))) return st;
-  if ((st = row_pass(c, ROP_SGP_GRAD, false))) return st;
-  if ((st = ctrl_pass(c, f ? (const void*)&k_ctrl_alpha<true> : (const void*)&k_ctrl_alpha<false>))) return st;
+  if ((st = row_pass(c, ROP_SGP_GRAD, false))) return st;      // + step-length controller
   if (c->prm.constraint == 1 && (st = seq_flux(c))) return st;
   if ((st = row_pass(c, ROP_SGP_Y, false))) return st;
   if ((st = col_pass(c, COL_1TOP, JOB_A * c->n))) return st;
-  if ((st = row_pass(c, ROP_SGP_AD, true))) return st;
-  if ((st = ctrl_pass(c, f ? (const void*)&k_ctrl_lambda<true> : (const void*)&k_ctrl_lambda<false>))) return st;
-  if ((st = row_pass(c, ROP_SGP_ARMX, false))) return st;
-  return ctrl_pass(c, f ? (const void*)&k_ctrl_lambda_extra<true> : (const void*)&k_ctrl_lambda_extra<false>);
+  if ((st = row_pass(c, ROP_SGP_AD, true))) return st;         // + line-search controller
+  return row_pass(c, ROP_SGP_ARMX, false);                     // + its continuation
 }
 
-sgp_status seq_sgp_finalize(sgp_ctx* c) {
-  sgp_status st;
-  if ((st = row_pass(c, ROP_SGP_UPDATE, true))) return st;
-  return ctrl_pass(c, c->fp64 ? (const void*)&k_ctrl_alpha<true> : (const void*)&k_ctrl_alpha<false>);
-}
+// a stop decided in the last unit of a graph leaves the update f^(k+1) = f^(k) + lambda d pending
+sgp_status seq_sgp_finalize(sgp_ctx* c) { return row_pass(c, ROP_SGP_UPDATE, true); }
 
 sgp_status build_graph(sgp_ctx* c, bool sgp, cudaGraphExec_t* out) {
   if (*out) return SGP_OK;
@@ -466,7 +462,7 @@ sgp_status run_fixed(sgp_ctx* c, bool sgp, int n_iter) {
   const int launches = (n_iter + c->graph_units - 1) / c->graph_units;
   for (int l = 0; l < launches; ++l) {
     CU(cudaGraphLaunch(sgp ? c->g_sgp : c->g_rl, c->s));
-    c->launches += c->graph_units * (sgp ? (c->prm.constraint == 1 ? 24 : 10) : 5);
+    c->launches += c->graph_units * (sgp ? (c->prm.constraint == 1 ? kSgpLaunches + kFluxLaunches : kSgpLaunches) : kRlLaunches);
   }
   if (sgp && (st = seq_sgp_finalize(c))) return st;
   return SGP_OK;
@@ -487,7 +483,7 @@ sgp_status run_until(sgp_ctx* c, bool sgp, const sgp_stop_rule* rule, int* iters
   const int max_launches = rule->max_iter / c->graph_units + 2;
   CtrlState* slot[2] = {c->h_ctrl, c->h_ctrl + c->n};
   // keep one chunk in flight while the flags of the previous one are inspected
-  const int per_graph = c->graph_units * (sgp ? (c->prm.constraint == 1 ? 24 : 10) : 5);
+  const int per_graph = c->graph_units * (sgp ? (c->prm.constraint == 1 ? kSgpLaunches + kFluxLaunches : kSgpLaunches) : kRlLaunches);
   CU(cudaGraphLaunch(g, c->s));
   c->launches += per_graph;
   CU(cudaMemcpyAsync(slot[0], c->L.ctrl, sizeof(CtrlState) * c->n, cudaMemcpyDeviceToHost, c->s));
@@ -560,7 +556,8 @@ size_t sgp_workspace_bytes(int n, const sgp_shape* shapes, const sgp_params* par
     register_small(g_reg);
     register_mid(g_reg);
     register_large(g_reg);
-    register_multi_sgp(g_reg);
+    register_multi_sgp_a(g_reg);
+    register_multi_sgp_b(g_reg);
     register_multi_rest(g_reg);
     g_reg_ready = true;
   }
@@ -1092,15 +1089,16 @@ sgp_status sgp_apply_AT(sgp_ctx* c, int image, const float* y, float* out) {
 }
 
 sgp_status sgp_time_passes(sgp_ctx* c, int iters, double* ms_out, int n_out) {
-  if (!c || !ms_out || n_out < 10 || iters <= 0) return fail(SGP_ERR_ARG, "need ctx, iters > 0 and 10 outputs");
+  if (!c || !ms_out || n_out < kSgpLaunches || iters <= 0)
+    return fail(SGP_ERR_ARG, "need ctx, iters > 0 and 7 outputs");
+  if (c->prm.constraint != 0) return fail(SGP_ERR_ARG, "pass timing covers the non-negativity constraint only");
   sgp_status st = enter(c);
   if (st) return st;
   if (c->mode != 1 && (st = prepare(c, 1))) return st;
   if ((st = arm(c, STOP_FIXED, 1 << 30, 0.0, 1.0))) return st;
-  std::vector<cudaEvent_t> ev(11);
+  std::vector<cudaEvent_t> ev(kSgpLaunches + 1);
   for (auto& e : ev) CU(cudaEventCreate(&e));
-  std::vector<double> acc(10, 0.0);
-  const bool f = c->fp64;
+  std::vector<double> acc(kSgpLaunches, 0.0);
   for (int it = 0; it < iters && st == SGP_OK; ++it) {
     int q = 0;
     CU(cudaEventRecord(ev[q++], c->s));
@@ -1108,15 +1106,12 @@ sgp_status sgp_time_passes(sgp_ctx* c, int iters, double* ms_out, int n_out) {
     step(row_pass(c, ROP_SGP_UPDATE, true));
     step(col_pass(c, COL_PTO1, JOB_AT * c->n));
     step(row_pass(c, ROP_SGP_GRAD, false));
-    step(ctrl_pass(c, f ? (const void*)&k_ctrl_alpha<true> : (const void*)&k_ctrl_alpha<false>));
     step(row_pass(c, ROP_SGP_Y, false));
     step(col_pass(c, COL_1TOP, JOB_A * c->n));
     step(row_pass(c, ROP_SGP_AD, true));
-    step(ctrl_pass(c, f ? (const void*)&k_ctrl_lambda<true> : (const void*)&k_ctrl_lambda<false>));
     step(row_pass(c, ROP_SGP_ARMX, false));
-    step(ctrl_pass(c, f ? (const void*)&k_ctrl_lambda_extra<true> : (const void*)&k_ctrl_lambda_extra<false>));
-    CU(cudaEventSynchronize(ev[10]));
-    for (int k = 0; k < 10; ++k) {
+    CU(cudaEventSynchronize(ev[kSgpLaunches]));
+    for (int k = 0; k < kSgpLaunches; ++k) {
       float ms = 0.0f;
       CU(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
       acc[k] += ms;
@@ -1124,7 +1119,7 @@ sgp_status sgp_time_passes(sgp_ctx* c, int iters, double* ms_out, int n_out) {
   }
   for (auto& e : ev) cudaEventDestroy(e);
   if (st) return st;
-  for (int k = 0; k < 10; ++k) ms_out[k] = acc[k] / iters;
+  for (int k = 0; k < kSgpLaunches; ++k) ms_out[k] = acc[k] / iters;
   c->mode = 0;   // the timed iterations advanced the state; the next solve re-initialises
   return leave(c);
 }

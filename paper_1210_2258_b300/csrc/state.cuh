@@ -21,13 +21,14 @@ enum Slot {
   SLOT_BB = 2,        // 4 slots: s'D^-2 s, s'D^-1 z, s'D z, z'D^2 z
   SLOT_GTD = 6,       // grad' d
   SLOT_FLUX = 7,      // sum f
-  SLOT_ARM = 8,       // 4 slots: Delta J(theta^i), i = 0..3
-  SLOT_ARMX = 12,     // 27 slots: Delta J(theta^i), i = 4..30
+  SLOT_ARM = 8,       // kArmMain slots: Delta J(theta^i), i < kArmMain (main pass)
+  SLOT_ARMX = 12,     // kArmExtra slots: Delta J(theta^i), i = kArmMain..30 (only when needed)
   SLOT_MIN = 40,      // min over positive pixels (set-up)
   SLOT_MAX = 41,      // max (set-up)
   SLOT_PROJ = 42,     // flux projection search sums (up to 6)
 };
-constexpr int kArmExtra = 27;
+constexpr int kArmMain = 4;         // step lengths 1, theta, theta^2, theta^3 of the main Armijo pass
+constexpr int kArmExtra = 31 - kArmMain;
 constexpr int kFluxCand = 16;       // candidate mu values per flux-search pass (slots SLOT_ARMX..)
 constexpr int kFluxPasses = 5;
 
@@ -41,7 +42,7 @@ struct CtrlState {
   int fresh;        // SGP: 1 when f[k&1] is current, 0 when f^(k+1) = f^(k) + lambda d is pending
   int done;         // 0 running; 1 stop decided, final SGP update pending; 2 stopped
   int status;       // device-side status (sgp_status code), 0 = OK
-  int need_more;    // Armijo: no lambda in {1..theta^3} accepted yet
+  int need_more;    // Armijo: no lambda of the main pass accepted
   int have_v;       // RL: spectrum plane 0 holds sum_j A_j^T r_j of the current iterate
   int branch;       // 0: alpha_0, 1: BB1, 2: windowed BB2
   int backtracks;
@@ -52,6 +53,7 @@ struct CtrlState {
   int M_alpha, warmup, max_backtracks, fp64;
   int constraint;   // 0 non-negativity, 1 + flux
   int proj_pass;    // flux projection search pass
+  unsigned arrive;  // blocks of the current row pass that have stored their partial sums
   double J;         // J_0 at the current iterate
   double J_pred;    // J_0 at the accepted trial point
   double J_prev;    // RL: J_0 at the previous iterate

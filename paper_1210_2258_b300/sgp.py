@@ -13,7 +13,7 @@ import re
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "lib", "libsgp_b300.so")
+LIB_PATH = os.environ.get("SGP_LIB_PATH") or os.path.join(HERE, "lib", "libsgp_b300.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "sgp.h")
 
 OK, ERR_ARG, ERR_SIZE, ERR_PSF, ERR_CUDA, ERR_WORKSPACE, ERR_LINESEARCH, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE = range(10)
@@ -22,6 +22,7 @@ STATUS_NAMES = ["OK", "ARG", "SIZE_UNSUPPORTED", "PSF", "CUDA", "WORKSPACE", "LI
 STOP_FIXED, STOP_CONVERGENCE, STOP_DISCREPANCY, STOP_MIN_ERROR = range(4)
 START_ZERO, START_DATA, START_CONSTANT, START_USER = range(4)
 PSF_CENTER, PSF_CORNER = 0, 1
+N_PASSES = 7    # passes of one SGP iteration (sgp_time_passes)
 SIDES = (16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048)
 
 
@@ -264,9 +265,9 @@ class Problems:
         return out
 
     def time_passes(self, iters: int = 5) -> list[float]:
-        """Mean duration (ms) of each of the 10 passes of an SGP iteration (CUDA events)."""
-        out = (C.c_double * 10)()
-        _check(load().sgp_time_passes(self.ctx, iters, out, 10))
+        """Mean duration (ms) of each of the 7 passes of an SGP iteration (CUDA events)."""
+        out = (C.c_double * N_PASSES)()
+        _check(load().sgp_time_passes(self.ctx, iters, out, N_PASSES))
         return list(out)
 
     def launch_count(self) -> int:

@@ -278,11 +278,16 @@ def train(net: WarmStartNet, g, f, b, epochs: int = 3, batch: int = 32, lr: floa
     return losses
 
 
-def evaluate(net: WarmStartNet, scs, max_iter: int = 2000, batch: int = 50):
-    """Flat-start vs warm-start SGP to the same discrepancy stop: iterations, GPU time, final KL."""
+def evaluate(net: WarmStartNet, scs, max_iter: int = 2000, batch: int = 50, n_single: int = 100):
+    """Flat-start vs warm-start SGP to the same discrepancy stop: iterations, GPU time, final KL.
+
+    Batched: every image of a batch of `batch` problems gets its own stop, the batch time is the time
+    until all have stopped.  Single: the first `n_single` images solved one at a time, each solve
+    timed after a first untimed solve has built the context's graph (flat: constant start; warm:
+    network forward + solve from its f^(0))."""
     import torch
     out = {"flat_iters": [], "warm_iters": [], "flat_kl": [], "warm_kl": [], "flat_ms": 0.0, "warm_ms": 0.0,
-           "net_ms": 0.0, "fallbacks": 0}
+           "net_ms": 0.0, "fallbacks": 0, "single_flat_ms": [], "single_warm_ms": [], "single_net_ms": []}
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     for a in range(0, len(scs), batch):
         part = scs[a:a + batch]
@@ -322,7 +327,36 @@ def evaluate(net: WarmStartNet, scs, max_iter: int = 2000, batch: int = 50):
             out[f"{mode}_iters"] += list(it)
             out[f"{mode}_kl"] += klw
             probs.close()
-    for k in ("flat_iters", "warm_iters", "flat_kl", "warm_kl"):
+    for sc in scs[:n_single]:
+        psf = torch.from_numpy(sc.psfs.astype(np.float32)).cuda()
+        g = torch.from_numpy(sc.g.astype(np.float32)).cuda()
+        bvec = torch.tensor([float(sc.b[0])], dtype=torch.float32, device="cuda")
+        prob = lib.Problems(psf, [float(sc.b[0])])
+        prob.set_data(0, g)
+        f0 = net.predict(g, bvec)
+        prob.solve_until(lib.STOP_DISCREPANCY, max_iter=max_iter, eta=1.0, raise_on_error=False)   # graph
+        times = {}
+        for mode in ("flat", "warm"):
+            torch.cuda.synchronize()
+            ev[0].record()
+            if mode == "warm":
+                f0 = net.predict(g, bvec)
+                ev[2].record()
+                prob.set_start(0, lib.START_USER, f0[0])
+            else:
+                prob.set_start(0, lib.START_CONSTANT)
+            prob.solve_until(lib.STOP_DISCREPANCY, max_iter=max_iter, eta=1.0, raise_on_error=False)
+            ev[1].record()
+            torch.cuda.synchronize()
+            times[mode] = ev[0].elapsed_time(ev[1]) if prob.info(0).status == 0 else None
+            if mode == "warm":
+                times["net"] = ev[0].elapsed_time(ev[2])
+        if times["flat"] is not None and times["warm"] is not None:
+            out["single_flat_ms"].append(times["flat"])
+            out["single_warm_ms"].append(times["warm"])
+            out["single_net_ms"].append(times["net"])
+        prob.close()
+    for k in ("flat_iters", "warm_iters", "flat_kl", "warm_kl", "single_flat_ms", "single_warm_ms", "single_net_ms"):
         out[k] = np.asarray(out[k])
     return out
 
@@ -394,6 +428,13 @@ def main(argv=None) -> int:
     res = evaluate(net, ev_scenes)
     t4 = time.perf_counter()
     done = (res["flat_iters"] < 2000) & (res["warm_iters"] < 2000)
+    single = {}
+    if len(res["single_flat_ms"]):
+        single = {"single_images": int(len(res["single_flat_ms"])),
+                  "single_flat_ms_median": float(np.median(res["single_flat_ms"])),
+                  "single_warm_ms_median": float(np.median(res["single_warm_ms"])),
+                  "single_net_ms_median": float(np.median(res["single_net_ms"])),
+                  "single_warm_faster_frac": float(np.mean(res["single_warm_ms"] < res["single_flat_ms"]))}
     kl_rel = np.abs(res["warm_kl"] - res["flat_kl"]) / res["flat_kl"]
     summary = {
         "train_pairs": len(tr), "train_side": a.train_side, "eval_images": len(ev_scenes), "eval_side": a.eval_side,
@@ -403,7 +444,9 @@ def main(argv=None) -> int:
         "flat_mean_iters": float(res["flat_iters"][done].mean()), "warm_mean_iters": float(res["warm_iters"][done].mean()),
         "flat_gpu_ms_total": res["flat_ms"], "warm_gpu_ms_total": res["warm_ms"], "net_ms_total": res["net_ms"],
         "final_kl_rel_diff_median": float(np.median(kl_rel[done])), "final_kl_rel_diff_max": float(np.max(kl_rel[done])),
-        "eval_s": t4 - t3, "fallbacks_to_flat": res["fallbacks"],
+        "flat_not_stopped": int((res["flat_iters"] >= 2000).sum()),
+        "warm_not_stopped": int((res["warm_iters"] >= 2000).sum()),
+        "eval_s": t4 - t3, "fallbacks_to_flat": res["fallbacks"], **single,
     }
     log(json.dumps(summary))
     if a.save:
