@@ -224,18 +224,6 @@ __device__ __forceinline__ void stockham_stage(const Lay& x0, int t, bool act) {
   constexpr int PER = NB / T;
   static_assert(PER * T == NB, "plan: each radix must divide the per-thread count");
   float2 v[PER][R];
-#if SGP_TW_EARLY
-  // twiddles are loaded before the barrier, so their latency overlaps the exchange
-  float2 w[PER][R - 1];
-  if (act && NS > 1) {
-#pragma unroll
-    for (int b = 0; b < PER; ++b) {
-      const int k = (t + b * T) % NS;
-#pragma unroll
-      for (int m = 1; m < R; ++m) w[b][m - 1] = twl<L, INV>(m * k * (L / (NS * R)));
-    }
-  }
-#endif
   if (act) {
 #pragma unroll
     for (int b = 0; b < PER; ++b) {
@@ -252,11 +240,7 @@ __device__ __forceinline__ void stockham_stage(const Lay& x0, int t, bool act) {
       const int k = j % NS;
       if (NS > 1) {
 #pragma unroll
-#if SGP_TW_EARLY
-        for (int m = 1; m < R; ++m) v[b][m] = cmul(v[b][m], w[b][m - 1]);
-#else
         for (int m = 1; m < R; ++m) v[b][m] = cmul(v[b][m], twl<L, INV>(m * k * (L / (NS * R))));
-#endif
       }
       DFT<R, INV>::run(v[b]);
       const int base = (j - k) * R + k;
