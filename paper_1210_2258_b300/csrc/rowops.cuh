@@ -30,6 +30,15 @@ template <int W> struct RowGeo {
   static constexpr size_t SMEM = size_t(ROWS) * PITCH * sizeof(float2);
 };
 
+// Pixel pairs per thread whose global loads are issued together, before any of them is used and
+// before any global store: a store in between would keep the compiler from moving later loads
+// above it (it cannot rule out aliasing), leaving one load latency per pixel pair.  The batch loop
+// itself is not unrolled (code size), and the passes that use it are held to 64 registers
+// (4 blocks per SM) by their launch bounds.
+template <int E, int WANT> constexpr int batch_of() {
+  return E % WANT == 0 ? WANT : (E % 4 == 0 ? 4 : (E % 2 == 0 ? 2 : 1));
+}
+
 // ------------------------------------------------------------------------------ pointwise math
 // Divisions whose result only enters a sum of pixel terms (the KL value, the Armijo differences)
 // use the fast form a * rcp(b) (error <= 2 ulp for the normal, positive divisors that reach it);
@@ -355,14 +364,22 @@ __device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ i
       const float* go = d.grad[k & 1];
       const float alpha = float(c->alpha), mu = float(c->mu);
       const float L1 = float(c->L1), L2 = float(c->L2);
-#pragma unroll 4
-      for (int q = 0; q < G::E; ++q) {
-        const size_t i = off + t + q * G::T;
-        const float2 f = ld2(fo, i), gr = ld2(go, i), w = w_pair(d, i);
-        float2 fn;
-        fn.x = fmaf(lam, proj_step(f.x, gr.x, w.x, alpha, mu, L1, L2) - f.x, f.x);
-        fn.y = fmaf(lam, proj_step(f.y, gr.y, w.y, alpha, mu, L1, L2) - f.y, f.y);
-        st2(fcur, i, fn);
+      constexpr int B = batch_of<G::E, 4>();
+#pragma unroll 1
+      for (int q0 = 0; q0 < G::E; q0 += B) {
+        float2 f[B], gr[B], w[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          const size_t i = off + t + (q0 + b) * G::T;
+          f[b] = ld2(fo, i); gr[b] = ld2(go, i); w[b] = w_pair(d, i);
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          float2 fn;
+          fn.x = fmaf(lam, proj_step(f[b].x, gr[b].x, w[b].x, alpha, mu, L1, L2) - f[b].x, f[b].x);
+          fn.y = fmaf(lam, proj_step(f[b].y, gr[b].y, w[b].y, alpha, mu, L1, L2) - f[b].y, f[b].y);
+          st2(fcur, off + t + (q0 + b) * G::T, fn);
+        }
       }
     }
     if (done == 0 && d.ftrue && c->stop_kind == STOP_MIN_ERROR) {
@@ -377,23 +394,32 @@ __device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ i
   const float* adj = d.Ad + size_t(j) * d.P;
   const float* gj = d.g + size_t(j) * d.P;
   if (act) {
-#pragma unroll 4
-    for (int q = 0; q < G::E; ++q) {
-      const size_t i = off + t + q * G::T;
-      float2 u = ld2(uj, i);
-      if (!fresh) {
-        const float2 a = ld2(adj, i);
-        u.x = fmaf(lam, a.x, u.x);
-        u.y = fmaf(lam, a.y, u.y);
-        st2(uj, i, u);
+    constexpr int B = batch_of<G::E, 4>();
+#pragma unroll 1
+    for (int q0 = 0; q0 < G::E; q0 += B) {
+      float2 u[B], a[B], g[B], bk[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const size_t i = off + t + (q0 + b) * G::T;
+        u[b] = ld2(uj, i);
+        a[b] = fresh ? make_float2(0.0f, 0.0f) : ld2(adj, i);
+        g[b] = done == 0 ? ld2(gj, i) : make_float2(0.0f, 0.0f);
+        bk[b] = b_pair(d, j, i);
       }
-      if (done == 0) {
-        const float2 g = ld2(gj, i), b = b_pair(d, j, i);
-        const float u0x = u.x + b.x, u0y = u.y + b.y;
-        float2 rm;
-        acc[0].add(kl_ratio(g.x, u0x, rm.x));
-        acc[0].add(kl_ratio(g.y, u0y, rm.y));
-        x(t + q * G::T) = rm;
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const size_t i = off + t + (q0 + b) * G::T;
+        if (!fresh) {
+          u[b].x = fmaf(lam, a[b].x, u[b].x);
+          u[b].y = fmaf(lam, a[b].y, u[b].y);
+          st2(uj, i, u[b]);
+        }
+        if (done == 0) {
+          float2 rm;
+          acc[0].add(kl_ratio(g[b].x, u[b].x + bk[b].x, rm.x));
+          acc[0].add(kl_ratio(g[b].y, u[b].y + bk[b].y, rm.y));
+          x(t + (q0 + b) * G::T) = rm;
+        }
       }
     }
   }
@@ -404,7 +430,7 @@ __device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ i
   if (arrive_last(d.ctrl, d.n_rv_items)) ctrl_sgp_begin<FP64>(d);
 }
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock) k_sgp_update_ratio(const ImgDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(kRowBlock, 4) k_sgp_update_ratio(const ImgDesc* __restrict__ imgs,
                                                                const int2* __restrict__ items, int n_items) {
   b_sgp_update_ratio<W, FP64>(imgs, items, n_items);
 }
@@ -437,16 +463,27 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
       float* gn = d.grad[ke & 1];
       const float L1 = float(c->L1), L2 = float(c->L2);
       const bool bb = ke >= 1;
-#pragma unroll 4
-      for (int q = 0; q < G::E; ++q) {
-        const size_t i = off + t + q * G::T;
-        const float2 v = x(t + q * G::T), w = w_pair(d, i);   // v = sum_j A_j^T (r_j - 1)
+      constexpr int B = batch_of<G::E, 4>();
+#pragma unroll 1
+      for (int q0 = 0; q0 < G::E; q0 += B) {
+        float2 wv[B], fcv[B], fov[B], gov[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          const size_t i = off + t + (q0 + b) * G::T;
+          wv[b] = w_pair(d, i);
+          const float2 z2 = make_float2(0.0f, 0.0f);
+          fcv[b] = bb ? ld2(f, i) : z2; fov[b] = bb ? ld2(fp, i) : z2; gov[b] = bb ? ld2(gp, i) : z2;
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+        const size_t i = off + t + (q0 + b) * G::T;
+        const float2 v = x(t + (q0 + b) * G::T), w = wv[b];   // v = sum_j A_j^T (r_j - 1)
         float2 gr;
         gr.x = w.x > 0.0f ? -v.x : 0.0f;
         gr.y = w.y > 0.0f ? -v.y : 0.0f;
         st2(gn, i, gr);
         if (bb) {
-          const float2 fc = ld2(f, i), fo = ld2(fp, i), go = ld2(gp, i);
+          const float2 fc = fcv[b], fo = fov[b], go = gov[b];
           const float sx = fc.x - fo.x, sy = fc.y - fo.y, zx = gr.x - go.x, zy = gr.y - go.y;
           const float Dx = w.x * clipf(fc.x, L1, L2), Dy = w.y * clipf(fc.y, L1, L2);
           if (Dx > 0.0f) {
@@ -458,6 +495,7 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
             acc[0].add(sd * sd); acc[1].add(sd * zy); acc[2].add(sy * zd); acc[3].add(zd * zd);
           }
         }
+        }
       }
     }
     block_sum_store<4, FP64>(acc, part_of(d, it) + SLOT_BB);
@@ -465,7 +503,7 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
   }
 }
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock) k_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(kRowBlock, 4) k_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
                                                           const int2* __restrict__ items, int n_items) {
   b_sgp_grad_bb<W, FP64>(imgs, items, n_items);
 }
@@ -494,16 +532,24 @@ __device__ __forceinline__ void b_sgp_y(const ImgDesc* __restrict__ imgs,
       const float* f = d.f[k & 1];
       const float* gr = d.grad[k & 1];
       const float alpha = float(c->alpha), mu = float(c->mu), L1 = float(c->L1), L2 = float(c->L2);
-#pragma unroll 4
-      for (int q = 0; q < G::E; ++q) {
-        const size_t i = off + t + q * G::T;
-        const float2 fv = ld2(f, i), gv = ld2(gr, i), w = w_pair(d, i);
-        const float yx = proj_step(fv.x, gv.x, w.x, alpha, mu, L1, L2);
-        const float yy = proj_step(fv.y, gv.y, w.y, alpha, mu, L1, L2);
-        const float dx = yx - fv.x, dy = yy - fv.y;
-        acc[0].add(gv.x * dx);
-        acc[0].add(gv.y * dy);
-        x(t + q * G::T) = make_float2(dx, dy);   // A d is transformed directly (no A y - A f cancellation)
+      constexpr int B = batch_of<G::E, 4>();
+#pragma unroll 1
+      for (int q0 = 0; q0 < G::E; q0 += B) {
+        float2 fv[B], gv[B], w[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          const size_t i = off + t + (q0 + b) * G::T;
+          fv[b] = ld2(f, i); gv[b] = ld2(gr, i); w[b] = w_pair(d, i);
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          const float yx = proj_step(fv[b].x, gv[b].x, w[b].x, alpha, mu, L1, L2);
+          const float yy = proj_step(fv[b].y, gv[b].y, w[b].y, alpha, mu, L1, L2);
+          const float dx = yx - fv[b].x, dy = yy - fv[b].y;
+          acc[0].add(gv[b].x * dx);
+          acc[0].add(gv[b].y * dy);
+          x(t + (q0 + b) * G::T) = make_float2(dx, dy);   // A d is transformed directly (no A y - A f cancellation)
+        }
       }
     }
     row_real_to_spec<W>(x, spec_plane(d, 0) + off, t, act);
@@ -551,9 +597,8 @@ __device__ __forceinline__ void b_sgp_ad_armijo(const ImgDesc* __restrict__ imgs
       const size_t i = off + t + q * G::T;
       const float2 ad = x(t + q * G::T), u = ld2(uj, i), g = ld2(gj, i), b = b_pair(d, j, i);
       st2(adj, i, ad);
-      const float u0x = u.x + b.x, u0y = u.y + b.y;
-      armijo_add<kArmMain>(acc, lam, g.x, u0x, ad.x);
-      armijo_add<kArmMain>(acc, lam, g.y, u0y, ad.y);
+      armijo_add<kArmMain>(acc, lam, g.x, u.x + b.x, ad.x);
+      armijo_add<kArmMain>(acc, lam, g.y, u.y + b.y, ad.y);
     }
   }
   block_sum_store<kArmMain, FP64>(acc, partv_of(d, it) + SLOT_ARM);
