@@ -592,13 +592,26 @@ __device__ __forceinline__ void b_sgp_ad_armijo(const ImgDesc* __restrict__ imgs
     const float* uj = d.u + size_t(j) * d.P;
     float* adj = d.Ad + size_t(j) * d.P;
     const float* gj = d.g + size_t(j) * d.P;
+    if (c->arm_nl == kArmMain) {
 #pragma unroll 2
-    for (int q = 0; q < G::E; ++q) {
-      const size_t i = off + t + q * G::T;
-      const float2 ad = x(t + q * G::T), u = ld2(uj, i), g = ld2(gj, i), b = b_pair(d, j, i);
-      st2(adj, i, ad);
-      armijo_add<kArmMain>(acc, lam, g.x, u.x + b.x, ad.x);
-      armijo_add<kArmMain>(acc, lam, g.y, u.y + b.y, ad.y);
+      for (int q = 0; q < G::E; ++q) {
+        const size_t i = off + t + q * G::T;
+        const float2 ad = x(t + q * G::T), u = ld2(uj, i), g = ld2(gj, i), b = b_pair(d, j, i);
+        st2(adj, i, ad);
+        armijo_add<kArmMain>(acc, lam, g.x, u.x + b.x, ad.x);
+        armijo_add<kArmMain>(acc, lam, g.y, u.y + b.y, ad.y);
+      }
+    } else {
+      KSum (&acc2)[kArmShort] = reinterpret_cast<KSum (&)[kArmShort]>(acc);
+      const float (&lam2)[kArmShort] = reinterpret_cast<const float (&)[kArmShort]>(lam);
+#pragma unroll 2
+      for (int q = 0; q < G::E; ++q) {
+        const size_t i = off + t + q * G::T;
+        const float2 ad = x(t + q * G::T), u = ld2(uj, i), g = ld2(gj, i), b = b_pair(d, j, i);
+        st2(adj, i, ad);
+        armijo_add<kArmShort>(acc2, lam2, g.x, u.x + b.x, ad.x);
+        armijo_add<kArmShort>(acc2, lam2, g.y, u.y + b.y, ad.y);
+      }
     }
   }
   block_sum_store<kArmMain, FP64>(acc, partv_of(d, it) + SLOT_ARM);
@@ -628,8 +641,8 @@ __device__ __forceinline__ void b_sgp_armijo_extra(const ImgDesc* __restrict__ i
     const size_t off = size_t(row) * G::M;
     const float th = float(c->theta);
     float lam0 = 1.0f;
-#pragma unroll
-    for (int l = 0; l < kArmMain; ++l) lam0 *= th;
+    const int nl = c->arm_nl == kArmMain ? kArmMain : kArmShort;
+    for (int l = 0; l < nl; ++l) lam0 *= th;
     KSum acc[kArmExtra];
     if (act) {
       for (int j = 0; j < d.p; ++j) {

@@ -21,14 +21,17 @@ enum Slot {
   SLOT_BB = 2,        // 4 slots: s'D^-2 s, s'D^-1 z, s'D z, z'D^2 z
   SLOT_GTD = 6,       // grad' d
   SLOT_FLUX = 7,      // sum f
-  SLOT_ARM = 8,       // kArmMain slots: Delta J(theta^i), i < kArmMain (main pass)
-  SLOT_ARMX = 12,     // kArmExtra slots: Delta J(theta^i), i = kArmMain..30 (only when needed)
-  SLOT_MIN = 40,      // min over positive pixels (set-up)
-  SLOT_MAX = 41,      // max (set-up)
-  SLOT_PROJ = 42,     // flux projection search sums (up to 6)
+  SLOT_ARM = 8,       // kArmMain slots: Delta J(theta^i), i < arm_nl (main pass)
+  SLOT_ARMX = 12,     // kArmExtra slots: Delta J(theta^i), i = arm_nl..30 (only when needed)
+  SLOT_MIN = 41,      // min over positive pixels (set-up)
+  SLOT_MAX = 42,      // max (set-up)
+  SLOT_PROJ = 43,     // flux projection search sums (5)
 };
-constexpr int kArmMain = 4;         // step lengths 1, theta, theta^2, theta^3 of the main Armijo pass
-constexpr int kArmExtra = 31 - kArmMain;
+// The main Armijo pass evaluates arm_nl step lengths 1, theta, ..: kArmShort while the previous
+// iteration accepted lambda >= theta, kArmMain after it needed a smaller one.
+constexpr int kArmMain = 4;
+constexpr int kArmShort = 2;
+constexpr int kArmExtra = 31 - kArmShort;
 constexpr int kFluxCand = 16;       // candidate mu values per flux-search pass (slots SLOT_ARMX..)
 constexpr int kFluxPasses = 5;
 
@@ -54,6 +57,7 @@ struct CtrlState {
   int constraint;   // 0 non-negativity, 1 + flux
   int proj_pass;    // flux projection search pass
   unsigned arrive;  // blocks of the current row pass that have stored their partial sums
+  int arm_nl;       // step lengths evaluated by the main Armijo pass (kArmShort or kArmMain)
   double J;         // J_0 at the current iterate
   double J_pred;    // J_0 at the accepted trial point
   double J_prev;    // RL: J_0 at the previous iterate
