@@ -193,6 +193,34 @@ def run_profile(args):
     return 0
 
 
+def cufft_comparison(torch, lib, prob, psf_d, g_d, reps=20):
+    """Comparison line: one forward operator A f at the workload's size through the library
+    (row R2C, column pass with the PSF spectrum, row C2R) and through cuFFT via torch.fft
+    (rfft2, product, irfft2), both on device-resident data, CUDA events, mean of `reps`."""
+    f = g_d[0].contiguous()
+    khat = torch.fft.rfft2(torch.fft.ifftshift(psf_d[0] / psf_d[0].sum()))
+    out = torch.empty_like(g_d)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(reps):
+            fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    ours_ms = timed(lambda: prob.apply_A(f, out=out))
+    ref = torch.fft.irfft2(torch.fft.rfft2(f) * khat, s=f.shape)
+    cufft_ms = timed(lambda: torch.fft.irfft2(torch.fft.rfft2(f) * khat, s=f.shape))
+    err = float(torch.linalg.vector_norm(out[0] - ref) / torch.linalg.vector_norm(ref))
+    return {"op": "A f (one periodic convolution)", "ours_ms": ours_ms, "cufft_torch_fft_ms": cufft_ms,
+            "rel_l2_difference": err}
+
+
 def run_ours(args):
     import torch
     if args.profile:
@@ -277,6 +305,8 @@ def run_ours(args):
     plain_info = plain.info()
     plain.close()
 
+    cufft = cufft_comparison(torch, lib, prob, psf_d, g_d)
+
     # end to end through the public API with host buffers
     f_h = torch.empty((N, N), dtype=torch.float32).pin_memory()
     e2e_ms, e2e_it = 0.0, 0
@@ -313,6 +343,7 @@ def run_ours(args):
             "plain_fp32": {"time_to_stop_ms": plain_ms, "iterations": it_plain, "final_kl": plain_info.J,
                            "final_discrepancy": plain_info.D, "iters_per_s": it_plain / (plain_ms / 1e3)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "cufft_comparison": cufft,
             "clocks": clocks}
     print(json.dumps(line))
     return 0

@@ -64,7 +64,14 @@ typedef enum {
   SGP_ERR_STATE = 9             /* call not valid in the current state */
 } sgp_status;
 
-enum { SGP_STOP_FIXED = 0, SGP_STOP_CONVERGENCE = 1, SGP_STOP_DISCREPANCY = 2, SGP_STOP_MIN_ERROR = 3 };
+enum { SGP_STOP_FIXED = 0, SGP_STOP_CONVERGENCE = 1, SGP_STOP_DISCREPANCY = 2, SGP_STOP_MIN_ERROR = 3,
+       SGP_STOP_DISCREPANCY_LANDED = 4 };
+/* SGP_STOP_DISCREPANCY_LANDED (SGP only): the discrepancy stop of Sect. 3.3 with the last step
+ * shortened so that the final discrepancy lies in [eta (1 - tol), eta] (tol <= 0 means 1e-5):
+ * two passes bracket lambda on [0, lambda_accepted] and a chord interpolation picks it; by
+ * convexity of J along the step the shortened step still satisfies the Armijo condition.  Runs
+ * stopped this way end at the same KL to within tol, whatever their start (the paper stops at
+ * the first iterate with D <= eta; this rule is a reading of it, not in the paper). */
 enum { SGP_START_ZERO = 0, SGP_START_DATA = 1, SGP_START_CONSTANT = 2, SGP_START_USER = 3 };
 enum { SGP_PSF_CENTER = 0, SGP_PSF_CORNER = 1 };
 
@@ -100,7 +107,7 @@ typedef struct {
 typedef struct {
   int kind;              /* SGP_STOP_* */
   int max_iter;          /* cap on the number of further iterations */
-  double tol;            /* convergence: |J_{k+1} - J_k| <= tol J_k */
+  double tol;            /* convergence: |J_{k+1} - J_k| <= tol J_k; landed discrepancy: band */
   double eta;            /* discrepancy: stop at the first k with 2 J_0 / (p |S|) <= eta */
 } sgp_stop_rule;
 
@@ -202,6 +209,18 @@ SGP_API sgp_status sgp_time_passes(sgp_ctx* ctx, int iters, double* ms_out, int 
 
 /* Number of kernels this context has enqueued so far (graph launches count their nodes). */
 SGP_API long long sgp_launch_count(sgp_ctx* ctx);
+
+/* Row tile of the hot row passes (contexts whose problems share one size).  A row pass runs one
+ * block per work item of R image rows, T = 256 / R_max threads per row, where R_max is the tile of
+ * a 256-thread block.  At the first iterate/solve call an autotuner times the projection pass for
+ * R = R_max, R_max/2, ... down to 32-thread blocks and keeps the fastest (the choice is shared by
+ * every context of the same H, W, p in the process).  sgp_get_tile reports R and the block size
+ * (R = 0 and 256 for mixed-size contexts); sgp_set_tile forces R (SGP_ERR_ARG if R is not a
+ * candidate, SGP_ERR_STATE for a mixed-size context), drops the captured graphs and makes the next
+ * iterate/solve call re-initialise from the current iterate.  Partial sums are grouped per work
+ * item, so results depend on R at rounding level. */
+SGP_API sgp_status sgp_get_tile(sgp_ctx* ctx, int* rows_per_item, int* threads_per_block);
+SGP_API sgp_status sgp_set_tile(sgp_ctx* ctx, int rows_per_item);
 
 /* Convolution without any device allocation, for callers that cannot allocate device memory --
  * for example code running where cudaMalloc is unavailable or forbidden (inside a captured region

@@ -223,7 +223,11 @@ class SGPParams:
 
 @dataclass
 class StopRule:
-    """Sect. 3.3: kind in {'fixed', 'convergence', 'discrepancy', 'min_error'}."""
+    """Sect. 3.3: kind in {'fixed', 'convergence', 'discrepancy', 'min_error', 'landed'}.
+
+    'landed' (SGP only; a reading, not in the paper): the discrepancy stop with the last step
+    shortened so that the final discrepancy is eta (1 - tol/2), found by bisection on the step
+    length; tol <= 0 means 1e-5."""
     kind: str = "fixed"
     max_iter: int = 100
     tol: float = 1e-4
@@ -334,9 +338,30 @@ class Result:
 def _stop_check(rule: StopRule, k: int, J_old: float, J_new: float, D_new: float) -> bool:
     if rule.kind == "convergence":
         return abs(J_new - J_old) <= rule.tol * J_old
-    if rule.kind == "discrepancy":
+    if rule.kind in ("discrepancy", "landed"):
         return D_new <= rule.eta
     return False
+
+
+def _land(prob: Problem, f, d, J, lam, Jn, rule: StopRule):
+    """Shorten an accepted step f + lam d whose discrepancy is below eta: the step length in
+    (0, lam] where D = eta (1 - tol/2), by bisection (J is convex along the step, J(0) above the
+    target, J(lam) below).  A(f + t d) = A f + t A d by linearity.  Returns (t, J(t), f + t d)."""
+    tol = rule.tol if rule.tol > 0 else 1e-5
+    Jt = rule.eta * (1.0 - 0.5 * tol) / prob.discrepancy(1.0)
+    if not (Jn < Jt < J):
+        return lam, Jn, f + lam * d
+    Afs = [prob.A(j, f) for j in range(prob.p)]
+    Ads = [prob.A(j, d) for j in range(prob.p)]
+    Jat = lambda t: prob.kl(f + t * d, [Afs[j] + t * Ads[j] for j in range(prob.p)])
+    lo, hi = 0.0, lam
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        if Jat(mid) > Jt:
+            lo = mid
+        else:
+            hi = mid
+    return hi, Jat(hi), f + hi * d
 
 
 def _rel_err(f, ft):
@@ -362,7 +387,7 @@ def sgp(prob: Problem, f0: np.ndarray | None = None, P: SGPParams | None = None,
     st = AlphaState(alpha_prev=P.alpha0, tau=P.tau1)
     g_prev = f_prev = None
     rho_prev = _rel_err(f, stop.f_true) if stop.kind == "min_error" else None
-    if stop.kind == "discrepancy" and prob.discrepancy(J) <= stop.eta:
+    if stop.kind in ("discrepancy", "landed") and prob.discrepancy(J) <= stop.eta:
         return Result(f, 0, J, trace, L1=L1, L2=L2)
     k = 0
     while k < stop.max_iter:
@@ -392,6 +417,8 @@ def sgp(prob: Problem, f0: np.ndarray | None = None, P: SGPParams | None = None,
             if nb > P.max_backtracks:
                 return Result(f, k, J, trace, status="linesearch", L1=L1, L2=L2)
             lam *= P.theta
+        if stop.kind == "landed" and prob.discrepancy(Jn) <= stop.eta:
+            lam, Jn, fl = _land(prob, f, d, J, lam, Jn, stop)
         # step 6
         f_prev, g_prev = f, grad
         f = fl

@@ -52,24 +52,37 @@ __device__ inline double bb_alpha(CtrlState* c, V n1, V d1, V n2, V d2, int k) {
   return double(alpha);
 }
 
-// The controller's working copy of the state: every thread loads one 8-byte word of it (in flight
-// while the partial sums are read), thread 0 decides on the shared copy, the block writes it back.
+// The controller's working copy of the state: every thread loads up to kCtrlPer 8-byte words of it
+// (in flight while the partial sums are read), thread 0 decides on the shared copy, the block
+// writes it back.  Blocks have at least 32 threads.
 constexpr int kCtrlWords = int(sizeof(CtrlState) / 8);
-static_assert(sizeof(CtrlState) % 8 == 0 && kCtrlWords <= kCtrlBlock && kCtrlWords <= kRowBlock,
-              "controller state must fit one word per thread");
+constexpr int kCtrlPer = 4;
+static_assert(sizeof(CtrlState) % 8 == 0 && kCtrlWords <= 32 * kCtrlPer,
+              "controller state must fit kCtrlPer words per thread of a 32-thread block");
 struct CtrlCopy {
-  unsigned long long w = 0ull;
+  unsigned long long w[kCtrlPer];
   __device__ __forceinline__ explicit CtrlCopy(const CtrlState* c) {
-    if (threadIdx.x < kCtrlWords) w = __ldcg(reinterpret_cast<const unsigned long long*>(c) + threadIdx.x);
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(c);
+#pragma unroll
+    for (int k = 0; k < kCtrlPer; ++k) {
+      const int i = threadIdx.x + k * blockDim.x;
+      w[k] = i < kCtrlWords ? __ldcg(src + i) : 0ull;
+    }
   }
   __device__ __forceinline__ void to_shared(CtrlState& s) const {
-    if (threadIdx.x < kCtrlWords) reinterpret_cast<unsigned long long*>(&s)[threadIdx.x] = w;
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s);
+#pragma unroll
+    for (int k = 0; k < kCtrlPer; ++k) {
+      const int i = threadIdx.x + k * blockDim.x;
+      if (i < kCtrlWords) dst[i] = w[k];
+    }
     __syncthreads();
   }
   __device__ __forceinline__ static void write_back(const CtrlState& s, CtrlState* c) {
     __syncthreads();
-    if (threadIdx.x < kCtrlWords)
-      reinterpret_cast<unsigned long long*>(c)[threadIdx.x] = reinterpret_cast<const unsigned long long*>(&s)[threadIdx.x];
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&s);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(c);
+    for (int i = threadIdx.x; i < kCtrlWords; i += blockDim.x) dst[i] = src[i];
   }
 };
 
@@ -135,8 +148,58 @@ __device__ inline void sgp_accept(const ImgDesc& d, CtrlState* c, int nb, double
   trace_push(d, c, kn, c->J_pred, c->alpha, lam, nb, c->branch, c->gTd);
   bool stop = kn >= c->max_iter;
   if (c->stop_kind == STOP_CONVERGENCE && fabs(c->J_pred - c->J) <= c->tol * c->J) stop = true;
-  if (c->stop_kind == STOP_DISCREPANCY && 2.0 * c->J_pred * c->inv_pS <= c->eta) stop = true;
+  if ((c->stop_kind == STOP_DISCREPANCY || c->stop_kind == STOP_LANDED) && 2.0 * c->J_pred * c->inv_pS <= c->eta) {
+    stop = true;
+    // landed stop: shorten this step so that the discrepancy ends in [eta (1 - tol), eta]
+    const double Jt = c->eta * (1.0 - 0.5 * c->tol) / (2.0 * c->inv_pS);
+    if (c->stop_kind == STOP_LANDED && c->J_pred < Jt && c->J > Jt) {
+      c->land_pass = 1;
+      c->land_lo = 0.0; c->land_hi = lam;
+      c->land_Jlo = c->J; c->land_Jhi = c->J_pred; c->land_Jt = Jt;
+      return;                         // the landing passes decide lambda and set done
+    }
+  }
   if (stop) c->done = 1;
+}
+
+// After a landing pass (K8): the candidates lam_i = lo + (i + 1) (hi - lo)/(kLandCand + 1) give
+// J(lam_i) = J + Delta J(lam_i).  J is convex along the step and J(lo) > Jt >= J(hi), so the first
+// candidate with J <= Jt closes the new bracket.  After the last pass lambda interpolates J
+// linearly between the bracket ends; by convexity the chord lies above J, so the stored J_pred
+// (= Jt) bounds the true value from above and the discrepancy ends at most eta (1 - tol/2).
+__device__ inline void sgp_land_decide(const ImgDesc& d, CtrlState* c, const double (&dj)[kLandCand]) {
+  const double lo = c->land_lo, hi = c->land_hi, h = (hi - lo) / double(kLandCand + 1);
+  double nlo = lo, nhi = hi, Jlo = c->land_Jlo, Jhi = c->land_Jhi;
+  for (int i = 0; i < kLandCand; ++i) {
+    const double Ji = c->J + dj[i];
+    if (!(Ji > c->land_Jt)) { nhi = lo + double(i + 1) * h; Jhi = Ji; break; }
+    nlo = lo + double(i + 1) * h; Jlo = Ji;
+  }
+  c->land_lo = nlo; c->land_hi = nhi; c->land_Jlo = Jlo; c->land_Jhi = Jhi;
+  c->land_pass += 1;
+  if (c->land_pass <= kLandPasses) return;
+  const double w = Jlo > Jhi ? (Jlo - c->land_Jt) / (Jlo - Jhi) : 1.0;
+  const double lam = nlo + fmin(fmax(w, 0.0), 1.0) * (nhi - nlo);
+  const double Jp = Jlo + fmin(fmax(w, 0.0), 1.0) * (Jhi - Jlo);
+  c->lambda = lam;
+  c->dJ = Jp - c->J;
+  c->J_pred = Jp;
+  c->land_pass = 0;
+  c->done = 1;
+  if (c->trace_n >= 1 && c->trace_n <= c->trace_cap) {   // the record sgp_accept wrote
+    double* r = d.trace + size_t(c->trace_n - 1) * kTraceStride;
+    r[1] = Jp; r[2] = 2.0 * Jp * c->inv_pS; r[4] = lam;
+  }
+}
+template <bool FP64>
+__device__ void ctrl_sgp_land(const ImgDesc& d) {
+  __shared__ CtrlState s;
+  const CtrlCopy cp(d.ctrl);
+  double dj[kLandCand];
+  ctrl_sum<kLandCand, FP64>(d, SLOT_ARMX, dj, false);
+  cp.to_shared(s);
+  if (threadIdx.x == 0) sgp_land_decide(d, &s, dj);
+  CtrlCopy::write_back(s, d.ctrl);
 }
 
 template <bool FP64>

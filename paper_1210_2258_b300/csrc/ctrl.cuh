@@ -45,6 +45,7 @@ __global__ void k_ctrl_arm(const ImgDesc* __restrict__ imgs, int n, int kind, in
   c->done = 0;
   c->result_prev = 0;
   c->need_more = 0;
+  c->land_pass = 0;
 }
 
 // ------------------------------------------------------------------------------ flux projection

@@ -18,6 +18,7 @@ void register_side(Registry& R) {
   SGP_ROW_BOTH(ROP_SGP_Y, k_sgp_y)
   SGP_ROW_BOTH(ROP_SGP_AD, k_sgp_ad_armijo)
   SGP_ROW_BOTH(ROP_SGP_ARMX, k_sgp_armijo_extra)
+  SGP_ROW_BOTH(ROP_SGP_LAND, k_sgp_land)
   SGP_ROW_BOTH(ROP_RL_UPDATE, k_rl_update)
   SGP_ROW_BOTH(ROP_RL_RATIO, k_rl_ratio)
 #undef SGP_ROW_BOTH

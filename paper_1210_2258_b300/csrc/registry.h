@@ -15,7 +15,7 @@ inline int side_index(int n) {
 
 enum RowOp {
   ROP_SGP_UPDATE = 0, ROP_SGP_GRAD, ROP_SGP_Y, ROP_SGP_AD, ROP_SGP_ARMX, ROP_RL_UPDATE, ROP_RL_RATIO,
-  ROP_MINMAX, ROP_R2C, ROP_C2R, ROP_COUNT
+  ROP_MINMAX, ROP_R2C, ROP_C2R, ROP_SGP_LAND, ROP_COUNT
 };
 // column variants: COL_KHAT, COL_1TOP, COL_1TOP_CONJ, COL_PTO1 (any p), COL_PTO1 for p = 1, p = 3
 constexpr int kColModes = 6;

@@ -112,23 +112,26 @@ __device__ __forceinline__ void armijo_add(KSum (&acc)[N], const float (&lam)[N]
     acc[l].add(q <= -1.0f ? f_inf() : fmaf(gm, q, g * phi_t(q)));
   }
 }
-// the same for the step lengths lam0 th^l, l = 0..N-1 (running products: few registers)
-template <int N>
-__device__ __forceinline__ void armijo_add_geom(KSum (&acc)[N], float lam0, float th, float g, float u0, float ad) {
+// the same for the step lengths lam0 th^l (GEOM) or lam0 + l th (arithmetic), l = 0..N-1, as
+// running products or sums (few registers)
+template <int N, bool GEOM>
+__device__ __forceinline__ void armijo_add_prog(KSum (&acc)[N], float lam0, float th, float g, float u0, float ad) {
   if (g < 0.0f) return;
-  float q, gm = 0.0f;
-  if (g == 0.0f) q = lam0 * ad;
-  else if (u0 > 0.0f) { q = lam0 * fdiv(ad, u0); gm = u0 - g; }
+  float a;
+  if (g == 0.0f) a = ad;                      // q = lam A d here
+  else if (u0 > 0.0f) a = fdiv(ad, u0);
   else {
 #pragma unroll
     for (int l = 0; l < N; ++l) acc[l].add(f_inf());
     return;
   }
+  const float gm = u0 - g, dq = th * a;
+  float q = lam0 * a;
 #pragma unroll
   for (int l = 0; l < N; ++l) {
-    if (g == 0.0f) acc[l].add(q);             // q = lam A d here
+    if (g == 0.0f) acc[l].add(q);
     else acc[l].add(q <= -1.0f ? f_inf() : fmaf(gm, q, g * phi_t(q)));
-    q *= th;
+    q = GEOM ? q * th : q + dq;
   }
 }
 // The row passes transform r - 1 on S (0 outside S) instead of r, so that
@@ -623,10 +626,12 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_ad_armijo(const ImgDesc* __re
   b_sgp_ad_armijo<W, FP64>(imgs, items, n_items);
 }
 
-// SGP K7 (only when no lambda of the main pass was accepted): Delta J(theta^i), i = kArmMain..30.
-template <int W, bool FP64>
-__device__ __forceinline__ void b_sgp_armijo_extra(const ImgDesc* __restrict__ imgs,
-                                                               const int2* __restrict__ items, int n_items) {
+// SGP K7 (only when no lambda of the main pass was accepted): Delta J(theta^i), i = arm_nl..30.
+// K8 (LAND, landed discrepancy stop only): Delta J at kLandCand equally spaced step lengths inside
+// the current landing bracket.  Both read A f, A d, g of every view.
+template <int W, bool FP64, bool LAND>
+__device__ __forceinline__ void b_sgp_lambda_scan(const ImgDesc* __restrict__ imgs,
+                                                  const int2* __restrict__ items, int n_items) {
   using G = RowGeo<W>;
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
   {
@@ -635,14 +640,22 @@ __device__ __forceinline__ void b_sgp_armijo_extra(const ImgDesc* __restrict__ i
     const int2 item = items[it];
     const ImgDesc& d = imgs[item.x];
     const CtrlState* c = d.ctrl;
-    if (c->done >= 1 || !c->need_more) return;
+    if (c->done >= 1) return;
+    if (LAND ? c->land_pass < 1 : !c->need_more) return;
     const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
-    const float th = float(c->theta);
-    float lam0 = 1.0f;
-    const int nl = c->arm_nl == kArmMain ? kArmMain : kArmShort;
-    for (int l = 0; l < nl; ++l) lam0 *= th;
+    float lam0, step;
+    if (LAND) {
+      const double h = (c->land_hi - c->land_lo) / double(kLandCand + 1);
+      lam0 = float(c->land_lo + h);
+      step = float(h);
+    } else {
+      step = float(c->theta);
+      lam0 = 1.0f;
+      const int nl = c->arm_nl == kArmMain ? kArmMain : kArmShort;
+      for (int l = 0; l < nl; ++l) lam0 *= step;
+    }
     KSum acc[kArmExtra];
     if (act) {
       for (int j = 0; j < d.p; ++j) {
@@ -652,19 +665,27 @@ __device__ __forceinline__ void b_sgp_armijo_extra(const ImgDesc* __restrict__ i
         for (int q = 0; q < G::E; ++q) {
           const size_t i = off + t + q * G::T;
           const float2 u = ld2(uj, i), ad = ld2(adj, i), g = ld2(gj, i), b = b_pair(d, j, i);
-          armijo_add_geom<kArmExtra>(acc, lam0, th, g.x, u.x + b.x, ad.x);
-          armijo_add_geom<kArmExtra>(acc, lam0, th, g.y, u.y + b.y, ad.y);
+          armijo_add_prog<kArmExtra, !LAND>(acc, lam0, step, g.x, u.x + b.x, ad.x);
+          armijo_add_prog<kArmExtra, !LAND>(acc, lam0, step, g.y, u.y + b.y, ad.y);
         }
       }
     }
     block_sum_store<kArmExtra, FP64>(acc, part_of(d, it) + SLOT_ARMX);
-    if (arrive_last(d.ctrl, d.n_row_items)) ctrl_sgp_lambda_extra<FP64>(d);
+    if (arrive_last(d.ctrl, d.n_row_items)) {
+      if (LAND) ctrl_sgp_land<FP64>(d);
+      else ctrl_sgp_lambda_extra<FP64>(d);
+    }
   }
 }
 template <int W, bool FP64>
 __global__ void __launch_bounds__(kRowBlock) k_sgp_armijo_extra(const ImgDesc* __restrict__ imgs,
                                                                const int2* __restrict__ items, int n_items) {
-  b_sgp_armijo_extra<W, FP64>(imgs, items, n_items);
+  b_sgp_lambda_scan<W, FP64, false>(imgs, items, n_items);
+}
+template <int W, bool FP64>
+__global__ void __launch_bounds__(kRowBlock) k_sgp_land(const ImgDesc* __restrict__ imgs,
+                                                       const int2* __restrict__ items, int n_items) {
+  b_sgp_lambda_scan<W, FP64, true>(imgs, items, n_items);
 }
 
 // RL K1: if plane 0 holds v = sum_j A_j^T r_j, f <- w f v (Eq. RL / multipleRL / boundaryRL);

@@ -6,7 +6,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/sgp.h"
@@ -96,6 +99,9 @@ struct Carver {
 };
 
 int rows_per_item(int W) { return g_reg.row_rows[side_index(W)]; }
+// Rows per work item of the hot row passes: the autotuner tries R_max / 2^k (R_max the rows of a
+// 256-thread block) down to blocks of 32 threads (T = 256 / R_max threads per row).
+int rows_min(int W) { return std::max(1, rows_per_item(W) / 8); }
 int cols_per_item(int H) { return g_reg.col_cols[side_index(H)]; }
 
 struct Layout {
@@ -115,6 +121,7 @@ struct Layout {
   int* d_flag = nullptr;
   size_t bytes = 0;
   int n_row = 0, n_rv = 0, n_colv = 0, n_col = 0, n_colk = 0, n_jobs = 0;
+  int cap_row = 0, cap_rv = 0;         // capacity of the row lists (smallest tile)
 };
 
 // Count items and carve every array (base == nullptr: only measure).
@@ -127,6 +134,7 @@ void plan_layout(char* base, int n, const sgp_shape* sh, int trace_cap, const bo
   L.scratch.assign(n, nullptr);
   L.mS.assign(n, nullptr);
   L.n_row = L.n_rv = L.n_colv = L.n_col = L.n_colk = 0;
+  L.cap_row = L.cap_rv = 0;
   for (int i = 0; i < n; ++i) {
     const int H = sh[i].H, W = sh[i].W, p = sh[i].p;
     const size_t P = size_t(H) * W;
@@ -135,9 +143,11 @@ void plan_layout(char* base, int n, const sgp_shape* sh, int trace_cap, const bo
     const int rpi = rows_per_item(W), cpi = cols_per_item(H), M = W / 2;
     d.rpi = rpi;
     const int nr = (H + rpi - 1) / rpi, nc = (M + cpi - 1) / cpi;
+    const int ncap = (H + rows_min(W) - 1) / rows_min(W);   // item capacity for the smallest tile
     d.row_item0 = 0; d.n_row_items = nr;      // indices within the problem's own range
     d.rv_item0 = 0; d.n_rv_items = nr * p;
     L.n_row += nr; L.n_rv += nr * p; L.n_col += nc; L.n_colv += nc * p; L.n_colk += nc * p;
+    L.cap_row += ncap; L.cap_rv += ncap * p;
     d.f[0] = cv.take<float>(P); d.f[1] = cv.take<float>(P);
     d.grad[0] = cv.take<float>(P); d.grad[1] = cv.take<float>(P);
     d.u = cv.take<float>(P * p);
@@ -149,8 +159,8 @@ void plan_layout(char* base, int n, const sgp_shape* sh, int trace_cap, const bo
     d.spec = cv.take<float>(P * (p + 1));
     L.khat[i] = cv.take<float>(P * p);
     L.khatq[i] = cv.take<float>(size_t(2) * H * p);
-    d.part = cv.take<double>(size_t(nr) * kPartStride);
-    d.partv = cv.take<double>(size_t(nr) * p * kPartStride);
+    d.part = cv.take<double>(size_t(ncap) * kPartStride);
+    d.partv = cv.take<double>(size_t(ncap) * p * kPartStride);
     d.trace = cv.take<double>(size_t(trace_cap) * kTraceStride);
     L.scratch[i] = cv.take<double>(64);
     L.mS[i] = d.boundary ? cv.take<uint8_t>(P) : nullptr;
@@ -158,8 +168,8 @@ void plan_layout(char* base, int n, const sgp_shape* sh, int trace_cap, const bo
   L.ctrl = cv.take<CtrlState>(n);
   for (int i = 0; i < n; ++i) L.d[i].ctrl = L.ctrl ? L.ctrl + i : nullptr;
   L.d_imgs = cv.take<ImgDesc>(n);
-  L.d_row = cv.take<int2>(L.n_row);
-  L.d_rv = cv.take<int2>(L.n_rv);
+  L.d_row = cv.take<int2>(L.cap_row);
+  L.d_rv = cv.take<int2>(L.cap_rv);
   L.d_colv = cv.take<int2>(L.n_colv);
   L.d_col = cv.take<int2>(L.n_col);
   L.d_colk = cv.take<int2>(L.n_colk);
@@ -188,6 +198,11 @@ struct sgp_ctx {
   int fp64 = 1;
   // host mirrors
   std::vector<int2> row, rv, colv, col, colk;
+  std::vector<int> order;          // problems, largest first (the order of their items)
+  int rpi_hot = 0;                 // rows per item of the hot row passes (uniform sizes)
+  int row_threads = kRowBlock;     // threads per block of the hot row passes
+  size_t row_smem_hot = 0;
+  bool tuned = false;
   std::vector<ColJob> jobs;        // per problem: [A, AT, CONJ, A_raw, AT_raw, KHAT x p]
   std::vector<int> job_base;
   std::vector<int> colv_begin, colv_count, col_begin, col_count;
@@ -197,7 +212,7 @@ struct sgp_ctx {
   std::vector<const float*> truth;
   std::vector<int> start_in_f0;    // 1: a new start was written to f[0] since the last set-up
   int mode = 0;                    // 0 not prepared, 1 SGP, 2 RL
-  cudaGraphExec_t g_sgp = nullptr, g_rl = nullptr;
+  cudaGraphExec_t g_sgp = nullptr, g_rl = nullptr, g_land = nullptr;   // g_land: SGP + landing passes
   int graph_units = 8;
   long long launches = 0;          // kernels enqueued (graph nodes counted per graph launch)
   CtrlState* h_ctrl = nullptr;     // pinned mirror of the controller array (2 slots for polling)
@@ -218,12 +233,50 @@ sgp_status launch(const void* fn, int grid, int block, size_t smem, cudaStream_t
 sgp_status row_pass(sgp_ctx* c, RowOp op, bool view_list, int extra = -1) {
   const int si = side_index(c->W);
   const void* fn = c->mixed ? g_reg.row_multi[op][c->fp64] : g_reg.row[op][c->fp64][si];
-  const size_t smem = c->mixed ? g_reg.row_multi_smem : g_reg.row_smem[si];
+  const size_t smem = c->mixed ? g_reg.row_multi_smem : c->row_smem_hot;
+  const int threads = c->mixed ? kRowBlock : c->row_threads;
   const ImgDesc* imgs = c->L.d_imgs;
   const int2* items = view_list ? c->L.d_rv : c->L.d_row;
   int n = view_list ? c->L.n_rv : c->L.n_row;
   void* args4[] = {(void*)&imgs, (void*)&items, (void*)&n, (void*)&extra};
-  return launch(fn, n, kRowBlock, smem, c->s, args4);
+  return launch(fn, n, threads, smem, c->s, args4);
+}
+
+// Row lists of the hot passes with R rows per item (every problem of a uniform context; a mixed
+// context keeps the 256-thread tiles of the multi-size kernels), uploaded with the descriptors.
+sgp_status fill_row_items(sgp_ctx* c, int R) {
+  Layout& L = c->L;
+  c->row.clear();
+  c->rv.clear();
+  int r0 = 0, rv0 = 0;
+  for (int i : c->order) {
+    ImgDesc& d = L.d[i];
+    const int rpi = c->mixed ? rows_per_item(d.W) : R;
+    d.rpi = rpi;
+    d.row_item0 = r0;
+    d.rv_item0 = rv0;
+    d.n_row_items = (d.H + rpi - 1) / rpi;
+    d.n_rv_items = d.n_row_items * d.p;
+    for (int y = 0; y < d.H; y += rpi) c->row.push_back(make_int2(i, y));
+    for (int j = 0; j < d.p; ++j)
+      for (int y = 0; y < d.H; y += rpi) c->rv.push_back(make_int2(i, y | (j << 16)));
+    r0 += d.n_row_items;
+    rv0 += d.n_rv_items;
+  }
+  if (r0 > L.cap_row || rv0 > L.cap_rv) return fail(SGP_ERR_ARG, "row tile below the planned minimum");
+  L.n_row = r0;
+  L.n_rv = rv0;
+  if (!c->mixed) {
+    const int si = side_index(c->W), rm = g_reg.row_rows[si];
+    c->rpi_hot = R;
+    c->row_threads = R * (kRowBlock / rm);
+    c->row_smem_hot = g_reg.row_smem[si] / size_t(rm) * size_t(R);
+  }
+  CU(cudaMemcpyAsync(L.d_imgs, L.d.data(), sizeof(ImgDesc) * c->n, cudaMemcpyHostToDevice, c->s));
+  CU(cudaMemcpyAsync(L.d_row, c->row.data(), sizeof(int2) * c->row.size(), cudaMemcpyHostToDevice, c->s));
+  CU(cudaMemcpyAsync(L.d_rv, c->rv.data(), sizeof(int2) * c->rv.size(), cudaMemcpyHostToDevice, c->s));
+  CU(cudaStreamSynchronize(c->s));
+  return SGP_OK;
 }
 
 // variant: COL_1TOP (views list), COL_1TOP_CONJ, COL_PTO1; job_off selects A/AT/CONJ/raw jobs
@@ -322,7 +375,7 @@ sgp_status seq_flux(sgp_ctx* c) {
   return SGP_OK;
 }
 
-sgp_status seq_sgp_unit(sgp_ctx* c) {
+sgp_status seq_sgp_unit(sgp_ctx* c, bool land = false) {
   sgp_status st;
   if ((st = row_pass(c, ROP_SGP_UPDATE, true))) return st;     // + iteration controller
   if ((st = col_pass(c, COL_PTO1, JOB_AT * c->n))) return st;
@@ -331,20 +384,23 @@ sgp_status seq_sgp_unit(sgp_ctx* c) {
   if ((st = row_pass(c, ROP_SGP_Y, false))) return st;
   if ((st = col_pass(c, COL_1TOP, JOB_A * c->n))) return st;
   if ((st = row_pass(c, ROP_SGP_AD, true))) return st;         // + line-search controller
-  return row_pass(c, ROP_SGP_ARMX, false);                     // + its continuation
+  if ((st = row_pass(c, ROP_SGP_ARMX, false))) return st;      // + its continuation
+  for (int i = 0; land && i < kLandPasses; ++i)                // landed stop: shorten the last step
+    if ((st = row_pass(c, ROP_SGP_LAND, false))) return st;
+  return SGP_OK;
 }
 
 // a stop decided in the last unit of a graph leaves the update f^(k+1) = f^(k) + lambda d pending
 sgp_status seq_sgp_finalize(sgp_ctx* c) { return row_pass(c, ROP_SGP_UPDATE, true); }
 
-sgp_status build_graph(sgp_ctx* c, bool sgp, cudaGraphExec_t* out) {
+sgp_status build_graph(sgp_ctx* c, bool sgp, cudaGraphExec_t* out, bool land = false) {
   if (*out) return SGP_OK;
   cudaGraph_t g = nullptr;
   CU(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
   long long* saved = g_launch_counter;
   g_launch_counter = nullptr;
   sgp_status st = SGP_OK;
-  for (int u = 0; u < c->graph_units && st == SGP_OK; ++u) st = sgp ? seq_sgp_unit(c) : seq_rl_unit(c);
+  for (int u = 0; u < c->graph_units && st == SGP_OK; ++u) st = sgp ? seq_sgp_unit(c, land) : seq_rl_unit(c);
   cudaError_t e = cudaStreamEndCapture(c->s, &g);
   g_launch_counter = saved;
   if (st) { if (g) cudaGraphDestroy(g); return st; }
@@ -390,11 +446,56 @@ sgp_status reset_ctrl(sgp_ctx* c) {
 }
 
 // Set-up passes from f^(0): A_j f0 (kept in u), J_0, one RL step -> L1/L2 (SGP).  mode 1 SGP, 2 RL.
+// Autotuner of the row tile: time the projection pass K4 (a row FFT with pointwise work and partial
+// sums that changes no iteration state) for every candidate rows-per-item R (256-thread tiles down
+// to 32-thread ones), keep the fastest (a smaller tile must win by 3 %), and remember the choice for
+// the process per (H, W, p) so that contexts of one size share it (and their summation order).
+sgp_status autotune_rows(sgp_ctx* c) {
+  static std::map<std::tuple<int, int, int>, int> cache;
+  static std::mutex mu;
+  const auto key = std::make_tuple(c->H, c->W, c->p);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return fill_row_items(c, it->second);
+  }
+  const int rmax = rows_per_item(c->W), rmin = rows_min(c->W);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  sgp_status st = SGP_OK;
+  float best = 0.0f;
+  int best_r = rmax;
+  for (int R = rmax; R >= rmin && st == SGP_OK; R /= 2) {
+    if ((st = fill_row_items(c, R))) break;
+    if ((st = row_pass(c, ROP_SGP_Y, false))) break;           // warm-up
+    cudaEventRecord(e0, c->s);
+    for (int r = 0; r < 3 && st == SGP_OK; ++r) st = row_pass(c, ROP_SGP_Y, false);
+    cudaEventRecord(e1, c->s);
+    float ms = 0.0f;
+    if (st == SGP_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      st = fail(SGP_ERR_CUDA, "autotuner timing failed");
+    if (st == SGP_OK && (R == rmax || ms < 0.97f * best)) { best = ms; best_r = R; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    cache.emplace(key, best_r);
+  }
+  return fill_row_items(c, best_r);
+}
+
 sgp_status prepare(sgp_ctx* c, int mode) {
   for (int i = 0; i < c->n; ++i)
     if (!c->has_data[i]) return fail(SGP_ERR_STATE, "sgp_set_data was not called for every problem");
   sgp_status st;
   if ((st = reset_ctrl(c))) return st;
+  if (!c->mixed && !c->tuned) {
+    c->tuned = true;
+    if ((st = autotune_rows(c))) return st;
+  }
   if (c->prm.constraint == 1 && mode == 1) {   // flux-constrained start: scale f0 to sum c
     for (int i = 0; i < c->n; ++i) {
       ImgDesc& d = c->L.d[i];
@@ -470,20 +571,27 @@ sgp_status run_fixed(sgp_ctx* c, bool sgp, int n_iter) {
 
 sgp_status run_until(sgp_ctx* c, bool sgp, const sgp_stop_rule* rule, int* iters) {
   if (!rule) return fail(SGP_ERR_ARG, "rule is NULL");
-  if (rule->kind < 0 || rule->kind > 3) return fail(SGP_ERR_ARG, "unknown stop rule");
+  if (rule->kind < 0 || rule->kind > 4) return fail(SGP_ERR_ARG, "unknown stop rule");
   if (rule->max_iter <= 0) return fail(SGP_ERR_ARG, "max_iter must be positive");
+  const bool land = rule->kind == STOP_LANDED;
+  if (land && !sgp) return fail(SGP_ERR_ARG, "the landed discrepancy stop is an SGP rule");
+  if (land && !(rule->tol < 0.5)) return fail(SGP_ERR_ARG, "landed stop: tol must be below 0.5");
+  const double tol = land && rule->tol <= 0.0 ? 1e-5 : rule->tol;
   sgp_status st;
   if (c->mode != (sgp ? 1 : 2) && (st = prepare(c, sgp ? 1 : 2))) return st;
   if (rule->kind == STOP_MIN_ERROR)
     for (int i = 0; i < c->n; ++i)
       if (!c->truth[i]) return fail(SGP_ERR_ARG, "minimum-error stop needs sgp_set_truth");
-  if ((st = build_graph(c, sgp, sgp ? &c->g_sgp : &c->g_rl))) return st;
-  if ((st = arm(c, rule->kind, rule->max_iter, rule->tol, rule->eta))) return st;
-  cudaGraphExec_t g = sgp ? c->g_sgp : c->g_rl;
+  cudaGraphExec_t* gp = land ? &c->g_land : (sgp ? &c->g_sgp : &c->g_rl);
+  if ((st = build_graph(c, sgp, gp, land))) return st;
+  if ((st = arm(c, rule->kind, rule->max_iter, tol, rule->eta))) return st;
+  cudaGraphExec_t g = *gp;
   const int max_launches = rule->max_iter / c->graph_units + 2;
   CtrlState* slot[2] = {c->h_ctrl, c->h_ctrl + c->n};
   // keep one chunk in flight while the flags of the previous one are inspected
-  const int per_graph = c->graph_units * (sgp ? (c->prm.constraint == 1 ? kSgpLaunches + kFluxLaunches : kSgpLaunches) : kRlLaunches);
+  const int per_graph = c->graph_units * (sgp ? (c->prm.constraint == 1 ? kSgpLaunches + kFluxLaunches : kSgpLaunches) +
+                                                    (land ? kLandPasses : 0)
+                                              : kRlLaunches);
   CU(cudaGraphLaunch(g, c->s));
   c->launches += per_graph;
   CU(cudaMemcpyAsync(slot[0], c->L.ctrl, sizeof(CtrlState) * c->n, cudaMemcpyDeviceToHost, c->s));
@@ -629,16 +737,11 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return L.d[a].P > L.d[b].P; });
-  int r0 = 0, rv0 = 0;
+  c->order = order;
   c->colv_begin.resize(n); c->colv_count.resize(n); c->col_begin.resize(n); c->col_count.resize(n);
   for (int i : order) {
     ImgDesc& d = L.d[i];
-    const int rpi = rows_per_item(d.W), cpi = cols_per_item(d.H), M = d.W / 2;
-    d.row_item0 = r0; d.rv_item0 = rv0;
-    for (int y = 0; y < d.H; y += rpi) c->row.push_back(make_int2(i, y));
-    for (int j = 0; j < d.p; ++j)
-      for (int y = 0; y < d.H; y += rpi) c->rv.push_back(make_int2(i, y | (j << 16)));
-    r0 += d.n_row_items; rv0 += d.n_rv_items;
+    const int cpi = cols_per_item(d.H), M = d.W / 2;
     c->colv_begin[i] = int(c->colv.size());
     for (int j = 0; j < d.p; ++j)
       for (int x = 0; x < M; x += cpi) c->colv.push_back(make_int2(i, x | (j << 16)));
@@ -729,13 +832,11 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
   }
   if (st) return bail(st);
   if (cudaMemcpyAsync(L.d_jobs, c->jobs.data(), sizeof(ColJob) * L.n_jobs, cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
-      cudaMemcpyAsync(L.d_imgs, L.d.data(), sizeof(ImgDesc) * n, cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
-      cudaMemcpyAsync(L.d_row, c->row.data(), sizeof(int2) * c->row.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
-      cudaMemcpyAsync(L.d_rv, c->rv.data(), sizeof(int2) * c->rv.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
       cudaMemcpyAsync(L.d_colv, c->colv.data(), sizeof(int2) * c->colv.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
       cudaMemcpyAsync(L.d_col, c->col.data(), sizeof(int2) * c->col.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
       cudaMemcpyAsync(L.d_colk, c->colk.data(), sizeof(int2) * c->colk.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess)
     return bail(fail(SGP_ERR_CUDA, "descriptor upload failed"));
+  if ((st = fill_row_items(c, rows_per_item(c->W)))) return bail(st);
   for (int i = 0; i < n; ++i) {  // PSF spectra (forward column transforms, P/Q packing, scaling, shift)
     const int si = side_index(L.d[i].H);
     const ColJob* jobs = L.d_jobs;
@@ -1126,10 +1227,38 @@ sgp_status sgp_time_passes(sgp_ctx* c, int iters, double* ms_out, int n_out) {
 
 long long sgp_launch_count(sgp_ctx* c) { return c ? c->launches : 0; }
 
+sgp_status sgp_get_tile(sgp_ctx* c, int* rows_per_item_out, int* threads_out) {
+  if (!c || !rows_per_item_out || !threads_out) return fail(SGP_ERR_ARG, "NULL argument");
+  *rows_per_item_out = c->mixed ? 0 : c->rpi_hot;
+  *threads_out = c->mixed ? kRowBlock : c->row_threads;
+  return SGP_OK;
+}
+
+sgp_status sgp_set_tile(sgp_ctx* c, int rows) {
+  if (!c) return fail(SGP_ERR_ARG, "ctx is NULL");
+  if (c->mixed) return fail(SGP_ERR_STATE, "contexts of mixed sizes keep the multi-size tiles");
+  const int rmax = rows_per_item(c->W), rmin = rows_min(c->W);
+  bool ok = false;
+  for (int R = rmax; R >= rmin; R /= 2) ok = ok || R == rows;
+  if (!ok) return fail(SGP_ERR_ARG, "rows per item must be R_max / 2^k with at least 32 threads per block");
+  sgp_status st = enter(c);
+  if (st) return st;
+  CU(cudaStreamSynchronize(c->s));
+  // captured graphs hold the old launch geometry
+  if (c->g_sgp) { cudaGraphExecDestroy(c->g_sgp); c->g_sgp = nullptr; }
+  if (c->g_land) { cudaGraphExecDestroy(c->g_land); c->g_land = nullptr; }
+  if (c->g_rl) { cudaGraphExecDestroy(c->g_rl); c->g_rl = nullptr; }
+  if ((st = fill_row_items(c, rows))) return st;
+  c->tuned = true;
+  c->mode = 0;   // the next solve re-initialises the iteration from the current iterate
+  return leave(c);
+}
+
 sgp_status sgp_destroy(sgp_ctx* c) {
   if (!c) return SGP_OK;
   if (c->s) cudaStreamSynchronize(c->s);
   if (c->g_sgp) cudaGraphExecDestroy(c->g_sgp);
+  if (c->g_land) cudaGraphExecDestroy(c->g_land);
   if (c->g_rl) cudaGraphExecDestroy(c->g_rl);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);

@@ -37,7 +37,9 @@ constexpr int kFluxPasses = 5;
 
 enum ColMode { COL_KHAT = 0, COL_1TOP = 1, COL_1TOP_CONJ = 2, COL_PTO1 = 3 };
 
-enum StopKind { STOP_FIXED = 0, STOP_CONVERGENCE = 1, STOP_DISCREPANCY = 2, STOP_MIN_ERROR = 3 };
+enum StopKind { STOP_FIXED = 0, STOP_CONVERGENCE = 1, STOP_DISCREPANCY = 2, STOP_MIN_ERROR = 3, STOP_LANDED = 4 };
+constexpr int kLandCand = kArmExtra;   // step lengths per landing pass (slots SLOT_ARMX..)
+constexpr int kLandPasses = 2;
 
 // Controller state of one problem (in the workspace; read by every hot kernel).
 struct CtrlState {
@@ -58,6 +60,8 @@ struct CtrlState {
   int proj_pass;    // flux projection search pass
   unsigned arrive;  // blocks of the current row pass that have stored their partial sums
   int arm_nl;       // step lengths evaluated by the main Armijo pass (kArmShort or kArmMain)
+  int land_pass;    // landed discrepancy stop: 0 idle; n > 0 landing the last step, n - 1 passes done
+  double land_lo, land_hi, land_Jlo, land_Jhi, land_Jt;   // bracket of lambda, J at its ends, target
   double J;         // J_0 at the current iterate
   double J_pred;    // J_0 at the accepted trial point
   double J_prev;    // RL: J_0 at the previous iterate

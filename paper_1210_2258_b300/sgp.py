@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "sgp.h")
 OK, ERR_ARG, ERR_SIZE, ERR_PSF, ERR_CUDA, ERR_WORKSPACE, ERR_LINESEARCH, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE = range(10)
 STATUS_NAMES = ["OK", "ARG", "SIZE_UNSUPPORTED", "PSF", "CUDA", "WORKSPACE", "LINESEARCH", "TIMEOUT",
                 "NONFINITE", "STATE"]
-STOP_FIXED, STOP_CONVERGENCE, STOP_DISCREPANCY, STOP_MIN_ERROR = range(4)
+STOP_FIXED, STOP_CONVERGENCE, STOP_DISCREPANCY, STOP_MIN_ERROR, STOP_LANDED = range(5)
 START_ZERO, START_DATA, START_CONSTANT, START_USER = range(4)
 PSF_CENTER, PSF_CORNER = 0, 1
 N_PASSES = 7    # passes of one SGP iteration (sgp_time_passes)
@@ -87,6 +87,8 @@ def load() -> C.CDLL:
         "sgp_apply_AT": (st, [vp, i, vp, vp]),
         "sgp_time_passes": (st, [vp, i, C.POINTER(d), i]),
         "sgp_launch_count": (C.c_longlong, [vp]),
+        "sgp_get_tile": (st, [vp, C.POINTER(i), C.POINTER(i)]),
+        "sgp_set_tile": (st, [vp, i]),
         "sgp_convolve_noalloc": (st, [vp, vp, vp, i, i, i, i, vp]),
         "sgp_destroy": (st, [vp]),
         "sgp_last_error": (C.c_char_p, []),
@@ -272,6 +274,15 @@ class Problems:
 
     def launch_count(self) -> int:
         return int(load().sgp_launch_count(self.ctx))
+
+    def tile(self) -> tuple[int, int]:
+        """(rows per work item, threads per block) of the hot row passes."""
+        r, t = C.c_int(), C.c_int()
+        _check(load().sgp_get_tile(self.ctx, C.byref(r), C.byref(t)))
+        return r.value, t.value
+
+    def set_tile(self, rows: int) -> None:
+        _check(load().sgp_set_tile(self.ctx, rows))
 
     def close(self) -> None:
         if getattr(self, "ctx", None):

@@ -137,6 +137,28 @@ def test_discrepancy_stop_matches_oracle(gpu, galaxy128):
     assert abs(it_rl - ref_rl.iters) <= 1 and it_rl > 4 * it
 
 
+def test_landed_discrepancy_stop(gpu, galaxy128):
+    """The landed stop ends at the oracle's iteration with the discrepancy in [eta (1 - tol), eta]
+    (the KL recomputed at the returned iterate), above the plain stop's KL."""
+    sc = galaxy128
+    orc = oracle_problem(sc)
+    tol = 1e-5
+    ref = O.sgp(orc, stop=O.StopRule("landed", max_iter=3000, eta=1.0, tol=tol))
+    prob = gpu_problem(gpu, sc)
+    it = prob.solve_until(gpu.STOP_LANDED, max_iter=3000, tol=tol, eta=1.0)[0]
+    assert it == ref.iters, (it, ref.iters)
+    info = prob.info()
+    J = prob.kl_value()
+    D = J * info.D / info.J
+    assert 1.0 - tol - 2e-6 <= D <= 1.0 + 2e-6, D
+    assert abs(J - ref.J) <= 1e-5 * ref.J, (J, ref.J)
+    assert info.J >= J * (1 - 2e-6)            # the reported J bounds the recomputed one
+    plain = gpu_problem(gpu, sc)
+    plain.solve_until(gpu.STOP_DISCREPANCY, max_iter=3000, eta=1.0)
+    assert plain.kl_value() < J
+    assert rel_l2(host(prob.get_f()), ref.f) <= 1e-3
+
+
 def test_convergence_and_min_error_stops(gpu, galaxy128):
     sc = galaxy128
     orc = oracle_problem(sc)

@@ -362,3 +362,28 @@ def test_sgp_trajectory_sensitivity():
     assert np.linalg.norm(ra.f - rb.f) / np.linalg.norm(ra.f) < 1e-5
     ra, rb = O.sgp(a, stop=O.StopRule("fixed", 200)), O.sgp(b, stop=O.StopRule("fixed", 200))
     assert np.linalg.norm(ra.f - rb.f) / np.linalg.norm(ra.f) > 1e-2
+
+
+def test_landed_discrepancy_stop():
+    """Landed stop (a reading of Sect. 3.3): same iteration as the plain discrepancy stop, final
+    discrepancy in the band [eta (1 - tol), eta], the shortened step still satisfies the Armijo
+    condition of Alg. 1 step 5 (J convex along the step), and two starts end at the same KL."""
+    sc = scenes.galaxy_scene(seed=0, N=64, n_stars=8)
+    prob = O.Problem(sc.psfs, sc.g, sc.b)
+    eta = 1.05                                      # this small scene's minimum discrepancy is 1.023
+    plain = O.sgp(prob, stop=O.StopRule("discrepancy", max_iter=500, eta=eta))
+    tol = 1e-5
+    land = O.sgp(prob, stop=O.StopRule("landed", max_iter=500, eta=eta, tol=tol))
+    assert land.iters == plain.iters and 1 < land.iters < 500
+    D = prob.discrepancy(land.J)
+    assert eta * (1.0 - tol) <= D <= eta
+    assert plain.trace[-1]["D"] < eta * (1.0 - tol)  # the plain stop overshoots the band here
+    # the last step: J(lam') <= J(0) + beta lam' g'd with the recomputed KL of the returned f
+    last, prev = land.trace[-1], land.trace[-2]
+    assert last["lam"] < plain.trace[-1]["lam"]
+    assert prob.kl(land.f) <= prev["J"] + O.SGPParams().beta * last["lam"] * last["gTd"] * (1 - 1e-12)
+    assert abs(prob.kl(land.f) - land.J) <= 1e-12 * land.J
+    # a different start reaches the same final KL within the band
+    f0 = np.maximum(sc.g[0] - sc.b[0], 0.0) + 1.0
+    other = O.sgp(prob, f0=f0, stop=O.StopRule("landed", max_iter=500, eta=eta, tol=tol))
+    assert abs(other.J - land.J) <= tol * land.J
