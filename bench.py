@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling driver: set up the workload, run this many SGP iterations, exit")
+    ap.add_argument("--workload", default="galaxy2048", choices=["galaxy2048", "stars256", "multiview1024", "batch64"],
+                    help="galaxy2048: the headline line (default); the others print one line each for the "
+                         "other configurations (256^2 star field RL/SGP 200 iterations, 3 x 1024^2 multi-view "
+                         "SGP to the discrepancy stop, a batch of 64 boundary problems of mixed sizes)")
     return ap.parse_args()
 
 
@@ -275,7 +279,10 @@ def run_ours(args):
         total_it_all = total_it
     value = total_it_all / (total_ms / 1e3)
 
-    # per-pass durations (CUDA events on the library's stream) -> roofline of the dominant pass
+    # per-pass durations (CUDA events on the library's stream) -> roofline of the dominant pass;
+    # timed over the first 10 iterations from the solve's own start (the solve's pass mix: the
+    # extra Armijo pass returns at once, the main pass evaluates lambda in {1, theta})
+    prob.set_start(0, lib.START_CONSTANT)
     passes = prob.time_passes(10)
     B = N * N * 4
     shares = [ms for ms in passes]
@@ -349,10 +356,91 @@ def run_ours(args):
     return 0
 
 
+def _timed(torch, fn, reps):
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = None
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        out = fn()
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / reps, out
+
+
+def run_other_workload(args):
+    """One JSON line for a non-headline configuration (same device-resident timing rules)."""
+    import torch
+    from paper_1210_2258_b300 import scenes
+    from paper_1210_2258_b300 import sgp as lib
+    torch.cuda.set_device(0)
+    lib.load()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(np.asarray(a, np.float32))).cuda()
+    line = {"workload": args.workload, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic"}
+    if args.workload == "stars256":
+        sc = scenes.stars_scene(seed=args.seed, N=256)
+        out = {}
+        for method in ("sgp", "rl"):
+            pr = lib.Problems(dev(sc.psfs), [float(sc.b[0])])
+            pr.set_data(0, dev(sc.g))
+            run = (lambda: pr.sgp_iterate(200)) if method == "sgp" else (lambda: pr.rl_iterate(200))
+            for _ in range(args.warmup):
+                pr.set_start(0, lib.START_CONSTANT)
+                run()
+            ms, _ = _timed(torch, lambda: (pr.set_start(0, lib.START_CONSTANT), run()), args.steps)
+            out[method] = {"ms_per_200_iterations": ms, "us_per_iteration": 1e3 * ms / 200,
+                           "iters_per_s": 200 / (ms / 1e3), "tile": pr.tile()}
+        line.update({"metric": "256^2 star field, 200 fixed iterations", "unit": "iter/s",
+                     "value": out["sgp"]["iters_per_s"], "sgp": out["sgp"], "rl": out["rl"],
+                     "config": {"N": 256, "stars": 50, "psf": "Gaussian sigma 2", "b": 10}})
+    elif args.workload == "multiview1024":
+        sc = scenes.cluster_multiview_scene(seed=args.seed, N=1024)
+        pr = lib.Problems(dev(sc.psfs), list(map(float, sc.b)))
+        pr.set_data(0, dev(sc.g))
+
+        def solve():
+            pr.set_start(0, lib.START_CONSTANT)
+            return pr.solve_until(lib.STOP_DISCREPANCY, max_iter=5000, eta=1.0, raise_on_error=False)[0]
+        for _ in range(args.warmup):
+            solve()
+        ms, it = _timed(torch, solve, args.steps)
+        line.update({"metric": "3 x 1024^2 multi-view SGP to the discrepancy stop", "unit": "iter/s",
+                     "value": it / (ms / 1e3), "time_to_stop_ms": ms, "iterations": it,
+                     "final_discrepancy": pr.info().D, "tile": pr.tile(),
+                     "config": {"N": 1024, "p": 3, "psf": "two-pupil |FFT|^2 at 0/60/120 deg", "b": 20}})
+    else:
+        scs = scenes.boundary_batch(seed=args.seed, count=64)
+        pr = lib.Problems([dev(s.psfs) for s in scs], [list(map(float, s.b)) for s in scs],
+                          [dev(s.mask) for s in scs])
+        for i, s in enumerate(scs):
+            pr.set_data(i, dev(s.g))
+
+        def solve():
+            for i in range(len(scs)):
+                pr.set_start(i, lib.START_CONSTANT)
+            return pr.solve_until(lib.STOP_DISCREPANCY, max_iter=3000, eta=1.0, raise_on_error=False)
+        for _ in range(args.warmup):
+            solve()
+        ms, its = _timed(torch, solve, args.steps)
+        px = sum(int(np.prod(s.g.shape[-2:])) for s in scs)
+        pix_it = sum(int(np.prod(s.g.shape[-2:])) * k for s, k in zip(scs, its))
+        line.update({"metric": "batch of 64 boundary problems (sides 128..1024 padded), discrepancy stop",
+                     "unit": "Mpixel-iterations/s", "value": pix_it / (ms / 1e3) / 1e6,
+                     "time_to_all_stopped_ms": ms, "iterations_min_max_mean": [int(min(its)), int(max(its)),
+                                                                              float(np.mean(its))],
+                     "padded_pixels": px, "not_stopped": int(sum(k >= 3000 for k in its)),
+                     "config": {"count": 64, "sides": [128, 256, 384, 512, 768, 1024], "psf": "Gaussian sigma U[1,4]",
+                                "b": "U[5,50]", "mask": "0/1 M_S, extended domain"}})
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "galaxy2048":
+        return run_other_workload(args)
     return run_ours(args)
 
 

@@ -60,6 +60,7 @@ __device__ __forceinline__ float2 col_product(const ColLayout<C>& x, int i, int 
 // register allocator keep every stage's addresses live, so views are separate items where possible.
 template <int H, int MODE, int NV = 0>
 __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int2* __restrict__ items, int n_items) {
+  pdl_enter();
   using G = ColGeo<H>;
   constexpr int C = G::C, T = G::T, E = G::E;
   extern __shared__ float2 smem[];

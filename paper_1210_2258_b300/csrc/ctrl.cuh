@@ -65,6 +65,7 @@ __device__ __forceinline__ void flux_xd(const ImgDesc& d, const CtrlState* c, si
 template <bool FP64>
 __global__ void __launch_bounds__(kRowBlock) k_flux_pass(const ImgDesc* __restrict__ imgs, const int2* __restrict__ items,
                                                         int n_items, int mode) {
+  pdl_enter();
   const int it = blockIdx.x;
   if (it >= n_items) return;
   const int2 item = items[it];
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(kRowBlock) k_flux_pass(const ImgDesc* __restri
 
 template <bool FP64>
 __global__ void __launch_bounds__(kCtrlBlock) k_ctrl_flux(const ImgDesc* __restrict__ imgs, int mode) {
+  pdl_enter();
   const ImgDesc& d = imgs[blockIdx.x];
   CtrlState* c = d.ctrl;
   if (c->done >= 1 || c->constraint == 0) return;

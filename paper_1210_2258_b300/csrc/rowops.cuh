@@ -342,6 +342,7 @@ __device__ __forceinline__ int item_view(int2 item) { return item.y >> 16; }
 template <int W, bool FP64>
 __device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ imgs,
                                                                const int2* __restrict__ items, int n_items) {
+  pdl_enter();
   using G = RowGeo<W>;
   extern __shared__ float2 smem[];
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
@@ -442,6 +443,7 @@ __global__ void __launch_bounds__(kRowBlock, 4) k_sgp_update_ratio(const ImgDesc
 template <int W, bool FP64>
 __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
                                                           const int2* __restrict__ items, int n_items) {
+  pdl_enter();
   using G = RowGeo<W>;
   extern __shared__ float2 smem[];
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
@@ -515,6 +517,7 @@ __global__ void __launch_bounds__(kRowBlock, 4) k_sgp_grad_bb(const ImgDesc* __r
 template <int W, bool FP64>
 __device__ __forceinline__ void b_sgp_y(const ImgDesc* __restrict__ imgs,
                                                     const int2* __restrict__ items, int n_items) {
+  pdl_enter();
   using G = RowGeo<W>;
   extern __shared__ float2 smem[];
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
@@ -570,6 +573,7 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_y(const ImgDesc* __restrict__
 template <int W, bool FP64>
 __device__ __forceinline__ void b_sgp_ad_armijo(const ImgDesc* __restrict__ imgs,
                                                             const int2* __restrict__ items, int n_items) {
+  pdl_enter();
   using G = RowGeo<W>;
   extern __shared__ float2 smem[];
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
@@ -632,6 +636,7 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_ad_armijo(const ImgDesc* __re
 template <int W, bool FP64, bool LAND>
 __device__ __forceinline__ void b_sgp_lambda_scan(const ImgDesc* __restrict__ imgs,
                                                   const int2* __restrict__ items, int n_items) {
+  pdl_enter();
   using G = RowGeo<W>;
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
   {
@@ -693,6 +698,7 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_land(const ImgDesc* __restric
 template <int W, bool FP64>
 __device__ __forceinline__ void b_rl_update(const ImgDesc* __restrict__ imgs,
                                                         const int2* __restrict__ items, int n_items) {
+  pdl_enter();
   using G = RowGeo<W>;
   extern __shared__ float2 smem[];
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
@@ -747,6 +753,7 @@ __global__ void __launch_bounds__(kRowBlock) k_rl_update(const ImgDesc* __restri
 template <int W, bool FP64>
 __device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
                                                        const int2* __restrict__ items, int n_items, int write_u) {
+  pdl_enter();
   using G = RowGeo<W>;
   extern __shared__ float2 smem[];
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;
@@ -792,6 +799,7 @@ __global__ void __launch_bounds__(kRowBlock) k_rl_ratio(const ImgDesc* __restric
 template <int W>
 __device__ __forceinline__ void b_rl_step_minmax(const ImgDesc* __restrict__ imgs,
                                                              const int2* __restrict__ items, int n_items) {
+  pdl_enter();
   using G = RowGeo<W>;
   extern __shared__ float2 smem[];
   const int r = threadIdx.x / G::T, t = threadIdx.x % G::T;

@@ -229,6 +229,24 @@ sgp_status launch(const void* fn, int grid, int block, size_t smem, cudaStream_t
   if (g_launch_counter) ++*g_launch_counter;
   return SGP_OK;
 }
+// Launch of a hot pass (its kernel starts with pdl_enter): programmatic dependent launch, so its
+// blocks may be scheduled while the previous pass drains.
+sgp_status launch_pdl(const void* fn, int grid, int block, size_t smem, cudaStream_t s, void** args) {
+  if (grid <= 0) return SGP_OK;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CU(cudaLaunchKernelExC(&cfg, fn, args));
+  if (g_launch_counter) ++*g_launch_counter;
+  return SGP_OK;
+}
 
 sgp_status row_pass(sgp_ctx* c, RowOp op, bool view_list, int extra = -1) {
   const int si = side_index(c->W);
@@ -239,7 +257,7 @@ sgp_status row_pass(sgp_ctx* c, RowOp op, bool view_list, int extra = -1) {
   const int2* items = view_list ? c->L.d_rv : c->L.d_row;
   int n = view_list ? c->L.n_rv : c->L.n_row;
   void* args4[] = {(void*)&imgs, (void*)&items, (void*)&n, (void*)&extra};
-  return launch(fn, n, threads, smem, c->s, args4);
+  return launch_pdl(fn, n, threads, smem, c->s, args4);
 }
 
 // Row lists of the hot passes with R rows per item (every problem of a uniform context; a mixed
@@ -300,7 +318,7 @@ sgp_status col_pass(sgp_ctx* c, int variant, int job_off, int image = -1) {
   // the job index of an item is the problem index; job_off picks the job kind
   const ColJob* jobs = c->L.d_jobs + job_off;
   void* args[] = {(void*)&jobs, (void*)&items, (void*)&n};
-  return launch(fn, n, kColBlock, smem, c->s, args);
+  return launch_pdl(fn, n, kColBlock, smem, c->s, args);
 }
 
 sgp_status ctrl_pass(sgp_ctx* c, const void* fn) {
@@ -368,9 +386,9 @@ sgp_status seq_flux(sgp_ctx* c) {
   for (int step = 0; step < kFluxPasses + 2; ++step) {
     int mode = step == 0 ? 0 : (step <= kFluxPasses ? 1 : 2);
     void* a[] = {(void*)&imgs, (void*)&items, (void*)&n, (void*)&mode};
-    if ((st = launch(fp, n, kRowBlock, 0, c->s, a))) return st;
+    if ((st = launch_pdl(fp, n, kRowBlock, 0, c->s, a))) return st;
     void* b[] = {(void*)&imgs, (void*)&mode};
-    if ((st = launch(fc, c->n, kCtrlBlock, 0, c->s, b))) return st;
+    if ((st = launch_pdl(fc, c->n, kCtrlBlock, 0, c->s, b))) return st;
   }
   return SGP_OK;
 }
@@ -446,10 +464,12 @@ sgp_status reset_ctrl(sgp_ctx* c) {
 }
 
 // Set-up passes from f^(0): A_j f0 (kept in u), J_0, one RL step -> L1/L2 (SGP).  mode 1 SGP, 2 RL.
-// Autotuner of the row tile: time the projection pass K4 (a row FFT with pointwise work and partial
-// sums that changes no iteration state) for every candidate rows-per-item R (256-thread tiles down
-// to 32-thread ones), keep the fastest (a smaller tile must win by 3 %), and remember the choice for
-// the process per (H, W, p) so that contexts of one size share it (and their summation order).
+// Autotuner of the row tile: time two row passes that change no iteration state -- the projection
+// pass K4 (pointwise work, R2C, partial sums) and the set-up ratio pass (C2R, KL and ratio, R2C;
+// it rewrites A f, which the set-up recomputes) -- for every candidate rows-per-item R (256-thread
+// tiles down to 32-thread ones), keep the fastest (a smaller tile must win by 5 %; best of three
+// rounds), and remember the choice for the process per (H, W, p), so that contexts of one size
+// share it (and their summation order).  It runs before the set-up passes.
 sgp_status autotune_rows(sgp_ctx* c) {
   static std::map<std::tuple<int, int, int>, int> cache;
   static std::mutex mu;
@@ -469,13 +489,21 @@ sgp_status autotune_rows(sgp_ctx* c) {
   for (int R = rmax; R >= rmin && st == SGP_OK; R /= 2) {
     if ((st = fill_row_items(c, R))) break;
     if ((st = row_pass(c, ROP_SGP_Y, false))) break;           // warm-up
-    cudaEventRecord(e0, c->s);
-    for (int r = 0; r < 3 && st == SGP_OK; ++r) st = row_pass(c, ROP_SGP_Y, false);
-    cudaEventRecord(e1, c->s);
-    float ms = 0.0f;
-    if (st == SGP_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-      st = fail(SGP_ERR_CUDA, "autotuner timing failed");
-    if (st == SGP_OK && (R == rmax || ms < 0.97f * best)) { best = ms; best_r = R; }
+    if ((st = row_pass(c, ROP_RL_RATIO, true, 1))) break;
+    float ms = 1e30f;                                          // best of three rounds
+    for (int round = 0; round < 3 && st == SGP_OK; ++round) {
+      cudaEventRecord(e0, c->s);
+      for (int r = 0; r < 2 && st == SGP_OK; ++r) {
+        st = row_pass(c, ROP_SGP_Y, false);
+        if (st == SGP_OK) st = row_pass(c, ROP_RL_RATIO, true, 1);
+      }
+      cudaEventRecord(e1, c->s);
+      float t = 0.0f;
+      if (st == SGP_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+        st = fail(SGP_ERR_CUDA, "autotuner timing failed");
+      ms = std::min(ms, t);
+    }
+    if (st == SGP_OK && (R == rmax || ms < 0.95f * best)) { best = ms; best_r = R; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
