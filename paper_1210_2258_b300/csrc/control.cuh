@@ -6,8 +6,8 @@
 //   ctrl_sgp_alpha         after K3: step 1 of Alg. 1, scaled BB values (Eq. BB1, BB2), the
 //                          safeguards, the alternation of Eq. (alphadef) with the M_alpha window
 //                          and tau, warm-up rule
-//   ctrl_sgp_lambda        after K6: step 5 of Alg. 1, first lambda in {1, theta} (or {1, .., theta^3}
-//                          after an iteration that needed lambda <= theta^2) with
+//   ctrl_sgp_lambda        after K6: step 5 of Alg. 1, first lambda in {1} ({1, theta} after one
+//                          backtrack, {1, .., theta^3} after more) with
 //                          J(f + lambda d) <= J(f) + beta lambda grad'd; stop rules of Sect. 3.3
 //   ctrl_sgp_lambda_extra  after K7: the remaining powers up to theta^30 when needed
 //   ctrl_rl                after the RL ratio pass: Richardson-Lucy bookkeeping (J, trace, stops)
@@ -143,7 +143,7 @@ __device__ inline void sgp_accept(const ImgDesc& d, CtrlState* c, int nb, double
   c->J_pred = c->J + dJ;
   c->fresh = 0;                       // f^(k+1) = f^(k) + lambda d is applied by the next K1
   c->need_more = 0;
-  c->arm_nl = nb >= kArmShort ? kArmMain : kArmShort;
+  c->arm_nl = nb == 0 ? 1 : (nb == 1 ? 2 : kArmMain);
   const int kn = c->k + 1;
   trace_push(d, c, kn, c->J_pred, c->alpha, lam, nb, c->branch, c->gTd);
   bool stop = kn >= c->max_iter;
@@ -207,7 +207,7 @@ __device__ void sgp_lambda_decide(const ImgDesc& d, CtrlState* c, double gTd, co
   c->gTd = gTd;
   if (!isfinite(gTd)) { c->status = 8; c->done = 2; return; }
   double lam = 1.0;
-  const int nl = c->arm_nl == kArmMain ? kArmMain : kArmShort;
+  const int nl = arm_count(c);
   for (int i = 0; i < nl && i <= c->max_backtracks; ++i) {
     const bool ok = FP64 ? (arm[i] <= c->beta * lam * gTd)
                          : (float(arm[i]) <= float(c->beta) * float(lam) * float(gTd));
@@ -230,7 +230,7 @@ __device__ void ctrl_sgp_lambda(const ImgDesc& d) {
 
 template <bool FP64>
 __device__ void sgp_lambda_extra_decide(const ImgDesc& d, CtrlState* c, const double (&arm)[kArmExtra]) {
-  const int nl = c->arm_nl == kArmMain ? kArmMain : kArmShort;
+  const int nl = arm_count(c);
   double lam = 1.0;
   for (int i = 0; i < nl; ++i) lam *= c->theta;
   const double gTd = c->gTd;

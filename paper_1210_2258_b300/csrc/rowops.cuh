@@ -568,6 +568,25 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_y(const ImgDesc* __restrict__
   b_sgp_y<W, FP64>(imgs, items, n_items);
 }
 
+// K6 pixel loop for the first N step lengths (the other sums stay 0): stores A d, adds the Armijo
+// terms
+template <int W, int N>
+__device__ __forceinline__ void sgp_armijo_rows(const RowLayout<W / 2>& x, KSum (&acc)[kArmMain],
+                                                const float (&lam)[kArmMain], const float* uj, float* adj,
+                                                const float* gj, const ImgDesc& d, int j, size_t off, int t) {
+  using G = RowGeo<W>;
+  KSum (&accN)[N] = reinterpret_cast<KSum (&)[N]>(acc);
+  const float (&lamN)[N] = reinterpret_cast<const float (&)[N]>(lam);
+#pragma unroll 2
+  for (int q = 0; q < G::E; ++q) {
+    const size_t i = off + t + q * G::T;
+    const float2 ad = x(t + q * G::T), u = ld2(uj, i), g = ld2(gj, i), b = b_pair(d, j, i);
+    st2(adj, i, ad);
+    armijo_add<N>(accN, lamN, g.x, u.x + b.x, ad.x);
+    armijo_add<N>(accN, lamN, g.y, u.y + b.y, ad.y);
+  }
+}
+
 // SGP K6: per view, C2R of plane j+1 (= A_j d) -> stored A_j d (A(f + lam d) = A f + lam A d: no FFT
 // per backtrack) and the Armijo partial sums Delta J(theta^i), i = 0..3 (Alg. 1 step 5).
 template <int W, bool FP64>
@@ -599,27 +618,10 @@ __device__ __forceinline__ void b_sgp_ad_armijo(const ImgDesc* __restrict__ imgs
     const float* uj = d.u + size_t(j) * d.P;
     float* adj = d.Ad + size_t(j) * d.P;
     const float* gj = d.g + size_t(j) * d.P;
-    if (c->arm_nl == kArmMain) {
-#pragma unroll 2
-      for (int q = 0; q < G::E; ++q) {
-        const size_t i = off + t + q * G::T;
-        const float2 ad = x(t + q * G::T), u = ld2(uj, i), g = ld2(gj, i), b = b_pair(d, j, i);
-        st2(adj, i, ad);
-        armijo_add<kArmMain>(acc, lam, g.x, u.x + b.x, ad.x);
-        armijo_add<kArmMain>(acc, lam, g.y, u.y + b.y, ad.y);
-      }
-    } else {
-      KSum (&acc2)[kArmShort] = reinterpret_cast<KSum (&)[kArmShort]>(acc);
-      const float (&lam2)[kArmShort] = reinterpret_cast<const float (&)[kArmShort]>(lam);
-#pragma unroll 2
-      for (int q = 0; q < G::E; ++q) {
-        const size_t i = off + t + q * G::T;
-        const float2 ad = x(t + q * G::T), u = ld2(uj, i), g = ld2(gj, i), b = b_pair(d, j, i);
-        st2(adj, i, ad);
-        armijo_add<kArmShort>(acc2, lam2, g.x, u.x + b.x, ad.x);
-        armijo_add<kArmShort>(acc2, lam2, g.y, u.y + b.y, ad.y);
-      }
-    }
+    const int nl = arm_count(c);
+    if (nl == kArmMain) sgp_armijo_rows<W, kArmMain>(x, acc, lam, uj, adj, gj, d, j, off, t);
+    else if (nl == 2) sgp_armijo_rows<W, 2>(x, acc, lam, uj, adj, gj, d, j, off, t);
+    else sgp_armijo_rows<W, 1>(x, acc, lam, uj, adj, gj, d, j, off, t);
   }
   block_sum_store<kArmMain, FP64>(acc, partv_of(d, it) + SLOT_ARM);
   if (arrive_last(d.ctrl, d.n_rv_items)) ctrl_sgp_lambda<FP64>(d);
@@ -658,7 +660,7 @@ __device__ __forceinline__ void b_sgp_lambda_scan(const ImgDesc* __restrict__ im
     } else {
       step = float(c->theta);
       lam0 = 1.0f;
-      const int nl = c->arm_nl == kArmMain ? kArmMain : kArmShort;
+      const int nl = arm_count(c);
       for (int l = 0; l < nl; ++l) lam0 *= step;
     }
     KSum acc[kArmExtra];

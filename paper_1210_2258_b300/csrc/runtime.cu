@@ -466,10 +466,12 @@ sgp_status reset_ctrl(sgp_ctx* c) {
 // Set-up passes from f^(0): A_j f0 (kept in u), J_0, one RL step -> L1/L2 (SGP).  mode 1 SGP, 2 RL.
 // Autotuner of the row tile: time two row passes that change no iteration state -- the projection
 // pass K4 (pointwise work, R2C, partial sums) and the set-up ratio pass (C2R, KL and ratio, R2C;
-// it rewrites A f, which the set-up recomputes) -- for every candidate rows-per-item R (256-thread
-// tiles down to 32-thread ones), keep the fastest (a smaller tile must win by 5 %; best of three
-// rounds), and remember the choice for the process per (H, W, p), so that contexts of one size
-// share it (and their summation order).  It runs before the set-up passes.
+// it rewrites A f, which the set-up recomputes) -- for the candidate rows-per-item R = R_max,
+// R_max/2, ... (256-thread tiles down to 32-thread ones), going to a smaller tile only while the
+// current one gives fewer work items than SMs (more blocks than that only add block scheduling and
+// arrival atomics, which these two passes do not show), keep the fastest (a smaller tile must win
+// by 5 %; best of three rounds), and remember the choice for the process per (H, W, p), so that
+// contexts of one size share it (and their summation order).  It runs before the set-up passes.
 sgp_status autotune_rows(sgp_ctx* c) {
   static std::map<std::tuple<int, int, int>, int> cache;
   static std::mutex mu;
@@ -480,6 +482,8 @@ sgp_status autotune_rows(sgp_ctx* c) {
     if (it != cache.end()) return fill_row_items(c, it->second);
   }
   const int rmax = rows_per_item(c->W), rmin = rows_min(c->W);
+  int sms = 0;
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
@@ -504,6 +508,7 @@ sgp_status autotune_rows(sgp_ctx* c) {
       ms = std::min(ms, t);
     }
     if (st == SGP_OK && (R == rmax || ms < 0.95f * best)) { best = ms; best_r = R; }
+    if (c->L.n_rv >= sms) break;   // this tile already fills every SM: smaller ones only add blocks
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

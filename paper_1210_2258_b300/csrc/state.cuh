@@ -8,7 +8,7 @@ namespace sgp {
 
 constexpr int kMaxViews = 8;        // p <= 8 views per problem
 constexpr int kMaxHist = 16;        // >= M_alpha
-constexpr int kPartStride = 48;     // doubles of partial sums per row item
+constexpr int kPartStride = 56;     // doubles of partial sums per row item
 constexpr int kTraceStride = 8;     // doubles per trace record
 constexpr int kRowBlock = 256;      // threads of every row-pass block
 constexpr int kColBlock = 512;      // threads of every column-pass block
@@ -31,15 +31,14 @@ enum Slot {
   SLOT_FLUX = 7,      // sum f
   SLOT_ARM = 8,       // kArmMain slots: Delta J(theta^i), i < arm_nl (main pass)
   SLOT_ARMX = 12,     // kArmExtra slots: Delta J(theta^i), i = arm_nl..30 (only when needed)
-  SLOT_MIN = 41,      // min over positive pixels (set-up)
-  SLOT_MAX = 42,      // max (set-up)
-  SLOT_PROJ = 43,     // flux projection search sums (5)
+  SLOT_MIN = 42,      // min over positive pixels (set-up)
+  SLOT_MAX = 43,      // max (set-up)
+  SLOT_PROJ = 44,     // flux projection search sums (5)
 };
-// The main Armijo pass evaluates arm_nl step lengths 1, theta, ..: kArmShort while the previous
-// iteration accepted lambda >= theta, kArmMain after it needed a smaller one.
+// The main Armijo pass evaluates arm_count() step lengths 1, theta, ..: one after an iteration that
+// accepted lambda = 1, two after one backtrack, kArmMain after more.
 constexpr int kArmMain = 4;
-constexpr int kArmShort = 2;
-constexpr int kArmExtra = 31 - kArmShort;
+constexpr int kArmExtra = 30;           // theta^1 .. theta^30 at most in the extra pass
 constexpr int kFluxCand = 16;       // candidate mu values per flux-search pass (slots SLOT_ARMX..)
 constexpr int kFluxPasses = 5;
 
@@ -67,7 +66,7 @@ struct CtrlState {
   int constraint;   // 0 non-negativity, 1 + flux
   int proj_pass;    // flux projection search pass
   unsigned arrive;  // blocks of the current row pass that have stored their partial sums
-  int arm_nl;       // step lengths evaluated by the main Armijo pass (kArmShort or kArmMain)
+  int arm_nl;       // step lengths of the main Armijo pass (1, 2 or kArmMain; 0 before the first)
   int land_pass;    // landed discrepancy stop: 0 idle; n > 0 landing the last step, n - 1 passes done
   double land_lo, land_hi, land_Jlo, land_Jhi, land_Jt;   // bracket of lambda, J at its ends, target
   double J;         // J_0 at the current iterate
@@ -81,6 +80,9 @@ struct CtrlState {
   double mu_lo, mu_hi, phi_lo, phi_hi;
   double scratch[8];
 };
+__host__ __device__ inline int arm_count(const CtrlState* c) {
+  return c->arm_nl == 1 || c->arm_nl == 2 || c->arm_nl == kArmMain ? c->arm_nl : 2;
+}
 
 // One problem (p views of an H x W object) as the kernels see it.  Arrays are FP32 row-major with
 // P = H*W elements per plane; spectra are H x W/2 complex (the real DC and Nyquist columns of the
