@@ -577,13 +577,22 @@ __device__ __forceinline__ void sgp_armijo_rows(const RowLayout<W / 2>& x, KSum 
   using G = RowGeo<W>;
   KSum (&accN)[N] = reinterpret_cast<KSum (&)[N]>(acc);
   const float (&lamN)[N] = reinterpret_cast<const float (&)[N]>(lam);
-#pragma unroll 2
-  for (int q = 0; q < G::E; ++q) {
-    const size_t i = off + t + q * G::T;
-    const float2 ad = x(t + q * G::T), u = ld2(uj, i), g = ld2(gj, i), b = b_pair(d, j, i);
-    st2(adj, i, ad);
-    armijo_add<N>(accN, lamN, g.x, u.x + b.x, ad.x);
-    armijo_add<N>(accN, lamN, g.y, u.y + b.y, ad.y);
+  constexpr int B = batch_of<G::E, 4>();
+#pragma unroll 1
+  for (int q0 = 0; q0 < G::E; q0 += B) {
+    float2 u[B], g[B], bk[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const size_t i = off + t + (q0 + b) * G::T;
+      u[b] = ld2(uj, i); g[b] = ld2(gj, i); bk[b] = b_pair(d, j, i);
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const float2 ad = x(t + (q0 + b) * G::T);
+      st2(adj, off + t + (q0 + b) * G::T, ad);
+      armijo_add<N>(accN, lamN, g[b].x, u[b].x + bk[b].x, ad.x);
+      armijo_add<N>(accN, lamN, g[b].y, u[b].y + bk[b].y, ad.y);
+    }
   }
 }
 
