@@ -269,14 +269,8 @@ def run_ours(args):
     launches = prob.launch_count() - l0
     clocks = sampler.stop() if sampler else None
     info = prob.info()
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        it = torch.tensor([total_it], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(it, op=torch.distributed.ReduceOp.SUM)
-        total_ms, total_it_all = float(t.item()), int(it.item())
-    else:
-        total_it_all = total_it
+    from paper_1210_2258_b300 import replicas
+    total_ms, total_it_all = replicas.aggregate(total_ms, total_it, device="cuda")
     value = total_it_all / (total_ms / 1e3)
 
     # per-pass durations (CUDA events on the library's stream) -> roofline of the dominant pass;
