@@ -801,7 +801,7 @@ __device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
   if (!write_u && arrive_last(d.ctrl, d.n_rv_items)) ctrl_rl<FP64>(d);   // RL iteration (not set-up)
 }
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock) k_rl_ratio(const ImgDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(kRowBlock, 4) k_rl_ratio(const ImgDesc* __restrict__ imgs,
                                                        const int2* __restrict__ items, int n_items, int write_u) {
   b_rl_ratio<W, FP64>(imgs, items, n_items, write_u);
 }
