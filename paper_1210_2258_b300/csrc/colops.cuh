@@ -15,6 +15,9 @@
 //   COL_1TOP_CONJ : as COL_1TOP with conj K_j (correlation, used for alpha_j = K_j (x) M_S)
 //   COL_PTO1      : nin planes -> one plane, out = IFFT(sum_j FFT(in_j) . conj K_j)
 //                   (sum_j A_j^T y_j, Eq. backprojection)
+//   COL_PTOV      : per view (one item per view and tile), out_{j+1} = IFFT(FFT(in_j) . conj K_j);
+//                   with the column transform linear, a view sum afterwards (k_view_sum) gives
+//                   COL_PTO1's plane with p times the parallelism
 #pragma once
 #include "fft.cuh"
 #include "state.cuh"
@@ -114,11 +117,11 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
         }
       }
       __syncthreads();
-    } else if (MODE == COL_1TOP || MODE == COL_1TOP_CONJ) {
-      constexpr bool CJ = MODE == COL_1TOP_CONJ;
+    } else if (MODE == COL_1TOP || MODE == COL_1TOP_CONJ || MODE == COL_PTOV) {
+      constexpr bool CJ = MODE != COL_1TOP;
       {
         const int j = item.y >> 16;
-        col_load<H, C>(x, jb.in + col, M, t, act);
+        col_load<H, C>(x, jb.in + (MODE == COL_PTOV ? size_t(j) * jb.plane_stride : size_t(0)) + col, M, t, act);
         __syncthreads();
         fft_inplace<H, false>(x, t, act);
         float2 v[E];
@@ -139,7 +142,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
         __syncthreads();
         fft_inplace<H, true>(x, t, act);
         if (act) {
-          float2* dst = jb.out + size_t(j) * jb.plane_stride + col;
+          float2* dst = jb.out + size_t(MODE == COL_PTOV ? j + 1 : j) * jb.plane_stride + col;
 #pragma unroll
           for (int q = 0; q < E; ++q) {
             const int i = t + q * T;
@@ -148,12 +151,39 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
         }
         __syncthreads();
       }
-    } else {  // COL_PTO1
-      float2 acc[E];
+    } else if (NV == 1) {  // COL_PTO1, one view: the product goes straight back to x
+      col_load<H, C>(x, jb.in + col, M, t, act);
+      __syncthreads();
+      fft_inplace<H, false>(x, t, act);
+      float2 v[E];
+      if (act) {
 #pragma unroll
-      for (int q = 0; q < E; ++q) acc[q] = make_float2(0.0f, 0.0f);
+        for (int q = 0; q < E; ++q) {
+          const int i = t + q * T;
+          v[q] = col_product<H, C, true>(x, i, col, x(i), jb.khat, jb.khatq, M);
+        }
+      }
+      __syncthreads();
+      if (act) {
+#pragma unroll
+        for (int q = 0; q < E; ++q) x(t + q * T) = v[q];
+      }
+      __syncthreads();
+      fft_inplace<H, true>(x, t, act);
+      if (act) {
+        float2* dst = jb.out + col;
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+          const int i = t + q * T;
+          dst[i * M] = x(i);
+        }
+      }
+      __syncthreads();
+    } else {  // COL_PTO1, p views: the sum over views accumulates in the output column (L2-resident;
+              // a register accumulator live across the p transforms spilled), then back into x
       const int nin = NV > 0 ? NV : jb.nin;
-#pragma unroll
+      float2* o = jb.out + col;
+#pragma unroll 1
       for (int j = 0; j < nin; ++j) {
         col_load<H, C>(x, jb.in + size_t(j) * jb.plane_stride + col, M, t, act);
         __syncthreads();
@@ -164,14 +194,18 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
 #pragma unroll
           for (int q = 0; q < E; ++q) {
             const int i = t + q * T;
-            acc[q] = cadd(acc[q], col_product<H, C, true>(x, i, col, x(i), kh, kq, M));
+            const float2 pr = col_product<H, C, true>(x, i, col, x(i), kh, kq, M);
+            o[i * M] = j == 0 ? pr : cadd(o[i * M], pr);   // this thread's own elements only
           }
         }
         __syncthreads();
       }
       if (act) {
 #pragma unroll
-        for (int q = 0; q < E; ++q) x(t + q * T) = acc[q];
+        for (int q = 0; q < E; ++q) {
+          const int i = t + q * T;
+          x(i) = o[i * M];
+        }
       }
       __syncthreads();
       fft_inplace<H, true>(x, t, act);

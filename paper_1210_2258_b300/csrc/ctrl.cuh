@@ -200,6 +200,25 @@ __global__ void __launch_bounds__(kCtrlBlock) k_ctrl_flux(const ImgDesc* __restr
   }
 }
 
+// Plane 0 of the spectra = sum of planes 1..p (after the per-view adjoint column pass COL_PTOV),
+// problems first .. first + gridDim.y - 1; skipped for a stopped problem when respect_done.
+__global__ void k_view_sum(const ImgDesc* __restrict__ imgs, int first, int respect_done) {
+  pdl_enter();
+  const ImgDesc& d = imgs[first + blockIdx.y];
+  if (respect_done && d.ctrl->done >= 1) return;
+  const size_t n = d.P / 2;   // complex values per plane
+  float2* s = reinterpret_cast<float2*>(d.spec);
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    float2 a = s[n + i];
+    for (int j = 2; j <= d.p; ++j) {
+      const float2 b = s[size_t(j) * n + i];
+      a.x += b.x;
+      a.y += b.y;
+    }
+    s[i] = a;
+  }
+}
+
 // Scale f[0] by flux_c / sum f (flux-constrained start); sum from the set-up statistics
 __global__ void k_scale(float* __restrict__ f, size_t P, const double* __restrict__ sum, double target) {
   const double s = sum[0];

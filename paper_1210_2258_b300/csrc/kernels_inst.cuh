@@ -29,8 +29,8 @@ void register_side(Registry& R) {
   R.col[COL_1TOP][s] = reinterpret_cast<const void*>(&k_col<N, COL_1TOP>);
   R.col[COL_1TOP_CONJ][s] = reinterpret_cast<const void*>(&k_col<N, COL_1TOP_CONJ>);
   R.col[COL_PTO1][s] = reinterpret_cast<const void*>(&k_col<N, COL_PTO1, 0>);
+  R.col[COL_PTOV][s] = reinterpret_cast<const void*>(&k_col<N, COL_PTOV>);
   R.col[kColPto1P1][s] = reinterpret_cast<const void*>(&k_col<N, COL_PTO1, 1>);
-  R.col[kColPto1P3][s] = reinterpret_cast<const void*>(&k_col<N, COL_PTO1, 3>);
   R.row_smem[s] = RowGeo<N>::SMEM;
   R.row_rows[s] = RowGeo<N>::ROWS;
   R.col_smem[s] = ColGeo<N>::SMEM;

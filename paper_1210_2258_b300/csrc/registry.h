@@ -17,9 +17,9 @@ enum RowOp {
   ROP_SGP_UPDATE = 0, ROP_SGP_GRAD, ROP_SGP_Y, ROP_SGP_AD, ROP_SGP_ARMX, ROP_RL_UPDATE, ROP_RL_RATIO,
   ROP_MINMAX, ROP_R2C, ROP_C2R, ROP_SGP_LAND, ROP_COUNT
 };
-// column variants: COL_KHAT, COL_1TOP, COL_1TOP_CONJ, COL_PTO1 (any p), COL_PTO1 for p = 1, p = 3
+// column variants: COL_KHAT, COL_1TOP, COL_1TOP_CONJ, COL_PTO1 (any p), COL_PTOV, COL_PTO1 for p = 1
 constexpr int kColModes = 6;
-constexpr int kColPto1P1 = 4, kColPto1P3 = 5;
+constexpr int kColPto1P1 = 5;
 
 constexpr int kTwiddleUnits = 6;   // translation units with their own twiddle table
 

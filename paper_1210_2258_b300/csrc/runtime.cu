@@ -297,11 +297,14 @@ sgp_status fill_row_items(sgp_ctx* c, int R) {
   return SGP_OK;
 }
 
+// jobs are stored job-kind-major: kind k of problem i at index k * n + i; KHAT jobs at 5n + ...
+enum JobKind { JOB_A = 0, JOB_AT = 1, JOB_CONJ = 2, JOB_A_RAW = 3, JOB_AT_RAW = 4 };
+
 // variant: COL_1TOP (views list), COL_1TOP_CONJ, COL_PTO1; job_off selects A/AT/CONJ/raw jobs
 sgp_status col_pass(sgp_ctx* c, int variant, int job_off, int image = -1) {
   const int si = side_index(image >= 0 ? c->L.d[image].H : c->H);
   int v = variant;
-  if (variant == COL_PTO1) v = c->p == 1 ? kColPto1P1 : (c->p == 3 ? kColPto1P3 : COL_PTO1);
+  if (variant == COL_PTO1) v = c->p == 1 ? kColPto1P1 : COL_PTO1;
   const void* fn = g_reg.col[v][si];
   size_t smem = g_reg.col_smem[si];
   if (c->mixed && image < 0) {
@@ -321,14 +324,39 @@ sgp_status col_pass(sgp_ctx* c, int variant, int job_off, int image = -1) {
   return launch_pdl(fn, n, kColBlock, smem, c->s, args);
 }
 
+// Sum over views of the adjoint column transforms into plane 0 (the column part of
+// sum_j A_j^T y_j): one view per item (COL_PTOV) and a view sum for uniform multi-view contexts,
+// the single-item form otherwise.
+sgp_status adjoint_cols(sgp_ctx* c, int job_off, int image = -1) {
+  if (c->p == 1 || c->mixed) return col_pass(c, COL_PTO1, job_off, image);
+  sgp_status st = col_pass(c, COL_PTOV, job_off, image);
+  if (st) return st;
+  const ImgDesc* imgs = c->L.d_imgs;
+  int first = image >= 0 ? image : 0, respect = job_off == JOB_AT * c->n ? 1 : 0;
+  const int count = image >= 0 ? 1 : c->n;
+  const size_t n = size_t(c->H) * c->W / 2;
+  const int gx = int(std::min<size_t>((n + 255) / 256, 148 * 4));
+  void* a[] = {(void*)&imgs, (void*)&first, (void*)&respect};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(gx, count);
+  cfg.blockDim = dim3(256);
+  cfg.stream = c->s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CU(cudaLaunchKernelExC(&cfg, (const void*)&k_view_sum, a));
+  if (g_launch_counter) ++*g_launch_counter;
+  return SGP_OK;
+}
+
 sgp_status ctrl_pass(sgp_ctx* c, const void* fn) {
   const ImgDesc* imgs = c->L.d_imgs;
   void* args[] = {(void*)&imgs};
   return launch(fn, c->n, kCtrlBlock, 0, c->s, args);
 }
 
-// jobs are stored job-kind-major: kind k of problem i at index k * n + i; KHAT jobs at 5n + ...
-enum JobKind { JOB_A = 0, JOB_AT = 1, JOB_CONJ = 2, JOB_A_RAW = 3, JOB_AT_RAW = 4 };
 
 sgp_status enter(sgp_ctx* c) {
   g_launch_counter = &c->launches;
@@ -371,7 +399,7 @@ sgp_status seq_rl_unit(sgp_ctx* c) {
   if ((st = row_pass(c, ROP_RL_UPDATE, false))) return st;
   if ((st = col_pass(c, COL_1TOP, JOB_A * c->n))) return st;
   if ((st = row_pass(c, ROP_RL_RATIO, true, 0))) return st;     // + RL controller
-  return col_pass(c, COL_PTO1, JOB_AT * c->n);
+  return adjoint_cols(c, JOB_AT * c->n);
 }
 
 // flux-constrained projection: bracket, kFluxPasses candidate passes, exact final solve
@@ -396,7 +424,7 @@ sgp_status seq_flux(sgp_ctx* c) {
 sgp_status seq_sgp_unit(sgp_ctx* c, bool land = false) {
   sgp_status st;
   if ((st = row_pass(c, ROP_SGP_UPDATE, true))) return st;     // + iteration controller
-  if ((st = col_pass(c, COL_PTO1, JOB_AT * c->n))) return st;
+  if ((st = adjoint_cols(c, JOB_AT * c->n))) return st;
   if ((st = row_pass(c, ROP_SGP_GRAD, false))) return st;      // + step-length controller
   if (c->prm.constraint == 1 && (st = seq_flux(c))) return st;
   if ((st = row_pass(c, ROP_SGP_Y, false))) return st;
@@ -548,7 +576,7 @@ sgp_status prepare(sgp_ctx* c, int mode) {
   if ((st = row_pass(c, ROP_RL_UPDATE, false))) return st;       // R2C of f0 into plane 0
   if ((st = col_pass(c, COL_1TOP, JOB_A * c->n))) return st;
   if ((st = row_pass(c, ROP_RL_RATIO, true, 1))) return st;      // u = A f0, J_0, r spectra
-  if ((st = col_pass(c, COL_PTO1, JOB_AT * c->n))) return st;    // plane 0 = sum_j A_j^T r_j
+  if ((st = adjoint_cols(c, JOB_AT * c->n))) return st;    // plane 0 = sum_j A_j^T r_j
   const bool bounds = mode == 1;
   if (bounds && (st = row_pass(c, ROP_MINMAX, false))) return st;
   {
@@ -596,7 +624,9 @@ sgp_status run_fixed(sgp_ctx* c, bool sgp, int n_iter) {
   const int launches = (n_iter + c->graph_units - 1) / c->graph_units;
   for (int l = 0; l < launches; ++l) {
     CU(cudaGraphLaunch(sgp ? c->g_sgp : c->g_rl, c->s));
-    c->launches += c->graph_units * (sgp ? (c->prm.constraint == 1 ? kSgpLaunches + kFluxLaunches : kSgpLaunches) : kRlLaunches);
+    const int vs = (c->p > 1 && !c->mixed) ? 1 : 0;
+    c->launches += c->graph_units * ((sgp ? (c->prm.constraint == 1 ? kSgpLaunches + kFluxLaunches : kSgpLaunches)
+                                          : kRlLaunches) + vs);
   }
   if (sgp && (st = seq_sgp_finalize(c))) return st;
   return SGP_OK;
@@ -622,9 +652,10 @@ sgp_status run_until(sgp_ctx* c, bool sgp, const sgp_stop_rule* rule, int* iters
   const int max_launches = rule->max_iter / c->graph_units + 2;
   CtrlState* slot[2] = {c->h_ctrl, c->h_ctrl + c->n};
   // keep one chunk in flight while the flags of the previous one are inspected
+  const int vs = (c->p > 1 && !c->mixed) ? 1 : 0;      // view-sum launch of the adjoint
   const int per_graph = c->graph_units * (sgp ? (c->prm.constraint == 1 ? kSgpLaunches + kFluxLaunches : kSgpLaunches) +
-                                                    (land ? kLandPasses : 0)
-                                              : kRlLaunches);
+                                                    (land ? kLandPasses : 0) + vs
+                                              : kRlLaunches + vs);
   CU(cudaGraphLaunch(g, c->s));
   c->launches += per_graph;
   CU(cudaMemcpyAsync(slot[0], c->L.ctrl, sizeof(CtrlState) * c->n, cudaMemcpyDeviceToHost, c->s));
@@ -1207,7 +1238,7 @@ sgp_status sgp_apply_AT(sgp_ctx* c, int image, const float* y, float* out) {
   float2* sp1 = reinterpret_cast<float2*>(d.spec) + P / 2;
   void* a2[] = {(void*)&src, (void*)&ivs, (void*)&sp1, (void*)&ovs, (void*)&Hh, (void*)&p, (void*)&clamp};
   if ((st = launch(g_reg.row[ROP_R2C][0][si], per_view * p, kRowBlock, g_reg.row_smem[si], c->s, a2))) return st;
-  if ((st = col_pass(c, COL_PTO1, JOB_AT_RAW * c->n, image))) return st;
+  if ((st = adjoint_cols(c, JOB_AT_RAW * c->n, image))) return st;
   const float2* sp0 = reinterpret_cast<const float2*>(d.spec);
   float sc = 1.0f;
   void* a3[] = {(void*)&sp0, (void*)&ovs, (void*)&out, (void*)&ivs, (void*)&Hh, (void*)&one, (void*)&sc};
@@ -1238,7 +1269,7 @@ sgp_status sgp_time_passes(sgp_ctx* c, int iters, double* ms_out, int n_out) {
     CU(cudaEventRecord(ev[q++], c->s));
     auto step = [&](sgp_status s2) { if (!st) st = s2; cudaEventRecord(ev[q++], c->s); };
     step(row_pass(c, ROP_SGP_UPDATE, true));
-    step(col_pass(c, COL_PTO1, JOB_AT * c->n));
+    step(adjoint_cols(c, JOB_AT * c->n));
     step(row_pass(c, ROP_SGP_GRAD, false));
     step(row_pass(c, ROP_SGP_Y, false));
     step(col_pass(c, COL_1TOP, JOB_A * c->n));

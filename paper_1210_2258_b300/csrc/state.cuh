@@ -42,7 +42,7 @@ constexpr int kArmExtra = 30;           // theta^1 .. theta^30 at most in the ex
 constexpr int kFluxCand = 16;       // candidate mu values per flux-search pass (slots SLOT_ARMX..)
 constexpr int kFluxPasses = 5;
 
-enum ColMode { COL_KHAT = 0, COL_1TOP = 1, COL_1TOP_CONJ = 2, COL_PTO1 = 3 };
+enum ColMode { COL_KHAT = 0, COL_1TOP = 1, COL_1TOP_CONJ = 2, COL_PTO1 = 3, COL_PTOV = 4 };
 
 enum StopKind { STOP_FIXED = 0, STOP_CONVERGENCE = 1, STOP_DISCREPANCY = 2, STOP_MIN_ERROR = 3, STOP_LANDED = 4 };
 constexpr int kLandCand = kArmExtra;   // step lengths per landing pass (slots SLOT_ARMX..)
