@@ -99,6 +99,34 @@ def test_multi_view_rl_and_sgp(gpu):
     assert abs(prob3.kl_value() - ref40.J) <= 1e-3 * ref40.J
 
 
+@pytest.mark.parametrize("p", [2, 5])
+def test_multi_view_other_view_counts(gpu, p):
+    """The per-view adjoint column pass and the view sum for p other than 3 (operators, RL, a few
+    SGP iterations)."""
+    sc = scenes.cluster_multiview_scene(seed=2, N=96, p=p, n_sources=30)
+    orc = oracle_problem(sc)
+    prob = gpu_problem(gpu, sc)
+    rng = np.random.default_rng(p)
+    f = rng.random(sc.g.shape[-2:])
+    y = rng.random(sc.g.shape)
+    Af = host(prob.apply_A(dev(f)))
+    ATy = host(prob.apply_AT(dev(y)))
+    f32, y32 = f.astype(np.float32).astype(np.float64), y.astype(np.float32).astype(np.float64)
+    for j in range(p):
+        assert rel_l2(Af[j], orc.A(j, f32)) <= 1e-5
+    assert rel_l2(ATy, sum(orc.AT(j, y32[j]) for j in range(p))) <= 1e-5
+    ref_rl = O.rl(orc, stop=O.StopRule("fixed", max_iter=30))
+    rl = gpu_problem(gpu, sc)
+    rl.rl_iterate(30)
+    assert rel_l2(host(rl.get_f()), ref_rl.f) <= 1e-3
+    assert abs(rl.kl_value() - ref_rl.J) <= 1e-5 * ref_rl.J
+    ref = O.sgp(orc, stop=O.StopRule("fixed", max_iter=10))
+    sg = gpu_problem(gpu, sc)
+    sg.sgp_iterate(10)
+    assert rel_l2(host(sg.get_f()), ref.f) <= 1e-3
+    assert abs(sg.kl_value() - ref.J) <= 1e-5 * ref.J
+
+
 def test_boundary_rl_and_sgp(gpu):
     sc = scenes.boundary_scene(scenes.rng_for(5), 96, 2.0, 10.0)
     orc = oracle_problem(sc)
