@@ -155,13 +155,13 @@ __device__ __forceinline__ bool arrive_last(CtrlState* c, int n_blocks) {
   __shared__ int s_last;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();                                   // release this block's partials
-    const unsigned prev = atomicAdd(&c->arrive, 1u);
+    // acquire-release at device scope: thread 0 stored this block's partials before the add
+    // (release); the last block then sees every other block's partials (acquire) and passes them
+    // to its other threads through the barrier below
+    unsigned prev;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(prev) : "l"(&c->arrive) : "memory");
     const int last = prev == unsigned(n_blocks - 1);
-    if (last) {
-      c->arrive = 0u;
-      __threadfence();                                 // acquire the other blocks' partials
-    }
+    if (last) c->arrive = 0u;
     s_last = last;
   }
   __syncthreads();
