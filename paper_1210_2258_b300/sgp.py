@@ -23,6 +23,7 @@ STOP_FIXED, STOP_CONVERGENCE, STOP_DISCREPANCY, STOP_MIN_ERROR, STOP_LANDED = ra
 START_ZERO, START_DATA, START_CONSTANT, START_USER = range(4)
 PSF_CENTER, PSF_CORNER = 0, 1
 N_PASSES = 7    # passes of one SGP iteration (sgp_time_passes)
+MAX_VIEWS = 8   # views per problem (sgp_inputs.b_const)
 SIDES = (16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048)
 
 
@@ -155,6 +156,8 @@ class Problems:
         masks = masks if masks is not None else [None] * n
         self.n = n
         self.p, self.H, self.W = (int(s) for s in psfs[0].shape)
+        if self.p > MAX_VIEWS:
+            raise SGPError(ERR_ARG, f"at most {MAX_VIEWS} views per problem")
         self.params = params or default_params()
         shapes = (Shape * n)()
         inputs = (Inputs * n)()
