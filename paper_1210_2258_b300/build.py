@@ -19,8 +19,10 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(LIBDIR, "libsgp_b300.so")
-UNITS = ["k_small.cu", "k_mid.cu", "k_large.cu", "k_multi_sgp_a.cu", "k_multi_sgp_b.cu", "k_multi_rest.cu", "runtime.cu",
-         "warmstart.cu"]
+# the slowest units first, so that the pool starts them first
+UNITS = ["k_multi_armx_d.cu", "k_multi_armx_f.cu", "k_multi_land_d.cu", "k_multi_land_f.cu", "k_multi_sgp_b.cu",
+         "k_mid_b.cu", "k_mid.cu", "k_large.cu", "k_large_b.cu", "k_small.cu", "k_multi_sgp_a.cu", "k_multi_rest.cu",
+         "runtime.cu", "warmstart.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-Wno-deprecated-gpu-targets"]
@@ -55,7 +57,7 @@ def _compile(unit: str, force: bool) -> str:
 def build(force: bool = False) -> str:
     os.makedirs(OBJDIR, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(UNITS), os.cpu_count() or 8)) as ex:
         objs = list(ex.map(lambda u: _compile(u, force), UNITS))
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart"]

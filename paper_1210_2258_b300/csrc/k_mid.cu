@@ -1,4 +1,4 @@
-// Passes for sides 96 128 192 256 384 512.
+// Passes for sides 96 128 192.
 #include "kernels_inst.cuh"
 
 namespace sgp {
@@ -7,9 +7,6 @@ void register_mid(Registry& R) {
   register_side<96>(R);
   register_side<128>(R);
   register_side<192>(R);
-  register_side<256>(R);
-  register_side<384>(R);
-  register_side<512>(R);
   R.twiddle_init[1] = &twiddle_init_mid;
 }
 }  // namespace sgp

@@ -36,4 +36,16 @@ constexpr size_t max_col_smem() {
     SGP_SWITCH_SIDE(W, BODY)                                                                              \
   }
 
+// the same with the reduction precision fixed (a plain kernel, for units that build one variant)
+#define SGP_MULTI_ROW_FIXED(NAME, BODY, FP64V)                                                            \
+  __global__ void __launch_bounds__(kRowBlock) NAME(const ImgDesc* __restrict__ imgs, const int2* __restrict__ items, \
+                                                    int n_items, int extra) {                              \
+    constexpr bool FP64 = FP64V;                                                                          \
+    const int it = blockIdx.x;                                                                            \
+    if (it >= n_items) return;                                                                            \
+    const int W = imgs[items[it].x].W;                                                                    \
+    (void)extra;                                                                                          \
+    SGP_SWITCH_SIDE(W, BODY)                                                                              \
+  }
+
 }  // namespace sgp

@@ -21,7 +21,7 @@ enum RowOp {
 constexpr int kColModes = 6;
 constexpr int kColPto1P1 = 5;
 
-constexpr int kTwiddleUnits = 6;   // translation units with their own twiddle table
+constexpr int kTwiddleUnits = 8;   // translation units with their own twiddle table (null: none)
 
 struct Registry {
   const void* row[ROP_COUNT][2][kNumSides];   // [op][fp64][side]
@@ -37,11 +37,18 @@ struct Registry {
   size_t row_multi_smem, col_multi_smem;
 };
 
+// one per translation unit; register_all (runtime.cu) calls every one
 void register_small(Registry&);
 void register_mid(Registry&);
+void register_mid_b(Registry&);
 void register_large(Registry&);
+void register_large_b(Registry&);
 void register_multi_sgp_a(Registry&);
 void register_multi_sgp_b(Registry&);
+void register_multi_armx_f(Registry&);
+void register_multi_armx_d(Registry&);
+void register_multi_land_f(Registry&);
+void register_multi_land_d(Registry&);
 void register_multi_rest(Registry&);
 
 }  // namespace sgp

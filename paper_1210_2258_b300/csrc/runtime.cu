@@ -38,17 +38,27 @@ sgp_status fail(sgp_status st, const std::string& msg) {
 // ------------------------------------------------------------------------------ registry
 Registry g_reg;
 bool g_reg_ready = false;
+
+void register_all(Registry& R) {
+  memset(&R, 0, sizeof(R));
+  register_small(R);
+  register_mid(R);
+  register_mid_b(R);
+  register_large(R);
+  register_large_b(R);
+  register_multi_sgp_a(R);
+  register_multi_sgp_b(R);
+  register_multi_armx_f(R);
+  register_multi_armx_d(R);
+  register_multi_land_f(R);
+  register_multi_land_d(R);
+  register_multi_rest(R);
+}
 bool g_dev_ready[64] = {false};
 
 sgp_status ensure_device_ready(int dev) {
   if (!g_reg_ready) {
-    memset(&g_reg, 0, sizeof(g_reg));
-    register_small(g_reg);
-    register_mid(g_reg);
-    register_large(g_reg);
-    register_multi_sgp_a(g_reg);
-    register_multi_sgp_b(g_reg);
-    register_multi_rest(g_reg);
+    register_all(g_reg);
     g_reg_ready = true;
   }
   if (dev < 0 || dev >= 64) return fail(SGP_ERR_CUDA, "device index out of range");
@@ -63,7 +73,8 @@ sgp_status ensure_device_ready(int dev) {
       tab[off + q] = make_float2(float(cos(a)), float(sin(a)));
     }
   }
-  for (int i = 0; i < kTwiddleUnits; ++i) CU(g_reg.twiddle_init[i](tab.data()));
+  for (int i = 0; i < kTwiddleUnits; ++i)
+    if (g_reg.twiddle_init[i]) CU(g_reg.twiddle_init[i](tab.data()));
   for (int op = 0; op < ROP_COUNT; ++op)
     for (int f = 0; f < 2; ++f)
       if (g_reg.row_multi[op][f])
@@ -724,13 +735,7 @@ size_t sgp_workspace_bytes(int n, const sgp_shape* shapes, const sgp_params* par
   int dev = 0;
   cudaGetDevice(&dev);
   if (!g_reg_ready) {
-    memset(&g_reg, 0, sizeof(g_reg));
-    register_small(g_reg);
-    register_mid(g_reg);
-    register_large(g_reg);
-    register_multi_sgp_a(g_reg);
-    register_multi_sgp_b(g_reg);
-    register_multi_rest(g_reg);
+    register_all(g_reg);
     g_reg_ready = true;
   }
   sgp_params P;
