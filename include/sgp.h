@@ -172,6 +172,17 @@ SGP_API sgp_status rl_iterate(sgp_ctx* ctx, int n);
 /* n SGP iterations (Algorithm 1) of every problem.  Asynchronous. */
 SGP_API sgp_status sgp_iterate(sgp_ctx* ctx, int n);
 
+/* n OSEM iterations (ordered-subset expectation maximisation, Sect. 2.3, Algorithm 2) of every
+ * problem, from its current iterate: each iteration cycles over the views j = 1..p in order with
+ * h <- h o A_j^T (g_j / (A_j h + b_j)) (Eq. OSEMstep), or, with a boundary mask,
+ * h <- (M_R / alpha_j) o h o A_j^T (...) (Eq. boundaryOSEM), alpha_j = K_j (x) M_S.  Four passes per
+ * view (4p transforms per iteration).  With p = 1 it is RL.  Afterwards kl_value gives J_0 of the
+ * result and sgp_get_f the result; sgp_get_info's k counts view updates (p per iteration).  No
+ * stop rule (the paper runs OSEM for a given number of iterations).  Needs problems of one size
+ * (SGP_ERR_STATE for a context of mixed sizes).  Asynchronous, except that the first call after
+ * set-up may tune the row tile (see sgp_get_tile). */
+SGP_API sgp_status osem_iterate(sgp_ctx* ctx, int n);
+
 /* Iterate SGP (resp. RL) on every problem until its stop rule fires or max_iter further
  * iterations; iters (n ints, may be NULL) receives each problem's iteration count.
  * Returns SGP_ERR_TIMEOUT if some problem reached max_iter before a non-FIXED rule fired, or the

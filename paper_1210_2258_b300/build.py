@@ -13,6 +13,7 @@ import os
 import shutil
 import subprocess
 import sys
+import time
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -48,9 +49,13 @@ def _compile(unit: str, force: bool) -> str:
     if not force and os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _headers_mtime(unit)):
         return obj
     cmd = [nvcc()] + ARCH + FLAGS + ["-c", src, "-o", obj]
+    t0 = time.time()
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {unit}:\n{r.stdout}\n{r.stderr}")
+    # date the object by the start of its compilation: a source edited while nvcc ran is newer,
+    # so the next build recompiles it (objects of one library must agree on the shared structs)
+    os.utime(obj, (t0, t0))
     return obj
 
 
@@ -59,7 +64,7 @@ def build(force: bool = False) -> str:
     os.makedirs(LIBDIR, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=min(len(UNITS), os.cpu_count() or 8)) as ex:
         objs = list(ex.map(lambda u: _compile(u, force), UNITS))
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) <= max(os.path.getmtime(o) for o in objs):
         cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

@@ -276,6 +276,15 @@ __device__ void rl_decide(const ImgDesc& d, CtrlState* c, double kl, double rr) 
   if (c->stop_kind == STOP_DISCREPANCY && 2.0 * c->J * c->inv_pS <= c->eta) stop = true;
   if (stop) { c->done = 2; c->have_v = 0; }
 }
+// OSEM bookkeeping (Algorithm 2), by one thread: an update h <- w_j h A_j^T r_j was applied when v
+// was available; count it (k counts view updates, p per OSEM iteration; f[k & 1] holds h).
+__device__ inline void osem_tick(CtrlState* c, int have_v_after) {
+  if (threadIdx.x == 0) {
+    c->k += c->have_v;
+    c->have_v = have_v_after;
+  }
+}
+
 template <bool FP64>
 __device__ void ctrl_rl(const ImgDesc& d) {
   __shared__ CtrlState s;

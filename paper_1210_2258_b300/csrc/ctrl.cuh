@@ -317,7 +317,9 @@ __global__ void k_fill_start(float* __restrict__ f, const float* __restrict__ w,
 }
 
 // boundary set-up: R = {alpha_j >= sigma for every j}, w = M_R / sum_j alpha_j (Eq. Rdef, boundaryRL)
-__global__ void k_make_w(const float* __restrict__ alpha, int p, size_t P, float sigma, float* __restrict__ w) {
+// and the per-view OSEM weights wv_j = M_R / alpha_j (Eq. boundaryOSEM)
+__global__ void k_make_w(const float* __restrict__ alpha, int p, size_t P, float sigma, float* __restrict__ w,
+                         float* __restrict__ wv) {
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < P; i += size_t(gridDim.x) * blockDim.x) {
     float s = 0.0f;
     bool inR = true;
@@ -327,7 +329,17 @@ __global__ void k_make_w(const float* __restrict__ alpha, int p, size_t P, float
       s += a;
     }
     w[i] = (inR && s > 0.0f) ? 1.0f / s : 0.0f;
+    for (int j = 0; j < p; ++j) {
+      const float a = alpha[size_t(j) * P + i];
+      wv[size_t(j) * P + i] = (inR && a > 0.0f) ? 1.0f / a : 0.0f;
+    }
   }
+}
+
+// OSEM: count the pending update of every problem (after the last sub-step of a call)
+__global__ void k_osem_tick(const ImgDesc* __restrict__ imgs, int n, int have_v_after) {
+  const int i = blockIdx.x;
+  if (i < n) osem_tick(imgs[i].ctrl, have_v_after);
 }
 
 __global__ void k_u8_to_float(const uint8_t* __restrict__ m, float* __restrict__ out, size_t P) {

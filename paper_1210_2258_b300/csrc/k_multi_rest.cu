@@ -2,7 +2,7 @@
 #include "multi_common.cuh"
 
 namespace sgp {
-#define B6(N) b_rl_update<N, FP64>(imgs, items, n_items)
+#define B6(N) b_rl_update<N, FP64>(imgs, items, n_items, extra)
 SGP_MULTI_ROW(km_rl_update, B6)
 #define B7(N) b_rl_ratio<N, FP64>(imgs, items, n_items, extra)
 SGP_MULTI_ROW(km_rl_ratio, B7)

@@ -706,9 +706,12 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_land(const ImgDesc* __restric
 
 // RL K1: if plane 0 holds v = sum_j A_j^T r_j, f <- w f v (Eq. RL / multipleRL / boundaryRL);
 // then R2C of the current iterate into plane 0 (and the rho partial).
+// OSEM sub-step (wview = j >= 0, Algorithm 2): plane j+1 holds v_j = A_j^T (r_j - 1) of view j
+// only, and h <- w_j h A_j^T r_j = h (1 + w_j v_j) with w_j = 1 / A_j^T 1 = 1 (periodic, unit-volume
+// PSF; Eq. OSEMstep) or M_R / alpha_j (Eq. boundaryOSEM); the R2C of h still goes to plane 0.
 template <int W, bool FP64>
 __device__ __forceinline__ void b_rl_update(const ImgDesc* __restrict__ imgs,
-                                                        const int2* __restrict__ items, int n_items) {
+                                                        const int2* __restrict__ items, int n_items, int wview) {
   pdl_enter();
   using G = RowGeo<W>;
   extern __shared__ float2 smem[];
@@ -726,7 +729,8 @@ __device__ __forceinline__ void b_rl_update(const ImgDesc* __restrict__ imgs,
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
     float2* sp = spec_plane(d, 0) + off;
-    if (hv) row_spec_to_real<W>(x, sp, t, act);
+    const bool osem = wview >= 0;
+    if (hv) row_spec_to_real<W>(x, osem ? spec_plane(d, wview + 1) + off : sp, t, act);
     KSum acc[1];
     if (act) {
       const float* fo = d.f[k & 1];
@@ -737,7 +741,9 @@ __device__ __forceinline__ void b_rl_update(const ImgDesc* __restrict__ imgs,
         const size_t i = off + t + q * G::T;
         float2 f = ld2(fo, i);
         if (hv) {   // w f sum_j A_j^T r_j = f (1 + w v) on R, v = sum_j A_j^T (r_j - 1)
-          const float2 v = x(t + q * G::T), w = w_pair(d, i);
+          const float2 v = x(t + q * G::T);
+          const float2 w = !osem ? w_pair(d, i)
+                                 : (d.wv ? ld2(d.wv + size_t(wview) * d.P, i) : make_float2(1.0f, 1.0f));
           f.x = w.x > 0.0f ? fmaf(f.x * w.x, v.x, f.x) : 0.0f;
           f.y = w.y > 0.0f ? fmaf(f.y * w.y, v.y, f.y) : 0.0f;
           st2(fn, i, f);
@@ -755,12 +761,14 @@ __device__ __forceinline__ void b_rl_update(const ImgDesc* __restrict__ imgs,
 }
 template <int W, bool FP64>
 __global__ void __launch_bounds__(kRowBlock) k_rl_update(const ImgDesc* __restrict__ imgs,
-                                                        const int2* __restrict__ items, int n_items) {
-  b_rl_update<W, FP64>(imgs, items, n_items);
+                                                        const int2* __restrict__ items, int n_items, int wview) {
+  b_rl_update<W, FP64>(imgs, items, n_items, wview);
 }
 
 // RL K3 (also a set-up pass): per view, C2R of plane j+1 (= A_j f) -> KL partials and
-// r_j = g_j/(A_j f + b_j) -> R2C back into plane j+1; optionally stores A_j f into u.
+// r_j = g_j/(A_j f + b_j) -> R2C back into plane j+1.  write_u: 0 RL iteration (RL controller),
+// 1 set-up (stores A_j f into u), 2 OSEM sub-step (the items of one view, in a view-major list: no
+// partial sums; the last block of a problem counts the update, see osem_tick).
 template <int W, bool FP64>
 __device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
                                                        const int2* __restrict__ items, int n_items, int write_u) {
@@ -788,7 +796,7 @@ __device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
     for (int q = 0; q < G::E; ++q) {
       const size_t i = off + t + q * G::T;
       const float2 u = x(t + q * G::T), g = ld2(gj, i), b = b_pair(d, j, i);
-      if (write_u) st2(uj, i, u);
+      if (write_u == 1) st2(uj, i, u);
       const float u0x = u.x + b.x, u0y = u.y + b.y;
       float2 rm;
       acc[0].add(kl_ratio(g.x, u0x, rm.x));
@@ -797,6 +805,10 @@ __device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
     }
   }
   row_real_to_spec<W>(x, sp, t, act);
+  if (write_u == 2) {
+    if (arrive_last(d.ctrl, d.n_row_items)) osem_tick(d.ctrl, 1);
+    return;
+  }
   block_sum_store<1, FP64>(acc, partv_of(d, it) + SLOT_KL);
   if (!write_u && arrive_last(d.ctrl, d.n_rv_items)) ctrl_rl<FP64>(d);   // RL iteration (not set-up)
 }

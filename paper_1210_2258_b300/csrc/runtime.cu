@@ -125,7 +125,9 @@ struct Layout {
   ImgDesc* d_imgs = nullptr;
   int2* d_row = nullptr;               // row list
   int2* d_rv = nullptr;                // row-view list
+  int2* d_rvo = nullptr;               // row-view list, view-major over the problems (OSEM sub-steps)
   int2* d_colv = nullptr;              // column list with views (1 -> p passes)
+  int2* d_colvo = nullptr;             // the same, view-major over the problems (OSEM sub-steps)
   int2* d_col = nullptr;               // column list (p -> 1 passes)
   int2* d_colk = nullptr;              // column list of the PSF spectrum jobs
   ColJob* d_jobs = nullptr;            // 5 jobs per problem: A, AT, CONJ, A_raw, AT_raw, then p KHAT jobs
@@ -167,6 +169,7 @@ void plan_layout(char* base, int n, const sgp_shape* sh, int trace_cap, const bo
     L.bcopy[i] = (has_b && has_b[i]) ? cv.take<float>(P * p) : nullptr;
     d.b = L.bcopy[i];
     d.w = d.boundary ? cv.take<float>(P) : nullptr;
+    d.wv = d.boundary ? cv.take<float>(P * p) : nullptr;
     d.spec = cv.take<float>(P * (p + 1));
     L.khat[i] = cv.take<float>(P * p);
     L.khatq[i] = cv.take<float>(size_t(2) * H * p);
@@ -181,7 +184,9 @@ void plan_layout(char* base, int n, const sgp_shape* sh, int trace_cap, const bo
   L.d_imgs = cv.take<ImgDesc>(n);
   L.d_row = cv.take<int2>(L.cap_row);
   L.d_rv = cv.take<int2>(L.cap_rv);
+  L.d_rvo = cv.take<int2>(L.cap_rv);
   L.d_colv = cv.take<int2>(L.n_colv);
+  L.d_colvo = cv.take<int2>(L.n_colv);
   L.d_col = cv.take<int2>(L.n_col);
   L.d_colk = cv.take<int2>(L.n_colk);
   int nj = 0;
@@ -209,6 +214,7 @@ struct sgp_ctx {
   int fp64 = 1;
   // host mirrors
   std::vector<int2> row, rv, colv, col, colk;
+  std::vector<int2> rvo, colvo;    // view-major lists of the OSEM sub-steps (uniform contexts)
   std::vector<int> order;          // problems, largest first (the order of their items)
   int rpi_hot = 0;                 // rows per item of the hot row passes (uniform sizes)
   int row_threads = kRowBlock;     // threads per block of the hot row passes
@@ -222,8 +228,9 @@ struct sgp_ctx {
   std::vector<int> has_data;
   std::vector<const float*> truth;
   std::vector<int> start_in_f0;    // 1: a new start was written to f[0] since the last set-up
-  int mode = 0;                    // 0 not prepared, 1 SGP, 2 RL
+  int mode = 0;                    // 0 not prepared, 1 SGP, 2 RL, 3 OSEM
   cudaGraphExec_t g_sgp = nullptr, g_rl = nullptr, g_land = nullptr;   // g_land: SGP + landing passes
+  cudaGraphExec_t g_osem = nullptr;  // one OSEM iteration (p sub-steps)
   int graph_units = 8;
   long long launches = 0;          // kernels enqueued (graph nodes counted per graph launch)
   CtrlState* h_ctrl = nullptr;     // pinned mirror of the controller array (2 slots for polling)
@@ -293,6 +300,13 @@ sgp_status fill_row_items(sgp_ctx* c, int R) {
     rv0 += d.n_rv_items;
   }
   if (r0 > L.cap_row || rv0 > L.cap_rv) return fail(SGP_ERR_ARG, "row tile below the planned minimum");
+  // view-major copy (uniform contexts: every problem has p views): the items of view j of every
+  // problem are the contiguous range [j * n_row, (j + 1) * n_row)
+  c->rvo.clear();
+  if (!c->mixed)
+    for (int j = 0; j < c->p; ++j)
+      for (int i : c->order)
+        for (int y = 0; y < L.d[i].H; y += L.d[i].rpi) c->rvo.push_back(make_int2(i, y | (j << 16)));
   L.n_row = r0;
   L.n_rv = rv0;
   if (!c->mixed) {
@@ -304,6 +318,8 @@ sgp_status fill_row_items(sgp_ctx* c, int R) {
   CU(cudaMemcpyAsync(L.d_imgs, L.d.data(), sizeof(ImgDesc) * c->n, cudaMemcpyHostToDevice, c->s));
   CU(cudaMemcpyAsync(L.d_row, c->row.data(), sizeof(int2) * c->row.size(), cudaMemcpyHostToDevice, c->s));
   CU(cudaMemcpyAsync(L.d_rv, c->rv.data(), sizeof(int2) * c->rv.size(), cudaMemcpyHostToDevice, c->s));
+  if (!c->rvo.empty())
+    CU(cudaMemcpyAsync(L.d_rvo, c->rvo.data(), sizeof(int2) * c->rvo.size(), cudaMemcpyHostToDevice, c->s));
   CU(cudaStreamSynchronize(c->s));
   return SGP_OK;
 }
@@ -411,6 +427,39 @@ sgp_status seq_rl_unit(sgp_ctx* c) {
   if ((st = col_pass(c, COL_1TOP, JOB_A * c->n))) return st;
   if ((st = row_pass(c, ROP_RL_RATIO, true, 0))) return st;     // + RL controller
   return adjoint_cols(c, JOB_AT * c->n);
+}
+
+// One OSEM iteration (Algorithm 2): for j = 0 .. p-1 the sub-step
+//   h <- w_{j-1} h A_{j-1}^T r_{j-1}  (pending from the previous sub-step; R2C of h -> plane 0)
+//   A_j h -> plane j+1;  r_j - 1 -> plane j+1;  v_j = A_j^T (r_j - 1) in plane j+1
+// over the view-major item lists, so that each launch covers view j of every problem: 4p launches
+// (the paper's 4p FFTs).  The update of the last view is applied by the next iteration's first
+// sub-step, or by the final pass of run_osem.
+sgp_status osem_row(sgp_ctx* c, RowOp op, int j, int extra) {
+  const void* fn = g_reg.row[op][c->fp64][side_index(c->W)];
+  const ImgDesc* imgs = c->L.d_imgs;
+  const int2* items = op == ROP_RL_UPDATE ? c->L.d_row : c->L.d_rvo + size_t(j) * c->L.n_row;
+  int n = c->L.n_row;
+  void* a[] = {(void*)&imgs, (void*)&items, (void*)&n, (void*)&extra};
+  return launch_pdl(fn, n, c->row_threads, c->row_smem_hot, c->s, a);
+}
+sgp_status osem_col(sgp_ctx* c, int variant, int job_off, int j) {
+  const int si = side_index(c->H);
+  const int2* items = c->L.d_colvo + size_t(j) * c->L.n_col;
+  int n = c->L.n_col;
+  const ColJob* jobs = c->L.d_jobs + job_off;
+  void* a[] = {(void*)&jobs, (void*)&items, (void*)&n};
+  return launch_pdl(g_reg.col[variant][si], n, kColBlock, g_reg.col_smem[si], c->s, a);
+}
+sgp_status seq_osem_iteration(sgp_ctx* c) {
+  sgp_status st;
+  for (int j = 0; j < c->p; ++j) {
+    if ((st = osem_row(c, ROP_RL_UPDATE, j, (j + c->p - 1) % c->p))) return st;
+    if ((st = osem_col(c, COL_1TOP, JOB_A * c->n, j))) return st;
+    if ((st = osem_row(c, ROP_RL_RATIO, j, 2))) return st;
+    if ((st = osem_col(c, COL_PTOV, JOB_AT * c->n, j))) return st;
+  }
+  return SGP_OK;
 }
 
 // flux-constrained projection: bracket, kFluxPasses candidate passes, exact final solve
@@ -695,6 +744,61 @@ sgp_status run_until(sgp_ctx* c, bool sgp, const sgp_stop_rule* rule, int* iters
   return res;
 }
 
+// n OSEM iterations from the current iterate; afterwards J_0 of the result (kl_value) and u = A f.
+sgp_status run_osem(sgp_ctx* c, int n_iter) {
+  if (n_iter < 0) return fail(SGP_ERR_ARG, "negative iteration count");
+  if (c->mixed) return fail(SGP_ERR_STATE, "OSEM needs problems of one size");
+  sgp_status st;
+  if (c->mode != 3) {
+    for (int i = 0; i < c->n; ++i)
+      if (!c->has_data[i]) return fail(SGP_ERR_STATE, "sgp_set_data was not called for every problem");
+    if ((st = reset_ctrl(c))) return st;   // k = 0, no pending update; f[0] holds the start
+    if (!c->tuned) {
+      c->tuned = true;
+      if ((st = autotune_rows(c))) return st;
+    }
+    c->mode = 3;
+  }
+  if (n_iter == 0) return SGP_OK;
+  if (!c->g_osem) {
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+    long long* saved = g_launch_counter;
+    g_launch_counter = nullptr;
+    st = seq_osem_iteration(c);
+    cudaError_t e = cudaStreamEndCapture(c->s, &g);
+    g_launch_counter = saved;
+    if (st) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return fail(SGP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->g_osem, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(SGP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  for (int l = 0; l < n_iter; ++l) {
+    CU(cudaGraphLaunch(c->g_osem, c->s));
+    c->launches += 4 * c->p;
+  }
+  // the pending update of view p-1, then J_0 and u at the result (as in the set-up)
+  if ((st = osem_row(c, ROP_RL_UPDATE, 0, c->p - 1))) return st;
+  {
+    const ImgDesc* imgs = c->L.d_imgs;
+    int n = c->n, zero = 0;
+    void* a[] = {(void*)&imgs, (void*)&n, (void*)&zero};
+    if ((st = launch((const void*)&k_osem_tick, n, 32, 0, c->s, a))) return st;
+  }
+  if ((st = col_pass(c, COL_1TOP, JOB_A * c->n))) return st;
+  if ((st = row_pass(c, ROP_RL_RATIO, true, 1))) return st;
+  {
+    const ImgDesc* imgs = c->L.d_imgs;
+    int adaptive = 0, wb = 0;
+    void* args[] = {(void*)&imgs, (void*)&adaptive, (void*)&wb};
+    if ((st = launch(c->fp64 ? (const void*)&k_ctrl_setup<true> : (const void*)&k_ctrl_setup<false>, c->n,
+                     kCtrlBlock, 0, c->s, args)))
+      return st;
+  }
+  return SGP_OK;
+}
+
 sgp_status check_image(sgp_ctx* c, int image) {
   if (!c) return fail(SGP_ERR_ARG, "ctx is NULL");
   if (image < 0 || image >= c->n) return fail(SGP_ERR_ARG, "image index out of range");
@@ -823,6 +927,10 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
     for (int j = 0; j < kMaxViews; ++j) d.bs[j] = j < d.p ? in[i].b_const[j] : 0.0f;
     d.ftrue = nullptr;
   }
+  if (!c->mixed)   // view-major column list of the OSEM sub-steps
+    for (int j = 0; j < c->p; ++j)
+      for (int i : order)
+        for (int x = 0; x < L.d[i].W / 2; x += cols_per_item(L.d[i].H)) c->colvo.push_back(make_int2(i, x | (j << 16)));
   // column jobs: kinds A, AT, CONJ, A_raw, AT_raw (index kind*n + i), then p KHAT jobs per problem
   c->jobs.assign(L.n_jobs, ColJob{});
   int kh = 5 * n;
@@ -902,6 +1010,8 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
   if (st) return bail(st);
   if (cudaMemcpyAsync(L.d_jobs, c->jobs.data(), sizeof(ColJob) * L.n_jobs, cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
       cudaMemcpyAsync(L.d_colv, c->colv.data(), sizeof(int2) * c->colv.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
+      (!c->colvo.empty() &&
+       cudaMemcpyAsync(L.d_colvo, c->colvo.data(), sizeof(int2) * c->colvo.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess) ||
       cudaMemcpyAsync(L.d_col, c->col.data(), sizeof(int2) * c->col.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
       cudaMemcpyAsync(L.d_colk, c->colk.data(), sizeof(int2) * c->colk.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess)
     return bail(fail(SGP_ERR_CUDA, "descriptor upload failed"));
@@ -948,8 +1058,9 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
     if ((st = launch(g_reg.row[ROP_C2R][0][si], per_view * d.p, kRowBlock, g_reg.row_smem[si], c->s, a3))) return bail(st);
     float sig = float(P.sigma_R);
     float* w = const_cast<float*>(d.w);
+    float* wv = const_cast<float*>(d.wv);
     const float* al = alpha;
-    void* a4[] = {(void*)&al, (void*)&nv, (void*)&d.P, (void*)&sig, (void*)&w};
+    void* a4[] = {(void*)&al, (void*)&nv, (void*)&d.P, (void*)&sig, (void*)&w, (void*)&wv};
     if ((st = launch((const void*)&k_make_w, grid_for(d.P), 256, 0, c->s, a4))) return bail(st);
   }
   // controller array: zero, then fresh state at first use
@@ -1088,6 +1199,13 @@ sgp_status rl_iterate(sgp_ctx* c, int n) {
   if (!c) return fail(SGP_ERR_ARG, "ctx is NULL");
   sgp_status st = enter(c);
   if (st || (st = run_fixed(c, false, n))) return st;
+  return leave(c);
+}
+
+sgp_status osem_iterate(sgp_ctx* c, int n) {
+  if (!c) return fail(SGP_ERR_ARG, "ctx is NULL");
+  sgp_status st = enter(c);
+  if (st || (st = run_osem(c, n))) return st;
   return leave(c);
 }
 
@@ -1317,6 +1435,7 @@ sgp_status sgp_set_tile(sgp_ctx* c, int rows) {
   if (c->g_sgp) { cudaGraphExecDestroy(c->g_sgp); c->g_sgp = nullptr; }
   if (c->g_land) { cudaGraphExecDestroy(c->g_land); c->g_land = nullptr; }
   if (c->g_rl) { cudaGraphExecDestroy(c->g_rl); c->g_rl = nullptr; }
+  if (c->g_osem) { cudaGraphExecDestroy(c->g_osem); c->g_osem = nullptr; }
   if ((st = fill_row_items(c, rows))) return st;
   c->tuned = true;
   c->mode = 0;   // the next solve re-initialises the iteration from the current iterate
@@ -1329,6 +1448,7 @@ sgp_status sgp_destroy(sgp_ctx* c) {
   if (c->g_sgp) cudaGraphExecDestroy(c->g_sgp);
   if (c->g_land) cudaGraphExecDestroy(c->g_land);
   if (c->g_rl) cudaGraphExecDestroy(c->g_rl);
+  if (c->g_osem) cudaGraphExecDestroy(c->g_osem);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   for (auto& e : c->ev_poll)

@@ -103,6 +103,7 @@ struct ImgDesc {
   float* g;                     // p planes: data; -1 marks pixels outside S (boundary mode)
   const float* b;               // p planes or nullptr
   const float* w;               // boundary: M_R / alpha (0 outside R); nullptr when periodic
+  const float* wv;              // boundary: p planes M_R / alpha_j (OSEM weights); nullptr when periodic
   float* spec;                  // (p+1) planes of packed spectra: plane 0, then views 1..p
   const float* ftrue;           // min-error stop only
   CtrlState* ctrl;

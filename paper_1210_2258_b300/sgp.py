@@ -78,6 +78,7 @@ def load() -> C.CDLL:
         "sgp_set_truth": (st, [vp, i, vp]),
         "rl_iterate": (st, [vp, i]),
         "sgp_iterate": (st, [vp, i]),
+        "osem_iterate": (st, [vp, i]),
         "sgp_solve_until": (st, [vp, C.POINTER(StopRule), C.POINTER(C.c_int)]),
         "rl_solve_until": (st, [vp, C.POINTER(StopRule), C.POINTER(C.c_int)]),
         "kl_value": (st, [vp, i, C.POINTER(d)]),
@@ -215,6 +216,10 @@ class Problems:
 
     def sgp_iterate(self, n: int) -> None:
         _check(load().sgp_iterate(self.ctx, n))
+
+    def osem_iterate(self, n: int) -> None:
+        """n OSEM iterations (Algorithm 2; boundary form with a mask)."""
+        _check(load().osem_iterate(self.ctx, n))
 
     def solve_until(self, kind: int, max_iter: int = 100000, tol: float = 0.0, eta: float = 1.0,
                     method: str = "sgp", raise_on_error: bool = True) -> list[int]:
