@@ -15,6 +15,9 @@ algorithm steps in the paper's order and notation:
   SGP        = Algorithm 1 with scaled BB1/BB2 (Eq. BB1, BB2), safeguards and alternation
                (Eq. alphadef), scaling (Eq. Dk / Dkbound), parameters of Sect. 3.2
   OSEM       = Algorithm 2, Eq. (OSEMstep) / (boundaryOSEM)
+  mosaic     = Sect. 4, second experiment (Table 2, Table 6): overlapping sub-domains, each
+               reconstructed with boundary-effect correction on a zero-padded array, the
+               non-overlapping central parts put together
   stop rules = Sect. 3.3 (fixed, Eq. convergence, min. reconstruction error, Eq. discrepancy)
 
 Readings of places where the paper is silent or garbled (all stated again in the design notes):
@@ -49,7 +52,7 @@ import numpy as np
 __all__ = [
     "prepare_psf", "conv_periodic", "corr_periodic", "Problem", "SGPParams", "StopRule",
     "sgp", "rl", "osem", "bb_steplengths", "choose_alpha", "adaptive_bounds",
-    "flux_projection", "kl_terms",
+    "flux_projection", "kl_terms", "mosaic_axis", "mosaic_split", "mosaic_stitch", "mosaic",
 ]
 
 
@@ -479,3 +482,81 @@ def osem(prob: Problem, f0: np.ndarray | None = None, n_iter: int = 10) -> Resul
                 h = h * v
         f = h
     return Result(f, n_iter, prob.kl(f), [])
+
+
+# ----------------------------------------------------------------------------- mosaic
+def mosaic_axis(N: int, n: int, s: int) -> list[tuple[int, int, int, int]]:
+    """One axis of the mosaic of Sect. 4 (second experiment): N pixels covered by n partially
+    overlapping sub-domains of s pixels and cut into n non-overlapping pieces.
+
+    Reading (the paper gives only the 256 -> 4 x 160^2 -> 4 x 128^2 example): sub-domain k starts
+    at floor(k (N - s) / (n - 1)) (0 for n = 1), so the first starts at 0 and the last ends at N;
+    piece k is [floor(k N / n), floor((k + 1) N / n)) and must lie inside sub-domain k.
+    Returns (sub-domain start, end, piece start, end) for k = 0..n-1."""
+    if n < 1 or s < 1 or s > N:
+        raise ValueError("need 1 <= s <= N and n >= 1")
+    out = []
+    for k in range(n):
+        w0 = 0 if n == 1 else (k * (N - s)) // (n - 1)
+        c0, c1 = (k * N) // n, ((k + 1) * N) // n
+        if c0 < w0 or c1 > w0 + s:
+            raise ValueError("piece %d [%d, %d) is not inside sub-domain [%d, %d)" % (k, c0, c1, w0, w0 + s))
+        out.append((w0, w0 + s, c0, c1))
+    return out
+
+
+def mosaic_split(g: np.ndarray, n, sub, ext):
+    """Sub-images of g (p, H, W) merged by zero padding into ext-sized arrays, the sub-image
+    centred (offset floor((ext - sub)/2)), with the masks M_S (1 on the sub-image).
+    Returns g_tiles (ny*nx, p, EH, EW) and masks (ny*nx, EH, EW), tiles in row-major order."""
+    g = np.asarray(g, np.float64)
+    if g.ndim == 2:
+        g = g[None]
+    p, H, W = g.shape
+    ay, ax = mosaic_axis(H, n[0], sub[0]), mosaic_axis(W, n[1], sub[1])
+    ey, ex = (ext[0] - sub[0]) // 2, (ext[1] - sub[1]) // 2
+    tiles, masks = [], []
+    for (y0, y1, _, _) in ay:
+        for (x0, x1, _, _) in ax:
+            t = np.zeros((p, ext[0], ext[1]))
+            t[:, ey:ey + sub[0], ex:ex + sub[1]] = g[:, y0:y1, x0:x1]
+            m = np.zeros((ext[0], ext[1]), np.uint8)
+            m[ey:ey + sub[0], ex:ex + sub[1]] = 1
+            tiles.append(t)
+            masks.append(m)
+    return np.stack(tiles), np.stack(masks)
+
+
+def mosaic_stitch(recs: np.ndarray, shape, n, sub, ext) -> np.ndarray:
+    """The mosaic: piece (ky, kx) of the H x W image taken from reconstruction ky*nx + kx."""
+    H, W = shape
+    ay, ax = mosaic_axis(H, n[0], sub[0]), mosaic_axis(W, n[1], sub[1])
+    ey, ex = (ext[0] - sub[0]) // 2, (ext[1] - sub[1]) // 2
+    out = np.zeros((H, W))
+    for ky, (y0, _, c0, c1) in enumerate(ay):
+        for kx, (x0, _, d0, d1) in enumerate(ax):
+            r = recs[ky * len(ax) + kx]
+            out[c0:c1, d0:d1] = r[ey + c0 - y0:ey + c1 - y0, ex + d0 - x0:ex + d1 - x0]
+    return out
+
+
+def mosaic(psfs_ext, g, b, n=(2, 2), sub=(160, 160), ext=(256, 256), method: str = "sgp",
+           n_iter: int = 50, sigma_R: float = 1e-2) -> np.ndarray:
+    """Boundary-corrected reconstruction of g (p, H, W) as a mosaic (Sect. 4, Table 2 / Table 6):
+    every sub-domain is reconstructed on its own zero-padded ext-sized array with the
+    boundary-effect correction of Sect. 2.4 (PSFs psfs_ext given on that array, centred), by
+    n_iter iterations of SGP, RL or OSEM; the pieces are put together."""
+    g = np.asarray(g, np.float64)
+    if g.ndim == 2:
+        g = g[None]
+    tiles, masks = mosaic_split(g, n, sub, ext)
+    recs = []
+    for t, m in zip(tiles, masks):
+        prob = Problem(psfs_ext, t, b, mask_S=m, sigma_R=sigma_R)
+        if method == "sgp":
+            recs.append(sgp(prob, stop=StopRule("fixed", max_iter=n_iter)).f)
+        elif method == "rl":
+            recs.append(rl(prob, stop=StopRule("fixed", max_iter=n_iter)).f)
+        else:
+            recs.append(osem(prob, n_iter=n_iter).f)
+    return mosaic_stitch(np.stack(recs), g.shape[-2:], n, sub, ext)
