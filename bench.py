@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling driver: set up the workload, run this many SGP iterations, exit")
-    ap.add_argument("--workload", default="galaxy2048", choices=["galaxy2048", "stars256", "multiview1024", "batch64"],
+    ap.add_argument("--workload", default="galaxy2048",
+                    choices=["galaxy2048", "stars256", "multiview1024", "batch64", "mosaic256"],
                     help="galaxy2048: the headline line (default); the others print one line each for the "
                          "other configurations (256^2 star field RL/SGP 200 iterations, 3 x 1024^2 multi-view "
                          "SGP to the discrepancy stop, a batch of 64 boundary problems of mixed sizes)")
@@ -448,6 +449,38 @@ def run_other_workload(args):
                      "value": it / (ms / 1e3), "time_to_stop_ms": ms, "iterations": it,
                      "final_discrepancy": D_sgp, "tile": pr.tile(), "rl": fixed["rl"], "osem": fixed["osem"],
                      "config": {"N": 1024, "p": 3, "psf": "two-pupil |FFT|^2 at 0/60/120 deg", "b": 20}})
+    elif args.workload == "mosaic256":
+        # Sect. 4 second experiment (Table 2): a 256^2 image as 4 overlapping 160^2 sub-domains, each
+        # zero-padded into 256^2 and reconstructed with the boundary correction (one context of 4
+        # problems), 128^2 pieces stitched; compared with the reconstruction of the full image
+        from paper_1210_2258_b300 import mosaic
+        rng = scenes.rng_for(args.seed)
+        N, sigma, b, n_it = 256, 2.0, 10.0, 100
+        f_true = scenes.star_field(rng, N, N, 50) + scenes.sersic_galaxy(rng, N, N, n_profiles=3, peak=5e3)
+        psf = scenes.gaussian_psf(N, N, sigma)
+        g = scenes.poisson(rng, scenes.blur_periodic(f_true, psf) + b)
+        ms = mosaic.MosaicSolver(dev(psf)[None], dev(g)[None], [b], (2, 2), (160, 160), (256, 256))
+        full = lib.Problems(dev(psf)[None], [b])
+        full.set_data(0, dev(g[None]))
+        err = lambda x: float(np.linalg.norm(x - f_true) / np.linalg.norm(f_true))
+        res = {}
+        for method in ("sgp", "rl"):
+            run = lambda m=method: ms.solve(m, n_it)
+            for _ in range(args.warmup):
+                run()
+            ms_m, out = _timed(torch, run, args.steps)
+            def run_full(m=method):
+                full.set_start(0, lib.START_CONSTANT)
+                getattr(full, m + "_iterate")(n_it)
+            for _ in range(args.warmup):
+                run_full()
+            ms_f, _ = _timed(torch, run_full, args.steps)
+            res[method] = {"iterations": n_it, "mosaic_ms": ms_m, "mosaic_rel_err": err(out.double().cpu().numpy()),
+                           "full_image_ms": ms_f, "full_image_rel_err": err(full.get_f().double().cpu().numpy())}
+        line.update({"metric": "256^2 mosaic of 4 boundary-corrected 160^2 sub-domains (in 256^2), 100 iterations",
+                     "unit": "ms", "value": res["sgp"]["mosaic_ms"], "higher_is_better": False,
+                     "sgp": res["sgp"], "rl": res["rl"],
+                     "config": {"N": N, "tiles": [2, 2], "sub": 160, "ext": 256, "psf": "Gaussian sigma 2", "b": b}})
     else:
         scs = scenes.boundary_batch(seed=args.seed, count=64)
         pr = lib.Problems([dev(s.psfs) for s in scs], [list(map(float, s.b)) for s in scs],

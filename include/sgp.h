@@ -252,6 +252,34 @@ SGP_API sgp_status sgp_set_tile(sgp_ctx* ctx, int rows_per_item);
 SGP_API sgp_status sgp_convolve_noalloc(const float* psf, const float* f, float* out, int H, int W,
                                         int psf_origin, int transpose, void* stream);
 
+/* Mosaic of boundary-corrected reconstructions (Sect. 4, second experiment; Table 2, Table 6).
+ * An H x W image is covered by ny x nx partially overlapping sub-domains of sub_h x sub_w pixels;
+ * each sub-image is merged by zero padding into an ext_h x ext_w array (sub-image centred at offset
+ * floor((ext - sub)/2), M_S = 1 on it), reconstructed there with the boundary-effect correction
+ * (a context of ny * nx boundary problems advancing together), and the mosaic keeps one
+ * non-overlapping piece of each reconstruction.  Along an axis of N pixels with n sub-domains of
+ * s pixels: sub-domain k = [floor(k (N - s)/(n - 1)), + s) and piece k = [floor(k N/n),
+ * floor((k + 1) N/n)) (the paper's example: 256 -> 2 x 160 -> pieces of 128).  1 <= ny, nx <= 16;
+ * sub <= the image and <= ext; every piece must lie inside its sub-domain (else SGP_ERR_ARG). */
+typedef struct {
+  int H, W;             /* image */
+  int ny, nx;           /* sub-domains per axis */
+  int sub_h, sub_w;     /* sub-domain size */
+  int ext_h, ext_w;     /* padded array (a supported side for the reconstruction context) */
+} sgp_mosaic;
+
+/* Checks the geometry and writes 4 (ny + nx) ints to out (may be NULL): for ky = 0..ny-1 the
+ * sub-domain start, end, piece start, end along H, then the same for kx along W. */
+SGP_API sgp_status sgp_mosaic_geometry(const sgp_mosaic* m, int* out);
+
+/* g: device p x H x W -> tiles: device (ny nx) x p x ext_h x ext_w (zero-padded sub-images, tile
+ * t = ky nx + kx) and masks: device (ny nx) x ext_h x ext_w uint8 M_S.  Asynchronous on stream. */
+SGP_API sgp_status sgp_mosaic_split(const sgp_mosaic* m, int p, const float* g, float* tiles, uint8_t* masks,
+                                    void* stream);
+
+/* recs: device (ny nx) x ext_h x ext_w reconstructions -> f: device H x W mosaic.  Asynchronous. */
+SGP_API sgp_status sgp_mosaic_stitch(const sgp_mosaic* m, const float* recs, float* f, void* stream);
+
 /* Release the context (not the workspace). */
 SGP_API sgp_status sgp_destroy(sgp_ctx* ctx);
 

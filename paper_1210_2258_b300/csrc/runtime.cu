@@ -14,6 +14,7 @@
 
 #include "../../include/sgp.h"
 #include "ctrl.cuh"
+#include "mosaic.cuh"
 #include "registry.h"
 #include "state.cuh"
 
@@ -1440,6 +1441,67 @@ sgp_status sgp_set_tile(sgp_ctx* c, int rows) {
   c->tuned = true;
   c->mode = 0;   // the next solve re-initialises the iteration from the current iterate
   return leave(c);
+}
+
+// ------------------------------------------------------------------------------ mosaic
+static sgp_status mosaic_geom(const sgp_mosaic* m, MosaicGeom& g) {
+  if (!m) return fail(SGP_ERR_ARG, "mosaic is NULL");
+  if (m->H < 1 || m->W < 1 || m->ny < 1 || m->nx < 1 || m->ny > kMosaicMax || m->nx > kMosaicMax)
+    return fail(SGP_ERR_ARG, "mosaic: need H, W >= 1 and 1 <= ny, nx <= 16");
+  if (m->sub_h < 1 || m->sub_w < 1 || m->sub_h > m->H || m->sub_w > m->W || m->ext_h < m->sub_h || m->ext_w < m->sub_w)
+    return fail(SGP_ERR_ARG, "mosaic: need 1 <= sub <= image and sub <= ext");
+  memset(&g, 0, sizeof(g));
+  g.H = m->H; g.W = m->W; g.ny = m->ny; g.nx = m->nx; g.sy = m->sub_h; g.sx = m->sub_w;
+  g.EH = m->ext_h; g.EW = m->ext_w; g.ey = (m->ext_h - m->sub_h) / 2; g.ex = (m->ext_w - m->sub_w) / 2;
+  for (int axis = 0; axis < 2; ++axis) {
+    const int N = axis ? m->W : m->H, n = axis ? m->nx : m->ny, sz = axis ? m->sub_w : m->sub_h;
+    int* w = axis ? g.wx : g.wy;
+    int* cb = axis ? g.cx : g.cy;
+    for (int k = 0; k < n; ++k) {
+      w[k] = n == 1 ? 0 : int((long long)k * (N - sz) / (n - 1));
+      cb[k] = int((long long)k * N / n);
+    }
+    cb[n] = N;
+    for (int k = 0; k < n; ++k)
+      if (cb[k] < w[k] || cb[k + 1] > w[k] + sz)
+        return fail(SGP_ERR_ARG, "mosaic: a piece is not inside its sub-domain (sub-domains too small)");
+  }
+  return SGP_OK;
+}
+
+sgp_status sgp_mosaic_geometry(const sgp_mosaic* m, int* out) {
+  MosaicGeom g;
+  sgp_status st = mosaic_geom(m, g);
+  if (st || !out) return st;
+  int o = 0;
+  for (int k = 0; k < g.ny; ++k) { out[o++] = g.wy[k]; out[o++] = g.wy[k] + g.sy; out[o++] = g.cy[k]; out[o++] = g.cy[k + 1]; }
+  for (int k = 0; k < g.nx; ++k) { out[o++] = g.wx[k]; out[o++] = g.wx[k] + g.sx; out[o++] = g.cx[k]; out[o++] = g.cx[k + 1]; }
+  return SGP_OK;
+}
+
+sgp_status sgp_mosaic_split(const sgp_mosaic* m, int p, const float* g, float* tiles, uint8_t* masks, void* stream) {
+  MosaicGeom geo;
+  sgp_status st = mosaic_geom(m, geo);
+  if (st) return st;
+  if (p < 1 || p > kMaxViews) return fail(SGP_ERR_SIZE_UNSUPPORTED, "1 <= p <= 8 views");
+  if (!g || !tiles || !masks) return fail(SGP_ERR_ARG, "NULL array");
+  const size_t total = size_t(geo.EH) * geo.EW * p * geo.ny * geo.nx;
+  const int grid = int(std::min<size_t>((total + 255) / 256, 148 * 8));
+  k_mosaic_split<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(g, p, geo, tiles, masks);
+  CU(cudaGetLastError());
+  return SGP_OK;
+}
+
+sgp_status sgp_mosaic_stitch(const sgp_mosaic* m, const float* recs, float* f, void* stream) {
+  MosaicGeom geo;
+  sgp_status st = mosaic_geom(m, geo);
+  if (st) return st;
+  if (!recs || !f) return fail(SGP_ERR_ARG, "NULL array");
+  const size_t total = size_t(geo.H) * geo.W;
+  const int grid = int(std::min<size_t>((total + 255) / 256, 148 * 8));
+  k_mosaic_stitch<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(recs, geo, f);
+  CU(cudaGetLastError());
+  return SGP_OK;
 }
 
 sgp_status sgp_destroy(sgp_ctx* c) {

@@ -54,6 +54,11 @@ class Info(C.Structure):
                 ("nS", C.c_double), ("flux_c", C.c_double)]
 
 
+class Mosaic(C.Structure):
+    _fields_ = [("H", C.c_int), ("W", C.c_int), ("ny", C.c_int), ("nx", C.c_int), ("sub_h", C.c_int),
+                ("sub_w", C.c_int), ("ext_h", C.c_int), ("ext_w", C.c_int)]
+
+
 _lib = None
 
 
@@ -92,6 +97,9 @@ def load() -> C.CDLL:
         "sgp_get_tile": (st, [vp, C.POINTER(i), C.POINTER(i)]),
         "sgp_set_tile": (st, [vp, i]),
         "sgp_convolve_noalloc": (st, [vp, vp, vp, i, i, i, i, vp]),
+        "sgp_mosaic_geometry": (st, [C.POINTER(Mosaic), C.POINTER(i)]),
+        "sgp_mosaic_split": (st, [C.POINTER(Mosaic), i, vp, vp, vp, vp]),
+        "sgp_mosaic_stitch": (st, [C.POINTER(Mosaic), vp, vp, vp]),
         "sgp_destroy": (st, [vp]),
         "sgp_last_error": (C.c_char_p, []),
     }
