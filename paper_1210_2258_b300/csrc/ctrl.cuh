@@ -336,6 +336,25 @@ __global__ void k_make_w(const float* __restrict__ alpha, int p, size_t P, float
   }
 }
 
+// Condition of the device-side solve loop (a WHILE node of a CUDA graph, see run_until): keep
+// iterating while some problem has not stopped (done == 0) and fewer than `cap` iterations have
+// run since the launch (counter, zeroed by the host before the launch).  One block; it is the last
+// node of the loop body, so it sees the controllers' decisions of this iteration.
+__global__ void k_loop_cond(const ImgDesc* __restrict__ imgs, int n, cudaGraphConditionalHandle h,
+                            int* __restrict__ counter, int cap) {
+  __shared__ int running;
+  if (threadIdx.x == 0) running = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (imgs[i].ctrl->done == 0) running = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int k = counter[0] + 1;
+    counter[0] = k;
+    cudaGraphSetConditional(h, (running && k < cap) ? 1u : 0u);
+  }
+}
+
 // OSEM: count the pending update of every problem (after the last sub-step of a call)
 __global__ void k_osem_tick(const ImgDesc* __restrict__ imgs, int n, int have_v_after) {
   const int i = blockIdx.x;

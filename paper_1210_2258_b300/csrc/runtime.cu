@@ -232,7 +232,11 @@ struct sgp_ctx {
   int mode = 0;                    // 0 not prepared, 1 SGP, 2 RL, 3 OSEM
   cudaGraphExec_t g_sgp = nullptr, g_rl = nullptr, g_land = nullptr;   // g_land: SGP + landing passes
   cudaGraphExec_t g_osem = nullptr;  // one OSEM iteration (p sub-steps)
+  // solve loops: a WHILE node around one iteration and the loop condition (run_until)
+  cudaGraphExec_t gl_sgp = nullptr, gl_rl = nullptr, gl_land = nullptr;
+  cudaGraphConditionalHandle hl_sgp = 0, hl_rl = 0, hl_land = 0;
   int graph_units = 8;
+  int loop_cap = 0;                // iteration cap captured in the solve loop graphs
   long long launches = 0;          // kernels enqueued (graph nodes counted per graph launch)
   CtrlState* h_ctrl = nullptr;     // pinned mirror of the controller array (2 slots for polling)
 };
@@ -519,6 +523,57 @@ sgp_status build_graph(sgp_ctx* c, bool sgp, cudaGraphExec_t* out, bool land = f
 }
 
 // Fresh controller state for every problem, with the current iterate moved to f[0].
+// The solve loop of run_until as one graph: a WHILE node whose body is one iteration (the same
+// passes as a unit of build_graph) followed by k_loop_cond, which ends the loop when every
+// problem has stopped or after `cap` iterations.  The iteration count stays on the device, so a
+// solve needs no host round trip and runs no idle iterations after the stop.
+constexpr int kLoopCounter = 4;   // index of the loop counter in L.d_flag
+sgp_status build_loop_graph(sgp_ctx* c, bool sgp, bool land, int cap, cudaGraphExec_t* out,
+                            cudaGraphConditionalHandle* hout) {
+  if (*out) return SGP_OK;
+  cudaGraph_t g = nullptr;
+  CU(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h = 0;
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  }
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(c->s, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                          cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(SGP_ERR_CUDA, std::string("solve loop graph: ") + cudaGetErrorString(e));
+  }
+  long long* saved = g_launch_counter;
+  g_launch_counter = nullptr;
+  sgp_status st = sgp ? seq_sgp_unit(c, land) : seq_rl_unit(c);
+  if (st == SGP_OK) {
+    const ImgDesc* imgs = c->L.d_imgs;
+    int n = c->n, cp = cap;
+    int* counter = c->L.d_flag + kLoopCounter;
+    void* a[] = {(void*)&imgs, (void*)&n, (void*)&h, (void*)&counter, (void*)&cp};
+    st = launch((const void*)&k_loop_cond, 1, 128, 0, c->s, a);
+  }
+  cudaGraph_t body = nullptr;
+  e = cudaStreamEndCapture(c->s, &body);
+  g_launch_counter = saved;
+  if (st || e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return st ? st : fail(SGP_ERR_CUDA, std::string("solve loop capture: ") + cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(SGP_ERR_CUDA, std::string("solve loop instantiate: ") + cudaGetErrorString(e));
+  *hout = h;
+  return SGP_OK;
+}
+
 sgp_status reset_ctrl(sgp_ctx* c) {
   CtrlState* h = c->h_ctrl;
   CU(cudaMemcpyAsync(h, c->L.ctrl, sizeof(CtrlState) * c->n, cudaMemcpyDeviceToHost, c->s));
@@ -706,35 +761,30 @@ sgp_status run_until(sgp_ctx* c, bool sgp, const sgp_stop_rule* rule, int* iters
   if (rule->kind == STOP_MIN_ERROR)
     for (int i = 0; i < c->n; ++i)
       if (!c->truth[i]) return fail(SGP_ERR_ARG, "minimum-error stop needs sgp_set_truth");
-  cudaGraphExec_t* gp = land ? &c->g_land : (sgp ? &c->g_sgp : &c->g_rl);
-  if ((st = build_graph(c, sgp, gp, land))) return st;
-  if ((st = arm(c, rule->kind, rule->max_iter, tol, rule->eta))) return st;
-  cudaGraphExec_t g = *gp;
-  const int max_launches = rule->max_iter / c->graph_units + 2;
-  CtrlState* slot[2] = {c->h_ctrl, c->h_ctrl + c->n};
-  // keep one chunk in flight while the flags of the previous one are inspected
-  const int vs = (c->p > 1 && !c->mixed) ? 1 : 0;      // view-sum launch of the adjoint
-  const int per_graph = c->graph_units * (sgp ? (c->prm.constraint == 1 ? kSgpLaunches + kFluxLaunches : kSgpLaunches) +
-                                                    (land ? kLandPasses : 0) + vs
-                                              : kRlLaunches + vs);
-  CU(cudaGraphLaunch(g, c->s));
-  c->launches += per_graph;
-  CU(cudaMemcpyAsync(slot[0], c->L.ctrl, sizeof(CtrlState) * c->n, cudaMemcpyDeviceToHost, c->s));
-  CU(cudaEventRecord(c->ev_poll[0], c->s));
-  int cur = 0;
-  for (int l = 1; l < max_launches; ++l) {
-    CU(cudaGraphLaunch(g, c->s));
-    c->launches += per_graph;
-    CU(cudaMemcpyAsync(slot[cur ^ 1], c->L.ctrl, sizeof(CtrlState) * c->n, cudaMemcpyDeviceToHost, c->s));
-    CU(cudaEventRecord(c->ev_poll[cur ^ 1], c->s));
-    CU(cudaEventSynchronize(c->ev_poll[cur]));
-    bool all = true;
-    for (int i = 0; i < c->n; ++i) all = all && slot[cur][i].done >= 1;
-    if (all) break;
-    cur ^= 1;
+  // one graph launch: a device-side loop of iterations until every problem has stopped (or
+  // max_iter + 2 iterations, past the controllers' own cap)
+  const int cap = rule->max_iter + 2;
+  cudaGraphExec_t* gp = land ? &c->gl_land : (sgp ? &c->gl_sgp : &c->gl_rl);
+  cudaGraphConditionalHandle* hp = land ? &c->hl_land : (sgp ? &c->hl_sgp : &c->hl_rl);
+  if (*gp && c->loop_cap != cap) {   // the cap is a kernel argument of the captured body
+    if (c->gl_sgp) { cudaGraphExecDestroy(c->gl_sgp); c->gl_sgp = nullptr; }
+    if (c->gl_rl) { cudaGraphExecDestroy(c->gl_rl); c->gl_rl = nullptr; }
+    if (c->gl_land) { cudaGraphExecDestroy(c->gl_land); c->gl_land = nullptr; }
   }
+  c->loop_cap = cap;
+  if ((st = build_loop_graph(c, sgp, land, cap, gp, hp))) return st;
+  if ((st = arm(c, rule->kind, rule->max_iter, tol, rule->eta))) return st;
+  const int vs = (c->p > 1 && !c->mixed) ? 1 : 0;      // view-sum launch of the adjoint
+  const int per_iter = (sgp ? (c->prm.constraint == 1 ? kSgpLaunches + kFluxLaunches : kSgpLaunches) +
+                                  (land ? kLandPasses : 0) + vs
+                            : kRlLaunches + vs) + 1;   // + the loop condition
+  CU(cudaMemsetAsync(c->L.d_flag + kLoopCounter, 0, sizeof(int), c->s));
+  CU(cudaGraphLaunch(*gp, c->s));
   if (sgp && (st = seq_sgp_finalize(c))) return st;
+  int bodies = 0;
+  CU(cudaMemcpyAsync(&bodies, c->L.d_flag + kLoopCounter, sizeof(int), cudaMemcpyDeviceToHost, c->s));
   if ((st = read_ctrl(c, c->h_ctrl))) return st;
+  c->launches += (long long)bodies * per_iter;
   sgp_status res = SGP_OK;
   for (int i = 0; i < c->n; ++i) {
     const CtrlState& h = c->h_ctrl[i];
@@ -1437,6 +1487,9 @@ sgp_status sgp_set_tile(sgp_ctx* c, int rows) {
   if (c->g_land) { cudaGraphExecDestroy(c->g_land); c->g_land = nullptr; }
   if (c->g_rl) { cudaGraphExecDestroy(c->g_rl); c->g_rl = nullptr; }
   if (c->g_osem) { cudaGraphExecDestroy(c->g_osem); c->g_osem = nullptr; }
+  if (c->gl_sgp) { cudaGraphExecDestroy(c->gl_sgp); c->gl_sgp = nullptr; }
+  if (c->gl_rl) { cudaGraphExecDestroy(c->gl_rl); c->gl_rl = nullptr; }
+  if (c->gl_land) { cudaGraphExecDestroy(c->gl_land); c->gl_land = nullptr; }
   if ((st = fill_row_items(c, rows))) return st;
   c->tuned = true;
   c->mode = 0;   // the next solve re-initialises the iteration from the current iterate
@@ -1511,6 +1564,9 @@ sgp_status sgp_destroy(sgp_ctx* c) {
   if (c->g_land) cudaGraphExecDestroy(c->g_land);
   if (c->g_rl) cudaGraphExecDestroy(c->g_rl);
   if (c->g_osem) cudaGraphExecDestroy(c->g_osem);
+  if (c->gl_sgp) cudaGraphExecDestroy(c->gl_sgp);
+  if (c->gl_rl) cudaGraphExecDestroy(c->gl_rl);
+  if (c->gl_land) cudaGraphExecDestroy(c->gl_land);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   for (auto& e : c->ev_poll)
