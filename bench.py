@@ -38,13 +38,16 @@ FALLBACK_HBM_GBS = 6400.0
 # extra Armijo pass and move O(1) bytes; the extra pass returns at once unless no step length of
 # the main pass was accepted (it then reads A f, A d, g), so it is counted as 0.
 PASS_NAMES = ["update_ratio", "col_AT", "grad_bb", "proj_y", "col_A", "ad_armijo", "armijo_extra"]
-PASS_PLANES = [8, 3, 5, 3, 3, 4, 0]
+# planes per pass: pixel planes (always whole) and spectrum planes (the PSF spectrum K_hat and the
+# packed spectra), of which the passes move only the band's columns (fraction band_cols / (N/2))
+PASS_PIX = [7, 0, 4, 2, 0, 3, 0]
+PASS_SPEC = [1, 3, 1, 1, 3, 1, 0]
+PASS_PLANES = [a + b for a, b in zip(PASS_PIX, PASS_SPEC)]   # without a band: 26 planes
 # DRAM bytes per launch of each pass at 2048^2 (ncu dram__bytes_read.sum + dram__bytes_write.sum,
 # caches flushed before the launch, second SGP iteration of `python bench.py --profile 8`), taken on
 # the kernels of this tree.  A pass's writes are still in L2 when its launch ends, so the figures
 # are its reads; they equal the algorithmic reads (no tile is read twice).
-TRAFFIC_2048 = {"update_ratio": 97.70e6, "col_AT": 33.64e6, "grad_bb": 67.54e6, "proj_y": 33.60e6,
-                "col_A": 33.64e6, "ad_armijo": 50.57e6, "armijo_extra": 0.07e6}
+TRAFFIC_2048 = {}
 
 
 def parse():
@@ -290,14 +293,16 @@ def run_ours(args):
     shares = [ms for ms in passes]
     dom = int(np.argmax(shares))
     peak, peak_kind = measured_peaks()
-    achieved = PASS_PLANES[dom] * B / (passes[dom] / 1e3) / 1e9
+    beta = info.band_cols / (N / 2)
+    planes = [a + b * beta for a, b in zip(PASS_PIX, PASS_SPEC)]
+    achieved = planes[dom] * B / (passes[dom] / 1e3) / 1e9
     iter_ms = sum(passes)
     roofline = {"bound": "hbm", "kernel": PASS_NAMES[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": TRAFFIC_2048.get(PASS_NAMES[dom]) if N == 2048 else None,
-                "algorithmic_bytes_per_launch": PASS_PLANES[dom] * B,
-                "iteration": {"modelled_bytes": sum(PASS_PLANES) * B, "ms_sum_of_passes": iter_ms,
-                              "achieved_gbs": sum(PASS_PLANES) * B / (iter_ms / 1e3) / 1e9},
+                "algorithmic_bytes_per_launch": planes[dom] * B, "band_cols": int(info.band_cols),
+                "iteration": {"modelled_bytes": sum(planes) * B, "ms_sum_of_passes": iter_ms,
+                              "achieved_gbs": sum(planes) * B / (iter_ms / 1e3) / 1e9},
                 "pass_ms": dict(zip(PASS_NAMES, passes))}
 
     # plain-FP32 comparison line (same GPU, same workload)

@@ -102,6 +102,13 @@ typedef struct {
   double flux_c;        /* flux for constraint 1; <= 0 means mean over views of sum_S (g - b) */
   int reduce_fp64;      /* 1: FP64 accumulation of KL / BB / Armijo sums (default); 0: plain FP32 */
   int trace_cap;        /* per-problem iteration records kept on the device (4096) */
+  double band_tol;      /* PSF band (1e-6): spectrum columns kx whose PSF spectrum entries are all
+                         * <= band_tol max|K_hat| (every view) are treated as zero, so the iteration's
+                         * row transforms store and load only the band and the column passes process
+                         * only it -- for band-limited PSFs (diffraction-limited pupils, whose
+                         * optical transfer function vanishes beyond the pupil's autocorrelation)
+                         * a large saving; the dropped entries lie below the FP32 transforms' own
+                         * rounding.  0 keeps every column. */
 } sgp_params;
 
 typedef struct {
@@ -129,6 +136,7 @@ typedef struct {
   double alpha, tau, lambda, rho;
   double nS;             /* |S| (pixels of the detected image) */
   double flux_c;         /* constant start value c of Sect. 3.1 */
+  int band_cols;         /* spectrum columns processed by the iteration (W/2 = all; see band_tol) */
 } sgp_info;
 
 /* Fill *out with the parameter values of Sect. 3.2. */

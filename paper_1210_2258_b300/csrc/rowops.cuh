@@ -164,20 +164,30 @@ __device__ __forceinline__ void block_minmax_store(float mn, float mx, double* o
 }
 
 // ------------------------------------------------------------------------------ row FFT pieces
+// Spectrum rows: only the columns < cb of the PSF band are stored and loaded; the loaded row is
+// zero beyond (the PSF spectrum is zero there, so is every product with it).  cb = W/2: all.
 template <int W>
-__device__ __forceinline__ void row_load(const RowLayout<W / 2>& x, const float2* __restrict__ src, int t, bool act) {
+__device__ __forceinline__ void row_load(const RowLayout<W / 2>& x, const float2* __restrict__ src, int t, bool act,
+                                         int cb) {
   using G = RowGeo<W>;
   if (act) {
 #pragma unroll
-    for (int q = 0; q < G::E; ++q) x(t + q * G::T) = src[t + q * G::T];
+    for (int q = 0; q < G::E; ++q) {
+      const int i = t + q * G::T;
+      x(i) = i < cb ? src[i] : make_float2(0.0f, 0.0f);
+    }
   }
 }
 template <int W>
-__device__ __forceinline__ void row_store(const RowLayout<W / 2>& x, float2* __restrict__ dst, int t, bool act) {
+__device__ __forceinline__ void row_store(const RowLayout<W / 2>& x, float2* __restrict__ dst, int t, bool act,
+                                          int cb) {
   using G = RowGeo<W>;
   if (act) {
 #pragma unroll
-    for (int q = 0; q < G::E; ++q) dst[t + q * G::T] = x(t + q * G::T);
+    for (int q = 0; q < G::E; ++q) {
+      const int i = t + q * G::T;
+      if (i < cb) dst[i] = x(i);
+    }
   }
 }
 
@@ -235,8 +245,9 @@ __device__ __forceinline__ void r2c_post(const RowLayout<W / 2>& x, int t, bool 
 
 // spectrum row (global) -> real values (times M) in shared memory; ends synchronised
 template <int W>
-__device__ __forceinline__ void row_spec_to_real(const RowLayout<W / 2>& x, const float2* src, int t, bool act) {
-  row_load<W>(x, src, t, act);
+__device__ __forceinline__ void row_spec_to_real(const RowLayout<W / 2>& x, const float2* src, int t, bool act,
+                                                 int cb = W / 2) {
+  row_load<W>(x, src, t, act, cb);
   __syncthreads();
   c2r_pre<W>(x, t, act);
   __syncthreads();
@@ -244,12 +255,13 @@ __device__ __forceinline__ void row_spec_to_real(const RowLayout<W / 2>& x, cons
 }
 // real values in shared memory -> spectrum row (global); starts with a barrier
 template <int W>
-__device__ __forceinline__ void row_real_to_spec(const RowLayout<W / 2>& x, float2* dst, int t, bool act) {
+__device__ __forceinline__ void row_real_to_spec(const RowLayout<W / 2>& x, float2* dst, int t, bool act,
+                                                 int cb = W / 2) {
   __syncthreads();
   fft_inplace<W / 2, false>(x, t, act);
   r2c_post<W>(x, t, act);
   __syncthreads();
-  row_store<W>(x, dst, t, act);
+  row_store<W>(x, dst, t, act, cb);
   __syncthreads();
 }
 
@@ -428,7 +440,7 @@ __device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ i
     }
   }
   if (done == 0) {
-    row_real_to_spec<W>(x, spec_plane(d, j + 1) + off, t, act);
+    row_real_to_spec<W>(x, spec_plane(d, j + 1) + off, t, act, d.cb);
     block_sum_store<2, FP64>(acc, partv_of(d, it) + SLOT_KL);
   }
   if (arrive_last(d.ctrl, d.n_rv_items)) ctrl_sgp_begin<FP64>(d);
@@ -459,7 +471,7 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
     const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
-    row_spec_to_real<W>(x, spec_plane(d, 0) + off, t, act);
+    row_spec_to_real<W>(x, spec_plane(d, 0) + off, t, act, d.cb);
     KSum acc[4];
     if (act) {
       const float* f = d.f[ke & 1];
@@ -558,7 +570,7 @@ __device__ __forceinline__ void b_sgp_y(const ImgDesc* __restrict__ imgs,
         }
       }
     }
-    row_real_to_spec<W>(x, spec_plane(d, 0) + off, t, act);
+    row_real_to_spec<W>(x, spec_plane(d, 0) + off, t, act, d.cb);
     block_sum_store<1, FP64>(acc, part_of(d, it) + SLOT_GTD);
   }
 }
@@ -622,7 +634,7 @@ __device__ __forceinline__ void b_sgp_ad_armijo(const ImgDesc* __restrict__ imgs
 #pragma unroll
   for (int l = 1; l < kArmMain; ++l) lam[l] = lam[l - 1] * th;
   KSum acc[kArmMain];
-  row_spec_to_real<W>(x, spec_plane(d, j + 1) + off, t, act);
+  row_spec_to_real<W>(x, spec_plane(d, j + 1) + off, t, act, d.cb);
   if (act) {
     const float* uj = d.u + size_t(j) * d.P;
     float* adj = d.Ad + size_t(j) * d.P;
@@ -730,7 +742,7 @@ __device__ __forceinline__ void b_rl_update(const ImgDesc* __restrict__ imgs,
     const size_t off = size_t(row) * G::M;
     float2* sp = spec_plane(d, 0) + off;
     const bool osem = wview >= 0;
-    if (hv) row_spec_to_real<W>(x, osem ? spec_plane(d, wview + 1) + off : sp, t, act);
+    if (hv) row_spec_to_real<W>(x, osem ? spec_plane(d, wview + 1) + off : sp, t, act, d.cb);
     KSum acc[1];
     if (act) {
       const float* fo = d.f[k & 1];
@@ -755,7 +767,7 @@ __device__ __forceinline__ void b_rl_update(const ImgDesc* __restrict__ imgs,
         x(t + q * G::T) = f;
       }
     }
-    row_real_to_spec<W>(x, sp, t, act);
+    row_real_to_spec<W>(x, sp, t, act, d.cb);
     block_sum_store<1, FP64>(acc, part_of(d, it) + SLOT_RHO);
   }
 }
@@ -788,7 +800,7 @@ __device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
   const size_t off = size_t(row) * G::M;
   KSum acc[1];
   float2* sp = spec_plane(d, j + 1) + off;
-  row_spec_to_real<W>(x, sp, t, act);
+  row_spec_to_real<W>(x, sp, t, act, d.cb);
   if (act) {
     float* uj = d.u + size_t(j) * d.P;
     const float* gj = d.g + size_t(j) * d.P;
@@ -804,7 +816,7 @@ __device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
       x(t + q * G::T) = rm;
     }
   }
-  row_real_to_spec<W>(x, sp, t, act);
+  row_real_to_spec<W>(x, sp, t, act, d.cb);
   if (write_u == 2) {
     if (arrive_last(d.ctrl, d.n_row_items)) osem_tick(d.ctrl, 1);
     return;
@@ -835,7 +847,7 @@ __device__ __forceinline__ void b_rl_step_minmax(const ImgDesc* __restrict__ img
     const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
-    row_spec_to_real<W>(x, spec_plane(d, 0) + off, t, act);
+    row_spec_to_real<W>(x, spec_plane(d, 0) + off, t, act, d.cb);
     float mn = f_inf(), mx = 0.0f;
     if (act) {
       const float* f = d.f[d.ctrl->k & 1];

@@ -129,6 +129,9 @@ struct Layout {
   int2* d_rvo = nullptr;               // row-view list, view-major over the problems (OSEM sub-steps)
   int2* d_colv = nullptr;              // column list with views (1 -> p passes)
   int2* d_colvo = nullptr;             // the same, view-major over the problems (OSEM sub-steps)
+  int2* d_colvb = nullptr;             // column list with views, PSF band only (hot passes)
+  int2* d_colb = nullptr;              // column list (p -> 1), PSF band only (hot passes)
+  int n_colvb = 0, n_colb = 0;
   int2* d_col = nullptr;               // column list (p -> 1 passes)
   int2* d_colk = nullptr;              // column list of the PSF spectrum jobs
   ColJob* d_jobs = nullptr;            // 5 jobs per problem: A, AT, CONJ, A_raw, AT_raw, then p KHAT jobs
@@ -156,6 +159,7 @@ void plan_layout(char* base, int n, const sgp_shape* sh, int trace_cap, const bo
     d.H = H; d.W = W; d.p = p; d.boundary = sh[i].has_mask ? 1 : 0; d.P = P;
     const int rpi = rows_per_item(W), cpi = cols_per_item(H), M = W / 2;
     d.rpi = rpi;
+    d.cb = M;
     const int nr = (H + rpi - 1) / rpi, nc = (M + cpi - 1) / cpi;
     const int ncap = (H + rows_min(W) - 1) / rows_min(W);   // item capacity for the smallest tile
     d.row_item0 = 0; d.n_row_items = nr;      // indices within the problem's own range
@@ -188,6 +192,8 @@ void plan_layout(char* base, int n, const sgp_shape* sh, int trace_cap, const bo
   L.d_rvo = cv.take<int2>(L.cap_rv);
   L.d_colv = cv.take<int2>(L.n_colv);
   L.d_colvo = cv.take<int2>(L.n_colv);
+  L.d_colvb = cv.take<int2>(L.n_colv);
+  L.d_colb = cv.take<int2>(L.n_col);
   L.d_col = cv.take<int2>(L.n_col);
   L.d_colk = cv.take<int2>(L.n_colk);
   int nj = 0;
@@ -344,10 +350,12 @@ sgp_status col_pass(sgp_ctx* c, int variant, int job_off, int image = -1) {
     smem = g_reg.col_multi_smem;
   }
   const bool views = variant != COL_PTO1;
-  const int2* items = views ? c->L.d_colv : c->L.d_col;
-  int n = views ? c->L.n_colv : c->L.n_col;
+  // the iteration's passes (image < 0) run over the PSF band only; a single problem's set-up and
+  // operator passes (image >= 0) over every column
+  const int2* items = views ? c->L.d_colvb : c->L.d_colb;
+  int n = views ? c->L.n_colvb : c->L.n_colb;
   if (image >= 0) {
-    items += views ? c->colv_begin[image] : c->col_begin[image];
+    items = (views ? c->L.d_colv : c->L.d_col) + (views ? c->colv_begin[image] : c->col_begin[image]);
     n = views ? c->colv_count[image] : c->col_count[image];
   }
   // the job index of an item is the problem index; job_off picks the job kind
@@ -450,12 +458,65 @@ sgp_status osem_row(sgp_ctx* c, RowOp op, int j, int extra) {
 }
 sgp_status osem_col(sgp_ctx* c, int variant, int job_off, int j) {
   const int si = side_index(c->H);
-  const int2* items = c->L.d_colvo + size_t(j) * c->L.n_col;
-  int n = c->L.n_col;
+  const int2* items = c->L.d_colvo + size_t(j) * c->L.n_colb;
+  int n = c->L.n_colb;
   const ColJob* jobs = c->L.d_jobs + job_off;
   void* a[] = {(void*)&jobs, (void*)&items, (void*)&n};
   return launch_pdl(g_reg.col[variant][si], n, kColBlock, g_reg.col_smem[si], c->s, a);
 }
+// PSF band of every problem (after the PSF spectra): cb = 1 + the last spectrum column whose
+// entries exceed tol max|K_hat| in some view, rounded up to the column tile; then the column lists
+// of the iteration's passes (image < 0) over the band, and the descriptors with cb.
+sgp_status set_band(sgp_ctx* c, double tol) {
+  Layout& L = c->L;
+  std::vector<float> cm;
+  for (int i = 0; i < c->n; ++i) {
+    ImgDesc& d = L.d[i];
+    const int M = d.W / 2, cpi = cols_per_item(d.H);
+    int cb = M;
+    if (tol > 0.0) {
+      const float2* kh = reinterpret_cast<const float2*>(L.khat[i]);
+      int Hh = d.H, Mm = M, p = d.p;
+      float* out = d.u;   // scratch (the iteration state is set later)
+      void* a[] = {(void*)&kh, (void*)&Hh, (void*)&Mm, (void*)&p, (void*)&out};
+      sgp_status st = launch((const void*)&k_khat_colmax, std::max(1, std::min(148, (M + 127) / 128)), 128, 0, c->s, a);
+      if (st) return st;
+      cm.resize(M);
+      CU(cudaMemcpyAsync(cm.data(), out, sizeof(float) * M, cudaMemcpyDeviceToHost, c->s));
+      CU(cudaStreamSynchronize(c->s));
+      float mx = 0.0f;
+      for (float v : cm) mx = std::max(mx, v);
+      int last = 0;
+      for (int col = 0; col < M; ++col)
+        if (cm[col] > float(tol) * mx) last = col;
+      cb = std::min(M, ((last + 1 + cpi - 1) / cpi) * cpi);
+    }
+    d.cb = cb;
+  }
+  std::vector<int2> vb, b;
+  c->colvo.clear();
+  for (int i : c->order) {
+    const ImgDesc& d = L.d[i];
+    const int cpi = cols_per_item(d.H);
+    for (int j = 0; j < d.p; ++j)
+      for (int x = 0; x < d.cb; x += cpi) vb.push_back(make_int2(i, x | (j << 16)));
+    for (int x = 0; x < d.cb; x += cpi) b.push_back(make_int2(i, x));
+  }
+  if (!c->mixed)   // view-major column list of the OSEM sub-steps
+    for (int j = 0; j < c->p; ++j)
+      for (int i : c->order)
+        for (int x = 0; x < L.d[i].cb; x += cols_per_item(L.d[i].H)) c->colvo.push_back(make_int2(i, x | (j << 16)));
+  L.n_colvb = int(vb.size());
+  L.n_colb = int(b.size());
+  CU(cudaMemcpyAsync(L.d_colvb, vb.data(), sizeof(int2) * vb.size(), cudaMemcpyHostToDevice, c->s));
+  CU(cudaMemcpyAsync(L.d_colb, b.data(), sizeof(int2) * b.size(), cudaMemcpyHostToDevice, c->s));
+  if (!c->colvo.empty())
+    CU(cudaMemcpyAsync(L.d_colvo, c->colvo.data(), sizeof(int2) * c->colvo.size(), cudaMemcpyHostToDevice, c->s));
+  CU(cudaMemcpyAsync(L.d_imgs, L.d.data(), sizeof(ImgDesc) * c->n, cudaMemcpyHostToDevice, c->s));
+  CU(cudaStreamSynchronize(c->s));
+  return SGP_OK;
+}
+
 sgp_status seq_osem_iteration(sgp_ctx* c) {
   sgp_status st;
   for (int j = 0; j < c->p; ++j) {
@@ -868,6 +929,7 @@ void sgp_params_default(sgp_params* o) {
   o->alpha_min = 1e-5; o->alpha_max = 1e5; o->M_alpha = 3; o->warmup_iters = 20;
   o->adaptive_L = 1; o->max_backtracks = 30; o->L1 = 1e-10; o->L2 = 1e10; o->sigma_R = 1e-2;
   o->constraint = 0; o->flux_c = 0.0; o->reduce_fp64 = 1; o->trace_cap = 4096;
+  o->band_tol = 1e-6;
 }
 
 const char* sgp_last_error(void) { return g_err.c_str(); }
@@ -978,10 +1040,6 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
     for (int j = 0; j < kMaxViews; ++j) d.bs[j] = j < d.p ? in[i].b_const[j] : 0.0f;
     d.ftrue = nullptr;
   }
-  if (!c->mixed)   // view-major column list of the OSEM sub-steps
-    for (int j = 0; j < c->p; ++j)
-      for (int i : order)
-        for (int x = 0; x < L.d[i].W / 2; x += cols_per_item(L.d[i].H)) c->colvo.push_back(make_int2(i, x | (j << 16)));
   // column jobs: kinds A, AT, CONJ, A_raw, AT_raw (index kind*n + i), then p KHAT jobs per problem
   c->jobs.assign(L.n_jobs, ColJob{});
   int kh = 5 * n;
@@ -1061,8 +1119,6 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
   if (st) return bail(st);
   if (cudaMemcpyAsync(L.d_jobs, c->jobs.data(), sizeof(ColJob) * L.n_jobs, cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
       cudaMemcpyAsync(L.d_colv, c->colv.data(), sizeof(int2) * c->colv.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
-      (!c->colvo.empty() &&
-       cudaMemcpyAsync(L.d_colvo, c->colvo.data(), sizeof(int2) * c->colvo.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess) ||
       cudaMemcpyAsync(L.d_col, c->col.data(), sizeof(int2) * c->col.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess ||
       cudaMemcpyAsync(L.d_colk, c->colk.data(), sizeof(int2) * c->colk.size(), cudaMemcpyHostToDevice, c->s) != cudaSuccess)
     return bail(fail(SGP_ERR_CUDA, "descriptor upload failed"));
@@ -1075,6 +1131,7 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
     void* a[] = {(void*)&jobs, (void*)&items, (void*)&nk};
     if ((st = launch(g_reg.col[COL_KHAT][si], nk, kColBlock, g_reg.col_smem[si], c->s, a))) return bail(st);
   }
+  if ((st = set_band(c, P.band_tol))) return bail(st);
   for (int i = 0; i < n; ++i) {
     ImgDesc& d = L.d[i];
     if (in[i].b && cudaMemcpyAsync(L.bcopy[i], in[i].b, sizeof(float) * d.P * d.p, cudaMemcpyDeviceToDevice, c->s) != cudaSuccess)
@@ -1304,6 +1361,7 @@ sgp_status sgp_get_info(sgp_ctx* c, int image, sgp_info* o) {
   o->L1 = h.L1; o->L2 = h.L2; o->alpha = h.alpha; o->tau = h.tau; o->lambda = h.lambda; o->rho = h.rho;
   o->nS = c->nS[image];
   o->flux_c = c->c_const[image];
+  o->band_cols = c->L.d[image].cb;
   return leave(c);
 }
 

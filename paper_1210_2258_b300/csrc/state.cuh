@@ -92,6 +92,8 @@ struct ImgDesc {
   int row_item0, n_row_items;   // this problem's items in the row-item list (image, row0)
   int rv_item0, n_rv_items;     // ... and in the row-view list (image, row0 | view << 16)
   int rpi;                      // image rows per row item
+  int cb;                       // spectrum columns in the PSF band (<= W/2): the hot row passes store
+                                // and load only columns < cb, the others are zero (band-limited PSF)
   float w_scalar;               // periodic: 1/p (RL factor, SGP scaling factor)
   float a1_scalar;              // periodic: p (= sum_j A_j^T 1)
   float bs[kMaxViews];          // constant backgrounds (used when b == nullptr)
