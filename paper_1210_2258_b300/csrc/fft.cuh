@@ -190,7 +190,7 @@ SGP_PLAN(512, 16, 16, 16, 2)
 SGP_PLAN(768, 24, 8, 8, 12)
 SGP_PLAN(1024, 16, 16, 16, 4)
 SGP_PLAN(1536, 24, 8, 8, 24)
-SGP_PLAN(2048, 16, 16, 16, 8)
+SGP_PLAN(2048, 8, 8, 8, 8, 4)     // column transforms only (rows of 2048 reals use length 1024)
 #undef SGP_PLAN
 
 // ------------------------------------------------------------------------------ layouts

@@ -61,3 +61,17 @@ def test_banded_landed_discrepancy_stop(gpu, galaxy256):
         Js.append(info.J)
     for J in Js:
         assert abs(J - ref.J) <= 3e-5 * ref.J, (Js, ref.J)
+
+
+def test_full_size_banded_sgp(gpu):
+    """The benchmark's 2048^2 galaxy workload in the configuration the benchmark times (PSF band,
+    tuned row tile, 2048-point column plan): five SGP iterations against the FP64 oracle."""
+    sc = scenes.galaxy_scene(seed=0, N=2048)
+    orc = oracle_problem(sc)
+    ref = O.sgp(orc, stop=O.StopRule("fixed", max_iter=5))
+    prob = gpu_problem(gpu, sc)
+    prob.sgp_iterate(5)
+    info = prob.info()
+    assert info.band_cols == 258          # |kx| <= 256: 257 columns, rounded up to the 2-column tile
+    assert abs(info.J - ref.J) <= 1e-5 * ref.J, (info.J, ref.J)
+    assert rel_l2(host(prob.get_f()), ref.f) <= 1e-3
