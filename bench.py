@@ -45,9 +45,11 @@ PASS_SPEC = [1, 3, 1, 1, 3, 1, 0]
 PASS_PLANES = [a + b for a, b in zip(PASS_PIX, PASS_SPEC)]   # without a band: 26 planes
 # DRAM bytes per launch of each pass at 2048^2 (ncu dram__bytes_read.sum + dram__bytes_write.sum,
 # caches flushed before the launch, second SGP iteration of `python bench.py --profile 8`), taken on
-# the kernels of this tree.  A pass's writes are still in L2 when its launch ends, so the figures
-# are its reads; they equal the algorithmic reads (no tile is read twice).
-TRAFFIC_2048 = {}
+# the kernels of this tree, PSF band of the Airy PSF in use (258 of 1024 spectrum columns).  A pass's
+# writes are mostly still in L2 when its launch ends, so the figures are mostly its reads; they
+# equal the algorithmic reads (no tile is read twice).
+TRAFFIC_2048 = {"update_ratio": 93.07e6, "col_AT": 8.98e6, "grad_bb": 55.21e6, "proj_y": 33.60e6,
+                "col_A": 8.98e6, "ad_armijo": 38.24e6, "armijo_extra": 0.07e6}
 
 
 def parse():

@@ -355,17 +355,20 @@ __global__ void k_loop_cond(const ImgDesc* __restrict__ imgs, int n, cudaGraphCo
   }
 }
 
-// PSF band: out[c] = max over views j and rows r of max(|Re|, |Im|) of the PSF spectrum column c
+// PSF band: out[c] = max over views j and rows r of max(|Re|, |Im|) of the PSF spectrum column c.
+// Block (x, y) covers columns x * blockDim.x .. and the rows y, y + gridDim.y, ..; the partial
+// maxima meet in out (zeroed by the caller) by an integer atomicMax, which orders non-negative
+// floats like their bit patterns.
 __global__ void k_khat_colmax(const float2* __restrict__ khat, int H, int M, int p, float* __restrict__ out) {
-  for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < M; col += gridDim.x * blockDim.x) {
-    float m = 0.0f;
-    for (int j = 0; j < p; ++j)
-      for (int r = 0; r < H; ++r) {
-        const float2 v = khat[(size_t(j) * H + r) * M + col];
-        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
-      }
-    out[col] = m;
-  }
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= M) return;
+  float m = 0.0f;
+  for (int j = 0; j < p; ++j)
+    for (int r = blockIdx.y; r < H; r += gridDim.y) {
+      const float2 v = khat[(size_t(j) * H + r) * M + col];
+      m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+  atomicMax(reinterpret_cast<int*>(out) + col, __float_as_int(m));
 }
 
 // OSEM: count the pending update of every problem (after the last sub-step of a call)

@@ -479,8 +479,9 @@ sgp_status set_band(sgp_ctx* c, double tol) {
       int Hh = d.H, Mm = M, p = d.p;
       float* out = d.u;   // scratch (the iteration state is set later)
       void* a[] = {(void*)&kh, (void*)&Hh, (void*)&Mm, (void*)&p, (void*)&out};
-      sgp_status st = launch((const void*)&k_khat_colmax, std::max(1, std::min(148, (M + 127) / 128)), 128, 0, c->s, a);
-      if (st) return st;
+      CU(cudaMemsetAsync(out, 0, sizeof(float) * M, c->s));
+      CU(cudaLaunchKernel((const void*)&k_khat_colmax, dim3((M + 127) / 128, std::min(d.H, 64)), dim3(128), a, 0, c->s));
+      ++c->launches;
       cm.resize(M);
       CU(cudaMemcpyAsync(cm.data(), out, sizeof(float) * M, cudaMemcpyDeviceToHost, c->s));
       CU(cudaStreamSynchronize(c->s));
