@@ -26,7 +26,7 @@ namespace sgp {
 
 
 template <int H> struct ColGeo {
-  using P = Plan<H>;
+  using P = ColPlan<H>;
   static constexpr int T = P::T, E = P::E;
   static constexpr int C = kColBlock / T;
   static constexpr int ROWSP = col_rows_padded<H>();
@@ -35,7 +35,7 @@ template <int H> struct ColGeo {
 
 template <int H, int C>
 __device__ __forceinline__ void col_load(const ColLayout<C>& x, const float2* __restrict__ src, int M, int t, bool act) {
-  constexpr int T = Plan<H>::T, E = Plan<H>::E;
+  constexpr int T = ColPlan<H>::T, E = ColPlan<H>::E;
   if (act) {
 #pragma unroll
     for (int q = 0; q < E; ++q) {
@@ -81,7 +81,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
     if (MODE == COL_KHAT) {
       col_load<H, C>(x, jb.in + col, M, t, act);
       __syncthreads();
-      fft_inplace<H, false>(x, t, act);
+      fft_inplace<H, false, ColLayout<C>, ColPlan<H>>(x, t, act);
       if (act) {
         float2 outv[E], qv[E];
         const float s = jb.scale;
@@ -123,7 +123,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
         const int j = item.y >> 16;
         col_load<H, C>(x, jb.in + (MODE == COL_PTOV ? size_t(j) * jb.plane_stride : size_t(0)) + col, M, t, act);
         __syncthreads();
-        fft_inplace<H, false>(x, t, act);
+        fft_inplace<H, false, ColLayout<C>, ColPlan<H>>(x, t, act);
         float2 v[E];
         if (act) {
           const float2* kh = jb.khat + size_t(j) * jb.plane_stride;
@@ -140,7 +140,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
           for (int q = 0; q < E; ++q) x(t + q * T) = v[q];
         }
         __syncthreads();
-        fft_inplace<H, true>(x, t, act);
+        fft_inplace<H, true, ColLayout<C>, ColPlan<H>>(x, t, act);
         if (act) {
           float2* dst = jb.out + size_t(MODE == COL_PTOV ? j + 1 : j) * jb.plane_stride + col;
 #pragma unroll
@@ -154,7 +154,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
     } else if (NV == 1) {  // COL_PTO1, one view: the product goes straight back to x
       col_load<H, C>(x, jb.in + col, M, t, act);
       __syncthreads();
-      fft_inplace<H, false>(x, t, act);
+      fft_inplace<H, false, ColLayout<C>, ColPlan<H>>(x, t, act);
       float2 v[E];
       if (act) {
 #pragma unroll
@@ -169,7 +169,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
         for (int q = 0; q < E; ++q) x(t + q * T) = v[q];
       }
       __syncthreads();
-      fft_inplace<H, true>(x, t, act);
+      fft_inplace<H, true, ColLayout<C>, ColPlan<H>>(x, t, act);
       if (act) {
         float2* dst = jb.out + col;
 #pragma unroll
@@ -187,7 +187,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
       for (int j = 0; j < nin; ++j) {
         col_load<H, C>(x, jb.in + size_t(j) * jb.plane_stride + col, M, t, act);
         __syncthreads();
-        fft_inplace<H, false>(x, t, act);
+        fft_inplace<H, false, ColLayout<C>, ColPlan<H>>(x, t, act);
         if (act) {
           const float2* kh = jb.khat + size_t(j) * jb.plane_stride;
           const float2* kq = jb.khatq + size_t(j) * H;
@@ -208,7 +208,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
         }
       }
       __syncthreads();
-      fft_inplace<H, true>(x, t, act);
+      fft_inplace<H, true, ColLayout<C>, ColPlan<H>>(x, t, act);
       if (act) {
         float2* dst = jb.out + col;
 #pragma unroll

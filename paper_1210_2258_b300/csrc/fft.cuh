@@ -193,6 +193,16 @@ SGP_PLAN(1536, 24, 8, 8, 24)
 SGP_PLAN(2048, 8, 8, 8, 8, 4)     // column transforms only (rows of 2048 reals use length 1024)
 #undef SGP_PLAN
 
+// Column transforms may use their own plan: fewer values per thread give more threads per column,
+// fewer columns per block and so more blocks when the PSF band leaves few column tiles (rows of
+// 2W reals keep Plan<W>, which measured faster with 16 values per thread).
+template <int L> struct ColPlan : Plan<L> {};
+template <> struct ColPlan<1024> {
+  static constexpr int L = 1024, E = 8, T = 128;
+  using Fwd = RL<8, 8, 8, 2>;
+  using Inv = typename Rev<Fwd>::type;
+};
+
 // ------------------------------------------------------------------------------ layouts
 // Row layout: element i of a row at base[i + (i >> 4)] (one pad slot per 16 elements keeps the
 // stride-R writes of the first stage free of bank conflicts).
@@ -259,10 +269,9 @@ __device__ __forceinline__ void run_stages(const Lay& x, int t, bool act, RL<R, 
   run_stages<L, T, INV, NS * R>(x, t, act, RL<Rest...>{});
 }
 
-// In-place complex FFT of length L (unnormalised), natural order in and out.
-template <int L, bool INV, class Lay>
+// In-place complex FFT of length L (unnormalised), natural order in and out, by the plan P.
+template <int L, bool INV, class Lay, class P = Plan<L>>
 __device__ __forceinline__ void fft_inplace(const Lay& x, int t, bool act) {
-  using P = Plan<L>;
   if (INV) run_stages<L, P::T, true, 1>(x, t, act, typename P::Inv{});
   else     run_stages<L, P::T, false, 1>(x, t, act, typename P::Fwd{});
 }
