@@ -25,17 +25,17 @@
 namespace sgp {
 
 
-template <int H> struct ColGeo {
-  using P = ColPlan<H>;
+template <int H, bool NARROW = false> struct ColGeo {
+  using P = typename std::conditional<NARROW, ColPlanNarrow<H>, ColPlan<H>>::type;
   static constexpr int T = P::T, E = P::E;
   static constexpr int C = kColBlock / T;
   static constexpr int ROWSP = col_rows_padded<H>();
   static constexpr size_t SMEM = size_t(C) * ROWSP * sizeof(float2);
 };
 
-template <int H, int C>
+template <class P, int C>
 __device__ __forceinline__ void col_load(const ColLayout<C>& x, const float2* __restrict__ src, int M, int t, bool act) {
-  constexpr int T = ColPlan<H>::T, E = ColPlan<H>::E;
+  constexpr int T = P::T, E = P::E;
   if (act) {
 #pragma unroll
     for (int q = 0; q < E; ++q) {
@@ -61,10 +61,11 @@ __device__ __forceinline__ float2 col_product(const ColLayout<C>& x, int i, int 
 // MODE as above; NV = number of views summed by COL_PTO1 (0: any number, runtime loop).
 // One block per item (job, col0 | view << 16): runtime loops around the transforms make the
 // register allocator keep every stage's addresses live, so views are separate items where possible.
-template <int H, int MODE, int NV = 0>
+template <int H, int MODE, int NV = 0, bool NARROW = false>
 __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int2* __restrict__ items, int n_items) {
   pdl_enter();
-  using G = ColGeo<H>;
+  using G = ColGeo<H, NARROW>;
+  using CP = typename G::P;
   constexpr int C = G::C, T = G::T, E = G::E;
   extern __shared__ float2 smem[];
   const int c = threadIdx.x % C, t = threadIdx.x / C;
@@ -79,9 +80,9 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
     const int col = (item.y & 0xffff) + c;
     const bool act = col < M;
     if (MODE == COL_KHAT) {
-      col_load<H, C>(x, jb.in + col, M, t, act);
+      col_load<CP, C>(x, jb.in + col, M, t, act);
       __syncthreads();
-      fft_inplace<H, false, ColLayout<C>, ColPlan<H>>(x, t, act);
+      fft_inplace<H, false, ColLayout<C>, CP>(x, t, act);
       if (act) {
         float2 outv[E], qv[E];
         const float s = jb.scale;
@@ -121,9 +122,9 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
       constexpr bool CJ = MODE != COL_1TOP;
       {
         const int j = item.y >> 16;
-        col_load<H, C>(x, jb.in + (MODE == COL_PTOV ? size_t(j) * jb.plane_stride : size_t(0)) + col, M, t, act);
+        col_load<CP, C>(x, jb.in + (MODE == COL_PTOV ? size_t(j) * jb.plane_stride : size_t(0)) + col, M, t, act);
         __syncthreads();
-        fft_inplace<H, false, ColLayout<C>, ColPlan<H>>(x, t, act);
+        fft_inplace<H, false, ColLayout<C>, CP>(x, t, act);
         float2 v[E];
         if (act) {
           const float2* kh = jb.khat + size_t(j) * jb.plane_stride;
@@ -140,7 +141,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
           for (int q = 0; q < E; ++q) x(t + q * T) = v[q];
         }
         __syncthreads();
-        fft_inplace<H, true, ColLayout<C>, ColPlan<H>>(x, t, act);
+        fft_inplace<H, true, ColLayout<C>, CP>(x, t, act);
         if (act) {
           float2* dst = jb.out + size_t(MODE == COL_PTOV ? j + 1 : j) * jb.plane_stride + col;
 #pragma unroll
@@ -152,9 +153,9 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
         __syncthreads();
       }
     } else if (NV == 1) {  // COL_PTO1, one view: the product goes straight back to x
-      col_load<H, C>(x, jb.in + col, M, t, act);
+      col_load<CP, C>(x, jb.in + col, M, t, act);
       __syncthreads();
-      fft_inplace<H, false, ColLayout<C>, ColPlan<H>>(x, t, act);
+      fft_inplace<H, false, ColLayout<C>, CP>(x, t, act);
       float2 v[E];
       if (act) {
 #pragma unroll
@@ -169,7 +170,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
         for (int q = 0; q < E; ++q) x(t + q * T) = v[q];
       }
       __syncthreads();
-      fft_inplace<H, true, ColLayout<C>, ColPlan<H>>(x, t, act);
+      fft_inplace<H, true, ColLayout<C>, CP>(x, t, act);
       if (act) {
         float2* dst = jb.out + col;
 #pragma unroll
@@ -185,9 +186,9 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
       float2* o = jb.out + col;
 #pragma unroll 1
       for (int j = 0; j < nin; ++j) {
-        col_load<H, C>(x, jb.in + size_t(j) * jb.plane_stride + col, M, t, act);
+        col_load<CP, C>(x, jb.in + size_t(j) * jb.plane_stride + col, M, t, act);
         __syncthreads();
-        fft_inplace<H, false, ColLayout<C>, ColPlan<H>>(x, t, act);
+        fft_inplace<H, false, ColLayout<C>, CP>(x, t, act);
         if (act) {
           const float2* kh = jb.khat + size_t(j) * jb.plane_stride;
           const float2* kq = jb.khatq + size_t(j) * H;
@@ -208,7 +209,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
         }
       }
       __syncthreads();
-      fft_inplace<H, true, ColLayout<C>, ColPlan<H>>(x, t, act);
+      fft_inplace<H, true, ColLayout<C>, CP>(x, t, act);
       if (act) {
         float2* dst = jb.out + col;
 #pragma unroll
@@ -222,10 +223,10 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
   }
 }
 
-template <int H, int MODE, int NV = 0>
+template <int H, int MODE, int NV = 0, bool NARROW = false>
 __global__ void __launch_bounds__(kColBlock) k_col(const ColJob* __restrict__ jobs, const int2* __restrict__ items,
                                                   int n_items) {
-  b_col<H, MODE, NV>(jobs, items, n_items);
+  b_col<H, MODE, NV, NARROW>(jobs, items, n_items);
 
 }
 

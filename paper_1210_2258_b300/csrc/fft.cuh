@@ -190,18 +190,28 @@ SGP_PLAN(512, 16, 16, 16, 2)
 SGP_PLAN(768, 24, 8, 8, 12)
 SGP_PLAN(1024, 16, 16, 16, 4)
 SGP_PLAN(1536, 24, 8, 8, 24)
-SGP_PLAN(2048, 8, 8, 8, 8, 4)     // column transforms only (rows of 2048 reals use length 1024)
+SGP_PLAN(2048, 16, 16, 16, 8)
 #undef SGP_PLAN
 
 // Column transforms may use their own plan: fewer values per thread give more threads per column,
 // fewer columns per block and so more blocks when the PSF band leaves few column tiles (rows of
-// 2W reals keep Plan<W>, which measured faster with 16 values per thread).
+// 2W reals keep Plan<W>, which measured faster with 16 values per thread).  Length 2048 has two
+// column plans: ColPlan (16 values, 4 columns per block: faster over all columns) and
+// ColPlanNarrow (8 values, 2 columns per block: faster when the band leaves half the columns or
+// fewer); a context picks one at set-up.
 template <int L> struct ColPlan : Plan<L> {};
 template <> struct ColPlan<1024> {
   static constexpr int L = 1024, E = 8, T = 128;
   using Fwd = RL<8, 8, 8, 2>;
   using Inv = typename Rev<Fwd>::type;
 };
+template <int L> struct ColPlanNarrow : ColPlan<L> {};
+template <> struct ColPlanNarrow<2048> {
+  static constexpr int L = 2048, E = 8, T = 256;
+  using Fwd = RL<8, 8, 8, 4>;
+  using Inv = typename Rev<Fwd>::type;
+};
+constexpr int kNarrowSide = 2048;   // the one length with a narrow column variant
 
 // ------------------------------------------------------------------------------ layouts
 // Row layout: element i of a row at base[i + (i >> 4)] (one pad slot per 16 elements keeps the

@@ -35,6 +35,16 @@ void register_side(Registry& R) {
   R.row_rows[s] = RowGeo<N>::ROWS;
   R.col_smem[s] = ColGeo<N>::SMEM;
   R.col_cols[s] = ColGeo<N>::C;
+  if constexpr (N == kNarrowSide) {   // the narrow column variant (ColPlanNarrow)
+    R.col_narrow[COL_KHAT] = reinterpret_cast<const void*>(&k_col<N, COL_KHAT, 0, true>);
+    R.col_narrow[COL_1TOP] = reinterpret_cast<const void*>(&k_col<N, COL_1TOP, 0, true>);
+    R.col_narrow[COL_1TOP_CONJ] = reinterpret_cast<const void*>(&k_col<N, COL_1TOP_CONJ, 0, true>);
+    R.col_narrow[COL_PTO1] = reinterpret_cast<const void*>(&k_col<N, COL_PTO1, 0, true>);
+    R.col_narrow[COL_PTOV] = reinterpret_cast<const void*>(&k_col<N, COL_PTOV, 0, true>);
+    R.col_narrow[kColPto1P1] = reinterpret_cast<const void*>(&k_col<N, COL_PTO1, 1, true>);
+    R.col_narrow_smem = ColGeo<N, true>::SMEM;
+    R.col_narrow_cols = ColGeo<N, true>::C;
+  }
 }
 
 }  // namespace sgp

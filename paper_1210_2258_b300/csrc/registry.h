@@ -28,6 +28,10 @@ struct Registry {
   const void* col[kColModes][kNumSides];      // [variant][side]
   size_t row_smem[kNumSides], col_smem[kNumSides];
   int row_rows[kNumSides], col_cols[kNumSides];
+  // narrow column variant of the one side that has it (kNarrowSide): [variant]
+  const void* col_narrow[kColModes];
+  size_t col_narrow_smem;
+  int col_narrow_cols;
   cudaError_t (*twiddle_init[kTwiddleUnits])(const float2*);
   // multi-size kernels (one launch covers problems of different sides): row ops, and the column
   // passes 1 -> p (index 0), p -> 1 for any p (index 1) and for p = 1 (index 2); dynamic shared

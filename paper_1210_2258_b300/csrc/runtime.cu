@@ -93,6 +93,9 @@ sgp_status ensure_device_ready(int dev) {
       CU(cudaFuncSetAttribute(g_reg.col[m][s], cudaFuncAttributeMaxDynamicSharedMemorySize,
                               int(g_reg.col_smem[s])));
   }
+  for (int m = 0; m < kColModes; ++m)
+    CU(cudaFuncSetAttribute(g_reg.col_narrow[m], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            int(g_reg.col_narrow_smem)));
   g_dev_ready[dev] = true;
   return SGP_OK;
 }
@@ -243,6 +246,7 @@ struct sgp_ctx {
   cudaGraphConditionalHandle hl_sgp = 0, hl_rl = 0, hl_land = 0;
   int graph_units = 8;
   int loop_cap = 0;                // iteration cap captured in the solve loop graphs
+  bool col_narrow = false;         // the iteration's column passes use the narrow variant (set_band)
   long long launches = 0;          // kernels enqueued (graph nodes counted per graph launch)
   CtrlState* h_ctrl = nullptr;     // pinned mirror of the controller array (2 slots for polling)
 };
@@ -348,6 +352,9 @@ sgp_status col_pass(sgp_ctx* c, int variant, int job_off, int image = -1) {
   if (c->mixed && image < 0) {
     fn = variant == COL_PTO1 ? g_reg.col_multi[c->p == 1 ? 2 : 1] : g_reg.col_multi[0];
     smem = g_reg.col_multi_smem;
+  } else if (c->col_narrow && image < 0) {
+    fn = g_reg.col_narrow[v];
+    smem = g_reg.col_narrow_smem;
   }
   const bool views = variant != COL_PTO1;
   // the iteration's passes (image < 0) run over the PSF band only; a single problem's set-up and
@@ -462,6 +469,7 @@ sgp_status osem_col(sgp_ctx* c, int variant, int job_off, int j) {
   int n = c->L.n_colb;
   const ColJob* jobs = c->L.d_jobs + job_off;
   void* a[] = {(void*)&jobs, (void*)&items, (void*)&n};
+  if (c->col_narrow) return launch_pdl(g_reg.col_narrow[variant], n, kColBlock, g_reg.col_narrow_smem, c->s, a);
   return launch_pdl(g_reg.col[variant][si], n, kColBlock, g_reg.col_smem[si], c->s, a);
 }
 // PSF band of every problem (after the PSF spectra): cb = 1 + the last spectrum column whose
@@ -470,9 +478,10 @@ sgp_status osem_col(sgp_ctx* c, int variant, int job_off, int j) {
 sgp_status set_band(sgp_ctx* c, double tol) {
   Layout& L = c->L;
   std::vector<float> cm;
+  std::vector<int> raw(c->n);   // columns in the band before rounding to a column tile
   for (int i = 0; i < c->n; ++i) {
     ImgDesc& d = L.d[i];
-    const int M = d.W / 2, cpi = cols_per_item(d.H);
+    const int M = d.W / 2;
     int cb = M;
     if (tol > 0.0) {
       const float2* kh = reinterpret_cast<const float2*>(L.khat[i]);
@@ -490,15 +499,26 @@ sgp_status set_band(sgp_ctx* c, double tol) {
       int last = 0;
       for (int col = 0; col < M; ++col)
         if (cm[col] > float(tol) * mx) last = col;
-      cb = std::min(M, ((last + 1 + cpi - 1) / cpi) * cpi);
+      cb = last + 1;
     }
-    d.cb = cb;
+    raw[i] = cb;
+  }
+  // a uniform context of the side with a narrow column variant uses it when every problem's band
+  // keeps half the columns or fewer (more, narrower column tiles)
+  c->col_narrow = !c->mixed && c->H == kNarrowSide;
+  for (int i = 0; i < c->n; ++i) c->col_narrow = c->col_narrow && raw[i] * 2 <= L.d[i].W / 2;
+  const int cpi_n = g_reg.col_narrow_cols;
+  auto tile_of = [&](const ImgDesc& d) { return c->col_narrow ? cpi_n : cols_per_item(d.H); };
+  for (int i = 0; i < c->n; ++i) {   // the band rounded up to whole column tiles
+    ImgDesc& d = L.d[i];
+    const int cpi = tile_of(d);
+    d.cb = std::min(d.W / 2, ((raw[i] + cpi - 1) / cpi) * cpi);
   }
   std::vector<int2> vb, b;
   c->colvo.clear();
   for (int i : c->order) {
     const ImgDesc& d = L.d[i];
-    const int cpi = cols_per_item(d.H);
+    const int cpi = tile_of(d);
     for (int j = 0; j < d.p; ++j)
       for (int x = 0; x < d.cb; x += cpi) vb.push_back(make_int2(i, x | (j << 16)));
     for (int x = 0; x < d.cb; x += cpi) b.push_back(make_int2(i, x));
@@ -506,7 +526,7 @@ sgp_status set_band(sgp_ctx* c, double tol) {
   if (!c->mixed)   // view-major column list of the OSEM sub-steps
     for (int j = 0; j < c->p; ++j)
       for (int i : c->order)
-        for (int x = 0; x < L.d[i].cb; x += cols_per_item(L.d[i].H)) c->colvo.push_back(make_int2(i, x | (j << 16)));
+        for (int x = 0; x < L.d[i].cb; x += tile_of(L.d[i])) c->colvo.push_back(make_int2(i, x | (j << 16)));
   L.n_colvb = int(vb.size());
   L.n_colb = int(b.size());
   CU(cudaMemcpyAsync(L.d_colvb, vb.data(), sizeof(int2) * vb.size(), cudaMemcpyHostToDevice, c->s));
