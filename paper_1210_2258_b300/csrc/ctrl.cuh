@@ -250,17 +250,22 @@ __global__ void __launch_bounds__(256) k_stats_partial(const float* __restrict__
   const float* a = x + size_t(plane) * P;
   const float* bj = b ? b + size_t(plane) * P : nullptr;
   const float bc = bconst ? bconst[plane] : 0.0f;
-  double s0 = 0.0, s1 = mode ? 0.0 : -INFINITY, s2 = mode ? 0.0 : INFINITY, s3 = 0.0;
+  // per thread: compensated FP32 sums (FP64 arithmetic is slow on this GPU) and FP32 max / min /
+  // counts (exact: a thread sees fewer than 2^24 pixels); FP64 from the block level up
+  KSum k0, k1;
+  float m1 = mode ? 0.0f : -INFINITY, m2 = mode ? 0.0f : INFINITY, n2 = 0.0f, n3 = 0.0f;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < P; i += size_t(gridDim.x) * blockDim.x) {
     const float v = a[i];
     if (mode == 0) {
-      if (!isfinite(v)) { s3 += 1.0; continue; }
-      s0 += v; s1 = fmax(s1, double(v)); s2 = fmin(s2, double(v));
+      if (!isfinite(v)) { n3 += 1.0f; continue; }
+      k0.add(v); m1 = fmaxf(m1, v); m2 = fminf(m2, v);
     } else {
       if (v < 0.0f) continue;
-      s0 += v; s1 += bj ? bj[i] : bc; s2 += 1.0;
+      k0.add(v); k1.add(bj ? bj[i] : bc); n2 += 1.0f;
     }
   }
+  const double s0 = double(k0.s) - double(k0.c), s3 = n3;
+  const double s1 = mode ? double(k1.s) - double(k1.c) : double(m1), s2 = mode ? double(n2) : double(m2);
   __shared__ double r[4][256];
   r[0][threadIdx.x] = s0; r[1][threadIdx.x] = s1; r[2][threadIdx.x] = s2; r[3][threadIdx.x] = s3;
   __syncthreads();
@@ -295,14 +300,21 @@ __global__ void __launch_bounds__(256) k_stats_final(const double* __restrict__ 
   }
   r[0][threadIdx.x] = s0; r[1][threadIdx.x] = s1; r[2][threadIdx.x] = s2; r[3][threadIdx.x] = s3;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int t = 1; t < int(blockDim.x); ++t) {   // fixed order: deterministic
-      r[0][0] += r[0][t]; r[3][0] += r[3][t];
-      if (mode == 0) { r[1][0] = fmax(r[1][0], r[1][t]); r[2][0] = fmin(r[2][0], r[2][t]); }
-      else { r[1][0] += r[1][t]; r[2][0] += r[2][t]; }
+  for (int o = 128; o > 0; o >>= 1) {   // tree in a fixed pattern: deterministic
+    if (threadIdx.x < o) {
+      r[0][threadIdx.x] += r[0][threadIdx.x + o];
+      r[3][threadIdx.x] += r[3][threadIdx.x + o];
+      if (mode == 0) {
+        r[1][threadIdx.x] = fmax(r[1][threadIdx.x], r[1][threadIdx.x + o]);
+        r[2][threadIdx.x] = fmin(r[2][threadIdx.x], r[2][threadIdx.x + o]);
+      } else {
+        r[1][threadIdx.x] += r[1][threadIdx.x + o];
+        r[2][threadIdx.x] += r[2][threadIdx.x + o];
+      }
     }
-    for (int k = 0; k < 4; ++k) out[4 * plane + k] = r[k][0];
+    __syncthreads();
   }
+  if (threadIdx.x < 4) out[4 * plane + threadIdx.x] = r[threadIdx.x][0];
 }
 
 // f = value on R (w > 0), 0 elsewhere; or f = max(src, 0) restricted to R when src != nullptr
