@@ -93,3 +93,16 @@ def test_osem_rejects_mixed_sizes(gpu):
         prob.set_data(i, dev(np.asarray(s.g, np.float32)))
     with pytest.raises(gpu.SGPError):
         prob.osem_iterate(1)
+
+
+def test_osem_with_psf_band(gpu):
+    """3 x 512^2 two-pupil views: the PSF band drops about half of the spectrum columns, and the
+    OSEM sub-steps run over it."""
+    sc = scenes.cluster_multiview_scene(seed=9, N=512, p=3, n_sources=80)
+    orc = oracle_problem(sc)
+    ref = O.osem(orc, n_iter=4)
+    prob = gpu_problem(gpu, sc)
+    assert prob.info().band_cols < 256
+    prob.osem_iterate(4)
+    assert rel_l2(host(prob.get_f()), ref.f) <= 1e-4
+    assert abs(prob.kl_value() - ref.J) <= 1e-5 * ref.J

@@ -181,6 +181,31 @@ def test_osem_with_one_view_is_rl():
     np.testing.assert_allclose(O.osem(prob, f0, 3).f, O.rl(prob, f0, O.StopRule("fixed", 3)).f, rtol=1e-12)
 
 
+def test_osem_last_subset_fixes_the_flux_b0():
+    """Eq. (OSEMstep) with b = 0 and unit-volume PSFs: sum_n h^(j) = <h^(j-1), A_j^T (g_j / A_j h^(j-1))>
+    = sum_m g_j(m), so after an iteration the flux is that of the last view of the cycle (the views
+    differ in flux here, so a summed or reversed cycle fails)."""
+    psfs, g, _ = _small_scene(14, p=3)
+    assert len({round(float(x)) for x in g.sum(axis=(1, 2))}) == 3
+    prob = O.Problem(psfs, g, [0.0] * 3)
+    f = O.osem(prob, n_iter=2).f
+    assert abs(f.sum() - g[2].sum()) <= 1e-11 * g[2].sum()
+
+
+def test_boundary_osem_flux_identity_b0():
+    """Eq. (boundaryOSEM) with b = 0: sum_n alpha_j h^(j) = <h^(j-1), A_j^T r_j> = sum_S g_j for the
+    last view j of the cycle (alpha_j = K_j (x) M_S)."""
+    rng = scenes.rng_for(15)
+    sc = scenes.boundary_scene(rng, 40, 1.5, 0.0)
+    psfs = np.concatenate([sc.psfs, scenes.gaussian_psf(*sc.g.shape[1:], 2.5)[None]])
+    g = np.concatenate([sc.g, np.roll(sc.g, 1, axis=2) * sc.mask])
+    prob = O.Problem(psfs, g, [0.0, 0.0], mask_S=sc.mask)
+    f = O.osem(prob, n_iter=2).f
+    lhs = float(np.sum(prob.alpha_j[1] * f))
+    assert abs(lhs - prob.g[1].sum()) <= 1e-10 * prob.g[1].sum()
+    assert np.all(f[prob.MR == 0] == 0)
+
+
 # ----------------------------------------------------------------- KL / discrepancy
 def test_expected_discrepancy_of_true_object_is_one():
     """E[J_0(f~; g)] ~ N^2/2 for Poisson data (Sect. 3.3), so D(f~) ~ 1."""
