@@ -31,24 +31,24 @@ METRIC = "2048² SGP iters/s & time-to-stop vs plain FP32 on same GPU; % HBM roo
 ROOT = os.path.dirname(os.path.abspath(__file__))
 FALLBACK_HBM_GBS = 6400.0
 # algorithmic bytes per launch of each pass of one SGP iteration, in units of one H x W float32
-# plane (single view): K1 reads f, grad, A f, A d, g and writes f, A f, the ratio spectrum; the
-# column passes read a spectrum and the PSF spectrum and write a spectrum; K3 reads the spectrum,
-# f, f_prev, grad_prev and writes grad; K4 reads f, grad and writes a spectrum; K6 reads the
-# spectrum, A f, g and writes A d.  The controllers run in the last block of K1, K3, K6 and the
+# plane (single view): K1 reads A f, A d, g and writes A f, the ratio spectrum; the column passes
+# read a spectrum and the PSF spectrum and write a spectrum; K3 reads the spectrum, f_prev,
+# grad_prev and writes f (the pending update, formed there) and grad; K4 reads f, grad and writes a
+# spectrum; K6 reads the spectrum, A f, g and writes A d.  The controllers run in the last block of K1, K3, K6 and the
 # extra Armijo pass and move O(1) bytes; the extra pass returns at once unless no step length of
 # the main pass was accepted (it then reads A f, A d, g), so it is counted as 0.
 PASS_NAMES = ["update_ratio", "col_AT", "grad_bb", "proj_y", "col_A", "ad_armijo", "armijo_extra"]
 # planes per pass: pixel planes (always whole) and spectrum planes (the PSF spectrum K_hat and the
 # packed spectra), of which the passes move only the band's columns (fraction band_cols / (N/2))
-PASS_PIX = [7, 0, 4, 2, 0, 3, 0]
+PASS_PIX = [4, 0, 4, 2, 0, 3, 0]
 PASS_SPEC = [1, 3, 1, 1, 3, 1, 0]
-PASS_PLANES = [a + b for a, b in zip(PASS_PIX, PASS_SPEC)]   # without a band: 26 planes
+PASS_PLANES = [a + b for a, b in zip(PASS_PIX, PASS_SPEC)]   # without a band: 23 planes
 # DRAM bytes per launch of each pass at 2048^2 (ncu dram__bytes_read.sum + dram__bytes_write.sum,
 # caches flushed before the launch, second SGP iteration of `python bench.py --profile 8`), taken on
 # the kernels of this tree, PSF band of the Airy PSF in use (258 of 1024 spectrum columns).  A pass's
 # writes are mostly still in L2 when its launch ends, so the figures are mostly its reads; they
 # equal the algorithmic reads (no tile is read twice).
-TRAFFIC_2048 = {"update_ratio": 93.07e6, "col_AT": 8.98e6, "grad_bb": 55.21e6, "proj_y": 33.60e6,
+TRAFFIC_2048 = {"update_ratio": 50.81e6, "col_AT": 8.98e6, "grad_bb": 38.79e6, "proj_y": 33.60e6,
                 "col_A": 8.98e6, "ad_armijo": 38.24e6, "armijo_extra": 0.07e6}
 
 

@@ -89,9 +89,17 @@ struct CtrlCopy {
 template <bool FP64>
 __device__ void sgp_begin_decide(CtrlState* c, const double (&kl)[2]) {
   const int done = c->done;
-  if (!c->fresh) { c->k += 1; c->fresh = 1; }
+  if (!c->fresh) {
+    c->k += 1;
+    c->fresh = 1;
+    c->f_pending = f_update_in_k1(c, done) ? 0 : 1;
+  }
   if (done == 1) { c->done = 2; c->J = c->J_pred; return; }
-  if (!isfinite(kl[0])) { c->status = 8; c->done = 2; return; }
+  if (!isfinite(kl[0])) {   // stop at the last stored iterate (a pending f^(k) is not formed)
+    c->status = 8; c->done = 2;
+    if (c->f_pending) { c->k -= 1; c->f_pending = 0; }
+    return;
+  }
   c->J = kl[0];
   if (c->stop_kind == STOP_MIN_ERROR && c->ftrue_norm2 > 0.0) {
     const double rho = sqrt(kl[1] / c->ftrue_norm2);
@@ -124,6 +132,7 @@ __device__ void sgp_alpha_decide(CtrlState* c, const double (&bb)[4]) {
     alpha = bb_alpha<float>(c, float(bb[0]), float(bb[1]), float(bb[2]), float(bb[3]), c->k);
   }
   c->alpha = alpha;
+  c->f_pending = 0;   // K3 has stored f^(k)
 }
 template <bool FP64>
 __device__ void ctrl_sgp_alpha(const ImgDesc& d) {

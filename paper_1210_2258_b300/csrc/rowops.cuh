@@ -375,7 +375,7 @@ __device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ i
   const float lam = float(c->lambda);
   if (j == 0 && act) {
     float* fcur = d.f[ke & 1];
-    if (!fresh) {
+    if (!fresh && f_update_in_k1(c, done)) {
       const float* fo = d.f[k & 1];
       const float* go = d.grad[k & 1];
       const float alpha = float(c->alpha), mu = float(c->mu);
@@ -452,6 +452,8 @@ __global__ void __launch_bounds__(kRowBlock, 4) k_sgp_update_ratio(const ImgDesc
 }
 
 // SGP K3: C2R of plane 0 (= sum_j A_j^T r_j) -> gradient, and the four scaled-BB partial sums.
+// With f_pending it first forms f^(k) = f^(k-1) + lambda d from f^(k-1) and grad^(k-1) (the step
+// of the previous iteration: its alpha, mu and lambda are still in the state) and stores it.
 template <int W, bool FP64>
 __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
                                                           const int2* __restrict__ items, int n_items) {
@@ -474,12 +476,14 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
     row_spec_to_real<W>(x, spec_plane(d, 0) + off, t, act, d.cb);
     KSum acc[4];
     if (act) {
-      const float* f = d.f[ke & 1];
+      float* f = d.f[ke & 1];
       const float* fp = d.f[(ke + 1) & 1];
       const float* gp = d.grad[(ke + 1) & 1];
       float* gn = d.grad[ke & 1];
       const float L1 = float(c->L1), L2 = float(c->L2);
       const bool bb = ke >= 1;
+      const bool pend = c->f_pending != 0;
+      const float lam = float(c->lambda), alpha = float(c->alpha), mu = float(c->mu);
       constexpr int B = batch_of<G::E, 4>();
 #pragma unroll 1
       for (int q0 = 0; q0 < G::E; q0 += B) {
@@ -489,7 +493,18 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
           const size_t i = off + t + (q0 + b) * G::T;
           wv[b] = w_pair(d, i);
           const float2 z2 = make_float2(0.0f, 0.0f);
-          fcv[b] = bb ? ld2(f, i) : z2; fov[b] = bb ? ld2(fp, i) : z2; gov[b] = bb ? ld2(gp, i) : z2;
+          fcv[b] = bb && !pend ? ld2(f, i) : z2; fov[b] = bb ? ld2(fp, i) : z2; gov[b] = bb ? ld2(gp, i) : z2;
+        }
+        if (pend) {   // f^(k) = f^(k-1) + lambda (P(f^(k-1) - alpha D grad^(k-1)) - f^(k-1)), as K1 forms it
+#pragma unroll
+          for (int b = 0; b < B; ++b) {
+            const float2 fo = fov[b], go = gov[b], w = wv[b];
+            float2 fn;
+            fn.x = fmaf(lam, proj_step(fo.x, go.x, w.x, alpha, mu, L1, L2) - fo.x, fo.x);
+            fn.y = fmaf(lam, proj_step(fo.y, go.y, w.y, alpha, mu, L1, L2) - fo.y, fo.y);
+            fcv[b] = fn;
+            st2(f, off + t + (q0 + b) * G::T, fn);
+          }
         }
 #pragma unroll
         for (int b = 0; b < B; ++b) {

@@ -68,6 +68,8 @@ struct CtrlState {
   unsigned arrive;  // blocks of the current row pass that have stored their partial sums
   int arm_nl;       // step lengths of the main Armijo pass (1, 2 or kArmMain; 0 before the first)
   int land_pass;    // landed discrepancy stop: 0 idle; n > 0 landing the last step, n - 1 passes done
+  int f_pending;    // SGP: K1 left f^(k+1) = f^(k) + lambda d to the gradient pass, which forms it
+                    // from f^(k) and grad^(k) and stores it (see f_update_in_k1)
   double land_lo, land_hi, land_Jlo, land_Jhi, land_Jt;   // bracket of lambda, J at its ends, target
   double J;         // J_0 at the current iterate
   double J_pred;    // J_0 at the accepted trial point
@@ -80,6 +82,13 @@ struct CtrlState {
   double mu_lo, mu_hi, phi_lo, phi_hi;
   double scratch[8];
 };
+// The pending SGP update f^(k+1) = f^(k) + lambda d (Alg. 1, step 6) is applied by K1 when the stop
+// is already decided (the final update) or the minimum-error rule needs f^(k+1) in K1; otherwise
+// by the gradient pass K3, which reads f^(k) and grad^(k) anyway, so K1 reads neither.  `done` is
+// the value at K1's start.
+__host__ __device__ inline bool f_update_in_k1(const CtrlState* c, int done) {
+  return done == 1 || c->stop_kind == STOP_MIN_ERROR;
+}
 __host__ __device__ inline int arm_count(const CtrlState* c) {
   return c->arm_nl == 1 || c->arm_nl == 2 || c->arm_nl == kArmMain ? c->arm_nl : 2;
 }
