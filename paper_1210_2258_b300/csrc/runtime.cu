@@ -215,7 +215,7 @@ struct sgp_ctx {
   int n = 0;
   cudaStream_t s = nullptr;        // internal stream (graphs are captured on it)
   cudaStream_t user = nullptr;     // caller's stream
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_poll[2] = {nullptr, nullptr};
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   sgp_params prm;
   std::vector<sgp_shape> sh;
   Layout L;
@@ -239,7 +239,7 @@ struct sgp_ctx {
   std::vector<const float*> truth;
   std::vector<int> start_in_f0;    // 1: a new start was written to f[0] since the last set-up
   int mode = 0;                    // 0 not prepared, 1 SGP, 2 RL, 3 OSEM
-  cudaGraphExec_t g_sgp = nullptr, g_rl = nullptr, g_land = nullptr;   // g_land: SGP + landing passes
+  cudaGraphExec_t g_sgp = nullptr, g_rl = nullptr;   // graph_units iterations (fixed counts)
   cudaGraphExec_t g_osem = nullptr;  // one OSEM iteration (p sub-steps)
   // solve loops: a WHILE node around one iteration and the loop condition (run_until)
   cudaGraphExec_t gl_sgp = nullptr, gl_rl = nullptr, gl_land = nullptr;
@@ -248,7 +248,7 @@ struct sgp_ctx {
   int loop_cap = 0;                // iteration cap captured in the solve loop graphs
   bool col_narrow = false;         // the iteration's column passes use the narrow variant (set_band)
   long long launches = 0;          // kernels enqueued (graph nodes counted per graph launch)
-  CtrlState* h_ctrl = nullptr;     // pinned mirror of the controller array (2 slots for polling)
+  CtrlState* h_ctrl = nullptr;     // pinned mirror of the controller array
 };
 
 namespace {
@@ -586,14 +586,14 @@ sgp_status seq_sgp_unit(sgp_ctx* c, bool land = false) {
 // a stop decided in the last unit of a graph leaves the update f^(k+1) = f^(k) + lambda d pending
 sgp_status seq_sgp_finalize(sgp_ctx* c) { return row_pass(c, ROP_SGP_UPDATE, true); }
 
-sgp_status build_graph(sgp_ctx* c, bool sgp, cudaGraphExec_t* out, bool land = false) {
+sgp_status build_graph(sgp_ctx* c, bool sgp, cudaGraphExec_t* out) {
   if (*out) return SGP_OK;
   cudaGraph_t g = nullptr;
   CU(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
   long long* saved = g_launch_counter;
   g_launch_counter = nullptr;
   sgp_status st = SGP_OK;
-  for (int u = 0; u < c->graph_units && st == SGP_OK; ++u) st = sgp ? seq_sgp_unit(c, land) : seq_rl_unit(c);
+  for (int u = 0; u < c->graph_units && st == SGP_OK; ++u) st = sgp ? seq_sgp_unit(c) : seq_rl_unit(c);
   cudaError_t e = cudaStreamEndCapture(c->s, &g);
   g_launch_counter = saved;
   if (st) { if (g) cudaGraphDestroy(g); return st; }
@@ -1023,11 +1023,9 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
   auto bail = [&](sgp_status s) { sgp_destroy(c); return s; };
   if (cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_poll[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_poll[1], cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(SGP_ERR_CUDA, "stream/event creation failed"));
-  if (cudaMallocHost(&c->h_ctrl, sizeof(CtrlState) * 2 * n) != cudaSuccess)
+  if (cudaMallocHost(&c->h_ctrl, sizeof(CtrlState) * n) != cudaSuccess)
     return bail(fail(SGP_ERR_CUDA, "pinned host buffer allocation failed"));
 
   std::vector<unsigned char> hb(n);
@@ -1563,7 +1561,6 @@ sgp_status sgp_set_tile(sgp_ctx* c, int rows) {
   CU(cudaStreamSynchronize(c->s));
   // captured graphs hold the old launch geometry
   if (c->g_sgp) { cudaGraphExecDestroy(c->g_sgp); c->g_sgp = nullptr; }
-  if (c->g_land) { cudaGraphExecDestroy(c->g_land); c->g_land = nullptr; }
   if (c->g_rl) { cudaGraphExecDestroy(c->g_rl); c->g_rl = nullptr; }
   if (c->g_osem) { cudaGraphExecDestroy(c->g_osem); c->g_osem = nullptr; }
   if (c->gl_sgp) { cudaGraphExecDestroy(c->gl_sgp); c->gl_sgp = nullptr; }
@@ -1640,7 +1637,6 @@ sgp_status sgp_destroy(sgp_ctx* c) {
   if (!c) return SGP_OK;
   if (c->s) cudaStreamSynchronize(c->s);
   if (c->g_sgp) cudaGraphExecDestroy(c->g_sgp);
-  if (c->g_land) cudaGraphExecDestroy(c->g_land);
   if (c->g_rl) cudaGraphExecDestroy(c->g_rl);
   if (c->g_osem) cudaGraphExecDestroy(c->g_osem);
   if (c->gl_sgp) cudaGraphExecDestroy(c->gl_sgp);
@@ -1648,8 +1644,6 @@ sgp_status sgp_destroy(sgp_ctx* c) {
   if (c->gl_land) cudaGraphExecDestroy(c->gl_land);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
-  for (auto& e : c->ev_poll)
-    if (e) cudaEventDestroy(e);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
   if (c->s) cudaStreamDestroy(c->s);
   delete c;
