@@ -238,6 +238,75 @@ def cufft_comparison(torch, lib, prob, psf_d, g_d, reps=20):
             "rel_l2_difference": err}
 
 
+def cufft_sgp_baseline(torch, psf_d, g_d, b, max_iter=3000):
+    """Comparison line: the same SGP (Algorithm 1: scaled BB1/BB2 with the safeguards, the
+    alternation, the window of 3 and the 20-iteration warm-up; Armijo backtracking; the scaling
+    clip(f, L1, L2) with L1, L2 from one RL step; constant start; discrepancy stop eta = 1) written
+    the way a plain FP32 PyTorch program would: cuFFT through torch.fft for A and A^T, torch
+    element-wise ops and reductions in FP32, the scalar decisions on the host (one device read per
+    decision).  Single periodic image.  Returns (iterations, ms, final discrepancy)."""
+    import math
+    psf = psf_d[0] / psf_d[0].sum()
+    khat = torch.fft.rfft2(torch.fft.ifftshift(psf))
+    g = g_d[0]
+    N2 = g.numel()
+    A = lambda x: torch.fft.irfft2(torch.fft.rfft2(x) * khat, s=x.shape)
+    AT = lambda y: torch.fft.irfft2(torch.fft.rfft2(y) * torch.conj(khat), s=y.shape)
+    pos = g > 0
+
+    def J(u):      # KL divergence at u = A f + b (0 ln 0 = 0)
+        return float(torch.sum(torch.where(pos, g * torch.log(g / u), torch.zeros_like(g)) + u - g))
+
+    def grad(u):   # 1 - A^T (g / u) (unit-volume PSF)
+        return 1.0 - AT(g / u)
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    c = max(float(g.sum()) / N2 - b, 1e-3)
+    f = torch.full_like(g, c)
+    u = A(f) + b
+    y = f * AT(g / u)                          # one RL step -> L1, L2 (Sect. 3.2)
+    ymin, ymax = float(y[y > 0].min()), float(y.max())
+    L1, L2 = (ymin / 10, ymax * 10) if ymax / ymin < 50 else (ymin, ymax)
+    Jk = J(u)
+    gr = grad(u)
+    alpha, tau, hist, k = 1.3, 0.5, [], 0
+    beta, theta, amin, amax = 1e-4, 0.4, 1e-5, 1e5
+    while 2 * Jk / N2 > 1.0 and k < max_iter:
+        D = torch.clamp(f, L1, L2)
+        d = torch.clamp(f - alpha * D * gr, min=0.0) - f
+        Ad = A(d)
+        gTd = float(torch.sum(gr * d))
+        lam = 1.0
+        while True:                            # Armijo backtracking (Alg. 1, step 5)
+            Jn = J(u + lam * Ad)
+            if Jn <= Jk + beta * lam * gTd or lam < 1e-12:
+                break
+            lam *= theta
+        fn = f + lam * d
+        un = u + lam * Ad
+        gn = grad(un)
+        s_, z = fn - f, gn - gr
+        Dn = torch.clamp(fn, L1, L2)
+        k += 1
+        n1, d1 = float(torch.sum(s_ * s_ / (Dn * Dn))), float(torch.sum(s_ * z / Dn))
+        n2, d2 = float(torch.sum(s_ * z * Dn)), float(torch.sum(z * z * Dn * Dn))
+        a1 = min(10 * alpha, amax) if d1 <= 0 else min(amax, max(amin, n1 / d1))
+        a2 = min(10 * alpha, amax) if n2 <= 0 else min(amax, max(amin, n2 / d2))
+        hist = (hist + [a2])[-3:]
+        if k <= 20:
+            alpha = min(hist)
+        elif a2 / a1 <= tau:
+            alpha, tau = min(hist), tau * 0.9
+        else:
+            alpha, tau = a1, tau * 1.1
+        f, u, gr, Jk = fn, un, gn, Jn
+    ev1.record()
+    torch.cuda.synchronize()
+    return k, ev0.elapsed_time(ev1), 2 * Jk / N2 if math.isfinite(Jk) else float("nan")
+
+
 def run_ours(args):
     import torch
     if args.profile:
@@ -323,6 +392,11 @@ def run_ours(args):
     plain.close()
 
     cufft = cufft_comparison(torch, lib, prob, psf_d, g_d)
+    cufft_sgp_baseline(torch, psf_d, g_d, float(sc.b[0]))          # warm-up (cuFFT plans)
+    it_c, ms_c, D_c = cufft_sgp_baseline(torch, psf_d, g_d, float(sc.b[0]))
+    cufft["sgp_to_stop"] = {"what": "plain FP32 PyTorch + cuFFT (torch.fft) SGP, host-side decisions",
+                            "iterations": it_c, "time_to_stop_ms": ms_c, "iters_per_s": it_c / (ms_c / 1e3),
+                            "final_discrepancy": D_c}
 
     # end to end through the public API with host buffers.  Headline: the instrument's context
     # (PSF spectrum, workspace, graphs) is prepared once; every step copies that step's image in
