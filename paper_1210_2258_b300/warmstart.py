@@ -291,7 +291,8 @@ def evaluate(net: WarmStartNet, scs, max_iter: int = 2000, batch: int = 50, n_si
     network forward + solve from its f^(0))."""
     import torch
     out = {"flat_iters": [], "warm_iters": [], "flat_kl": [], "warm_kl": [], "flat_ms": 0.0, "warm_ms": 0.0,
-           "net_ms": 0.0, "fallbacks": 0, "single_flat_ms": [], "single_warm_ms": [], "single_net_ms": []}
+           "net_ms": 0.0, "fallbacks": 0, "single_flat_ms": [], "single_warm_ms": [], "single_net_ms": [],
+           "single_flat32_ms": [], "single_kl_rel_warm_flat32": []}
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     for a in range(0, len(scs), batch):
         part = scs[a:a + batch]
@@ -339,28 +340,44 @@ def evaluate(net: WarmStartNet, scs, max_iter: int = 2000, batch: int = 50, n_si
         prob.set_data(0, g)
         f0 = net.predict(g, bvec)
         prob.solve_until(lib.STOP_LANDED, max_iter=max_iter, eta=1.0, tol=LAND_TOL, raise_on_error=False)   # graph
-        times = {}
-        for mode in ("flat", "warm"):
+        # the plain FP32 single-image form (FP32 reductions and decisions, flat start)
+        prob32 = lib.Problems(psf, [float(sc.b[0])], params=lib.default_params(reduce_fp64=0))
+        prob32.set_data(0, g)
+        prob32.solve_until(lib.STOP_LANDED, max_iter=max_iter, eta=1.0, tol=LAND_TOL, raise_on_error=False)
+        times, kls = {}, {}
+        for mode in ("flat", "warm", "flat32"):
+            pr = prob32 if mode == "flat32" else prob
             torch.cuda.synchronize()
             ev[0].record()
             if mode == "warm":
                 f0 = net.predict(g, bvec)
                 ev[2].record()
-                prob.set_start(0, lib.START_USER, f0[0])
+                pr.set_start(0, lib.START_USER, f0[0])
             else:
-                prob.set_start(0, lib.START_CONSTANT)
-            prob.solve_until(lib.STOP_LANDED, max_iter=max_iter, eta=1.0, tol=LAND_TOL, raise_on_error=False)
+                pr.set_start(0, lib.START_CONSTANT)
+            pr.solve_until(lib.STOP_LANDED, max_iter=max_iter, eta=1.0, tol=LAND_TOL, raise_on_error=False)
             ev[1].record()
             torch.cuda.synchronize()
-            times[mode] = ev[0].elapsed_time(ev[1]) if prob.info(0).status == 0 else None
+            inf = pr.info(0)
+            times[mode] = ev[0].elapsed_time(ev[1]) if inf.status == 0 and inf.stopped else None
+            kls[mode] = pr.get_f(0).clone()
             if mode == "warm":
                 times["net"] = ev[0].elapsed_time(ev[2])
+        # final KL of the warm (mixed) and plain-FP32 results, both evaluated with FP64 accumulation
+        for mode in ("warm", "flat32"):
+            prob.set_start(0, lib.START_USER, kls[mode])
+            kls[mode] = prob.kl_value(0)
         if times["flat"] is not None and times["warm"] is not None:
             out["single_flat_ms"].append(times["flat"])
             out["single_warm_ms"].append(times["warm"])
             out["single_net_ms"].append(times["net"])
+            if times["flat32"] is not None:
+                out["single_flat32_ms"].append(times["flat32"])
+                out["single_kl_rel_warm_flat32"].append(abs(kls["warm"] - kls["flat32"]) / kls["flat32"])
         prob.close()
-    for k in ("flat_iters", "warm_iters", "flat_kl", "warm_kl", "single_flat_ms", "single_warm_ms", "single_net_ms"):
+        prob32.close()
+    for k in ("flat_iters", "warm_iters", "flat_kl", "warm_kl", "single_flat_ms", "single_warm_ms", "single_net_ms",
+              "single_flat32_ms", "single_kl_rel_warm_flat32"):
         out[k] = np.asarray(out[k])
     return out
 
@@ -439,6 +456,15 @@ def main(argv=None) -> int:
                   "single_warm_ms_median": float(np.median(res["single_warm_ms"])),
                   "single_net_ms_median": float(np.median(res["single_net_ms"])),
                   "single_warm_faster_frac": float(np.mean(res["single_warm_ms"] < res["single_flat_ms"]))}
+        if len(res["single_flat32_ms"]) == len(res["single_warm_ms"]):
+            single.update({"single_flat_plain_fp32_ms_median": float(np.median(res["single_flat32_ms"])),
+                           "single_warm_faster_than_plain_fp32_frac":
+                               float(np.mean(res["single_warm_ms"] < res["single_flat32_ms"])),
+                           "single_kl_rel_warm_vs_plain_fp32_max": float(np.max(res["single_kl_rel_warm_flat32"])),
+                           "single_kl_rel_warm_vs_plain_fp32_median":
+                               float(np.median(res["single_kl_rel_warm_flat32"])),
+                           "single_kl_rel_warm_vs_plain_fp32_le_1e-4_frac":
+                               float(np.mean(res["single_kl_rel_warm_flat32"] <= 1e-4))})
     kl_rel = np.abs(res["warm_kl"] - res["flat_kl"]) / res["flat_kl"]
     summary = {
         "train_pairs": len(tr), "train_side": a.train_side, "eval_images": len(ev_scenes), "eval_side": a.eval_side,
