@@ -174,7 +174,7 @@ __device__ __forceinline__ void row_load(const RowLayout<W / 2>& x, const float2
 #pragma unroll
     for (int q = 0; q < G::E; ++q) {
       const int i = t + q * G::T;
-      x(i) = i < cb ? src[i] : make_float2(0.0f, 0.0f);
+      x(i) = i < cb ? src[kSpecColStride * i] : make_float2(0.0f, 0.0f);
     }
   }
 }
@@ -186,7 +186,7 @@ __device__ __forceinline__ void row_store(const RowLayout<W / 2>& x, float2* __r
 #pragma unroll
     for (int q = 0; q < G::E; ++q) {
       const int i = t + q * G::T;
-      if (i < cb) dst[i] = x(i);
+      if (i < cb) dst[kSpecColStride * i] = x(i);
     }
   }
 }
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kRowBlock) k_row_r2c(const float* __restrict__
         x(t + q * G::T) = z;
       }
     }
-    row_real_to_spec<W>(x, out + v * out_vs + size_t(row) * G::M, t, act);
+    row_real_to_spec<W>(x, out + v * out_vs + spec_row_off(row, G::M), t, act);
   }
 }
 
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kRowBlock) k_row_c2r(const float2* __restrict_
     const int v = it / per_view;
     const int row = (it % per_view) * G::ROWS + r;
     const bool act = row < H;
-    row_spec_to_real<W>(x, in + v * in_vs + size_t(row) * G::M, t, act);
+    row_spec_to_real<W>(x, in + v * in_vs + spec_row_off(row, G::M), t, act);
     float2* dst = reinterpret_cast<float2*>(out + v * out_vs + size_t(row) * W);
     if (act) {
 #pragma unroll
@@ -440,7 +440,7 @@ __device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ i
     }
   }
   if (done == 0) {
-    row_real_to_spec<W>(x, spec_plane(d, j + 1) + off, t, act, d.cb);
+    row_real_to_spec<W>(x, spec_plane(d, j + 1) + spec_row_off(row, G::M), t, act, d.cb);
     block_sum_store<2, FP64>(acc, partv_of(d, it) + SLOT_KL);
   }
   if (arrive_last(d.ctrl, d.n_rv_items)) ctrl_sgp_begin<FP64>(d);
@@ -473,7 +473,7 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
     const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
-    row_spec_to_real<W>(x, spec_plane(d, 0) + off, t, act, d.cb);
+    row_spec_to_real<W>(x, spec_plane(d, 0) + spec_row_off(row, G::M), t, act, d.cb);
     KSum acc[4];
     if (act) {
       float* f = d.f[ke & 1];
@@ -585,7 +585,7 @@ __device__ __forceinline__ void b_sgp_y(const ImgDesc* __restrict__ imgs,
         }
       }
     }
-    row_real_to_spec<W>(x, spec_plane(d, 0) + off, t, act, d.cb);
+    row_real_to_spec<W>(x, spec_plane(d, 0) + spec_row_off(row, G::M), t, act, d.cb);
     block_sum_store<1, FP64>(acc, part_of(d, it) + SLOT_GTD);
   }
 }
@@ -649,7 +649,7 @@ __device__ __forceinline__ void b_sgp_ad_armijo(const ImgDesc* __restrict__ imgs
 #pragma unroll
   for (int l = 1; l < kArmMain; ++l) lam[l] = lam[l - 1] * th;
   KSum acc[kArmMain];
-  row_spec_to_real<W>(x, spec_plane(d, j + 1) + off, t, act, d.cb);
+  row_spec_to_real<W>(x, spec_plane(d, j + 1) + spec_row_off(row, G::M), t, act, d.cb);
   if (act) {
     const float* uj = d.u + size_t(j) * d.P;
     float* adj = d.Ad + size_t(j) * d.P;
@@ -755,9 +755,9 @@ __device__ __forceinline__ void b_rl_update(const ImgDesc* __restrict__ imgs,
     const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
-    float2* sp = spec_plane(d, 0) + off;
+    float2* sp = spec_plane(d, 0) + spec_row_off(row, G::M);
     const bool osem = wview >= 0;
-    if (hv) row_spec_to_real<W>(x, osem ? spec_plane(d, wview + 1) + off : sp, t, act, d.cb);
+    if (hv) row_spec_to_real<W>(x, osem ? spec_plane(d, wview + 1) + spec_row_off(row, G::M) : sp, t, act, d.cb);
     KSum acc[1];
     if (act) {
       const float* fo = d.f[k & 1];
@@ -814,7 +814,7 @@ __device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
   const bool act = row < d.H;
   const size_t off = size_t(row) * G::M;
   KSum acc[1];
-  float2* sp = spec_plane(d, j + 1) + off;
+  float2* sp = spec_plane(d, j + 1) + spec_row_off(row, G::M);
   row_spec_to_real<W>(x, sp, t, act, d.cb);
   if (act) {
     float* uj = d.u + size_t(j) * d.P;
@@ -862,7 +862,7 @@ __device__ __forceinline__ void b_rl_step_minmax(const ImgDesc* __restrict__ img
     const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
-    row_spec_to_real<W>(x, spec_plane(d, 0) + off, t, act, d.cb);
+    row_spec_to_real<W>(x, spec_plane(d, 0) + spec_row_off(row, G::M), t, act, d.cb);
     float mn = f_inf(), mx = 0.0f;
     if (act) {
       const float* f = d.f[d.ctrl->k & 1];
