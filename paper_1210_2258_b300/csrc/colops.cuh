@@ -36,11 +36,12 @@ template <int H, bool NARROW = false> struct ColGeo {
 template <class P, int C>
 __device__ __forceinline__ void col_load(const ColLayout<C>& x, const float2* __restrict__ src, int M, int t, bool act) {
   constexpr int T = P::T, E = P::E;
+  constexpr bool IL = spec_interleaved(P::L);
   if (act) {
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const int i = t + q * T;
-      x(i) = src[spec_col_idx(i, M)];
+      x(i) = src[spec_row_off(i, M, IL)];
     }
   }
 }
@@ -49,7 +50,8 @@ __device__ __forceinline__ void col_load(const ColLayout<C>& x, const float2* __
 template <int H, int C, bool CONJ>
 __device__ __forceinline__ float2 col_product(const ColLayout<C>& x, int i, int col, float2 X,
                                               const float2* __restrict__ kh, const float2* __restrict__ kq, int M) {
-  float2 K = __ldg(&kh[spec_col_idx(i, M) + kSpecColStride * col]);
+  constexpr bool IL = spec_interleaved(H);
+  float2 K = __ldg(&kh[spec_row_off(i, M, IL) + (IL ? 4 : 1) * col]);
   if (CONJ) K = cconj(K);
   if (col != 0) return cmul(X, K);
   float2 Q = __ldg(&kq[i]);
@@ -68,10 +70,15 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
   using CP = typename G::P;
   constexpr int C = G::C, T = G::T, E = G::E;
   extern __shared__ float2 smem[];
-  // lanes: 4 consecutive lanes take 4 consecutive rows of one column, then the next column, so a
-  // warp's global accesses are runs of 4 rows x C columns of the interleaved spectrum layout
-  const int c = T % 4 == 0 ? int(threadIdx.x >> 2) % C : int(threadIdx.x) % C;
-  const int t = T % 4 == 0 ? int(threadIdx.x & 3) + 4 * int(threadIdx.x / (4 * C)) : int(threadIdx.x) / C;
+  // lanes: for tiles of up to 8 columns, 4 consecutive lanes take 4 consecutive rows of one column,
+  // then the next column, so a warp's global accesses are runs of 4 rows x C columns of the
+  // interleaved spectrum layout; wider tiles keep the columns fastest (4 rows of a 16- or more
+  // column tile would fall into the same shared-memory banks)
+  // (the mapping only affects speed: addresses follow the plane's layout, spec_row_off)
+  constexpr bool RUNS = T % 4 == 0 && C <= 8;
+  constexpr bool IL = spec_interleaved(H);
+  const int c = RUNS ? int(threadIdx.x >> 2) % C : int(threadIdx.x) % C;
+  const int t = RUNS ? int(threadIdx.x & 3) + 4 * int(threadIdx.x / (4 * C)) : int(threadIdx.x) / C;
   const ColLayout<C> x{smem + c};
   {
     const int it = blockIdx.x;
@@ -83,7 +90,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
     const int col = (item.y & 0xffff) + c;
     const bool act = col < M;
     if (MODE == COL_KHAT) {
-      col_load<CP, C>(x, jb.in + kSpecColStride * col, M, t, act);
+      col_load<CP, C>(x, jb.in + (IL ? 4 : 1) * col, M, t, act);
       __syncthreads();
       fft_inplace<H, false, ColLayout<C>, CP>(x, t, act);
       if (act) {
@@ -116,7 +123,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
 #pragma unroll
         for (int q = 0; q < E; ++q) {
           const int i = t + q * T;
-          jb.out[spec_col_idx(i, M) + kSpecColStride * col] = outv[q];
+          jb.out[spec_row_off(i, M, IL) + (IL ? 4 : 1) * col] = outv[q];
           if (col == 0) jb.khatq[i] = qv[q];
         }
       }
@@ -125,7 +132,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
       constexpr bool CJ = MODE != COL_1TOP;
       {
         const int j = item.y >> 16;
-        col_load<CP, C>(x, jb.in + (MODE == COL_PTOV ? size_t(j) * jb.plane_stride : size_t(0)) + kSpecColStride * col,
+        col_load<CP, C>(x, jb.in + (MODE == COL_PTOV ? size_t(j) * jb.plane_stride : size_t(0)) + (IL ? 4 : 1) * col,
                         M, t, act);
         __syncthreads();
         fft_inplace<H, false, ColLayout<C>, CP>(x, t, act);
@@ -147,17 +154,17 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
         __syncthreads();
         fft_inplace<H, true, ColLayout<C>, CP>(x, t, act);
         if (act) {
-          float2* dst = jb.out + size_t(MODE == COL_PTOV ? j + 1 : j) * jb.plane_stride + kSpecColStride * col;
+          float2* dst = jb.out + size_t(MODE == COL_PTOV ? j + 1 : j) * jb.plane_stride + (IL ? 4 : 1) * col;
 #pragma unroll
           for (int q = 0; q < E; ++q) {
             const int i = t + q * T;
-            dst[spec_col_idx(i, M)] = x(i);
+            dst[spec_row_off(i, M, IL)] = x(i);
           }
         }
         __syncthreads();
       }
     } else if (NV == 1) {  // COL_PTO1, one view: the product goes straight back to x
-      col_load<CP, C>(x, jb.in + kSpecColStride * col, M, t, act);
+      col_load<CP, C>(x, jb.in + (IL ? 4 : 1) * col, M, t, act);
       __syncthreads();
       fft_inplace<H, false, ColLayout<C>, CP>(x, t, act);
       float2 v[E];
@@ -176,21 +183,21 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
       __syncthreads();
       fft_inplace<H, true, ColLayout<C>, CP>(x, t, act);
       if (act) {
-        float2* dst = jb.out + kSpecColStride * col;
+        float2* dst = jb.out + (IL ? 4 : 1) * col;
 #pragma unroll
         for (int q = 0; q < E; ++q) {
           const int i = t + q * T;
-          dst[spec_col_idx(i, M)] = x(i);
+          dst[spec_row_off(i, M, IL)] = x(i);
         }
       }
       __syncthreads();
     } else {  // COL_PTO1, p views: the sum over views accumulates in the output column (L2-resident;
               // a register accumulator live across the p transforms spilled), then back into x
       const int nin = NV > 0 ? NV : jb.nin;
-      float2* o = jb.out + kSpecColStride * col;
+      float2* o = jb.out + (IL ? 4 : 1) * col;
 #pragma unroll 1
       for (int j = 0; j < nin; ++j) {
-        col_load<CP, C>(x, jb.in + size_t(j) * jb.plane_stride + kSpecColStride * col, M, t, act);
+        col_load<CP, C>(x, jb.in + size_t(j) * jb.plane_stride + (IL ? 4 : 1) * col, M, t, act);
         __syncthreads();
         fft_inplace<H, false, ColLayout<C>, CP>(x, t, act);
         if (act) {
@@ -200,7 +207,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
           for (int q = 0; q < E; ++q) {
             const int i = t + q * T;
             const float2 pr = col_product<H, C, true>(x, i, col, x(i), kh, kq, M);
-            const size_t oi = spec_col_idx(i, M);
+            const size_t oi = spec_row_off(i, M, IL);
             o[oi] = j == 0 ? pr : cadd(o[oi], pr);   // this thread's own elements only
           }
         }
@@ -210,17 +217,17 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
 #pragma unroll
         for (int q = 0; q < E; ++q) {
           const int i = t + q * T;
-          x(i) = o[spec_col_idx(i, M)];
+          x(i) = o[spec_row_off(i, M, IL)];
         }
       }
       __syncthreads();
       fft_inplace<H, true, ColLayout<C>, CP>(x, t, act);
       if (act) {
-        float2* dst = jb.out + kSpecColStride * col;
+        float2* dst = jb.out + (IL ? 4 : 1) * col;
 #pragma unroll
         for (int q = 0; q < E; ++q) {
           const int i = t + q * T;
-          dst[spec_col_idx(i, M)] = x(i);
+          dst[spec_row_off(i, M, IL)] = x(i);
         }
       }
       __syncthreads();

@@ -377,7 +377,7 @@ __global__ void k_khat_colmax(const float2* __restrict__ khat, int H, int M, int
   float m = 0.0f;
   for (int j = 0; j < p; ++j)
     for (int r = blockIdx.y; r < H; r += gridDim.y) {
-      const float2 v = khat[size_t(j) * H * M + spec_row_off(r, M) + kSpecColStride * col];   // interleaved rows
+      const float2 v = khat[size_t(j) * H * M + spec_row_off(r, M, spec_interleaved(H)) + (spec_interleaved(H) ? 4 : 1) * col];
       m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
     }
   atomicMax(reinterpret_cast<int*>(out) + col, __float_as_int(m));

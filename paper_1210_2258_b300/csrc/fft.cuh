@@ -214,17 +214,17 @@ template <> struct ColPlanNarrow<2048> {
 constexpr int kNarrowSide = 2048;   // the one length with a narrow column variant
 
 // ------------------------------------------------------------------------------ spectrum layout
-// Packed spectra (and the PSF spectra) are stored interleaved by groups of 4 rows: element (row r,
-// column i) of an H x M plane at ((r / 4) M + i) 4 + r % 4 (H is a multiple of 4).  A column pass
-// then reads and writes runs of 4 rows x its columns (64 - 128 contiguous bytes) instead of one
-// 16 - 32-byte piece per row; a row is read or written with a stride of 4 elements.
-__host__ __device__ __forceinline__ size_t spec_row_off(int row, int M) {   // start of row r
-  return size_t(row >> 2) * 4 * size_t(M) + (row & 3);
+// Packed spectra (and the PSF spectra) of H >= 1024 rows are stored interleaved by groups of 4
+// rows: element (row r, column i) of an H x M plane at ((r / 4) M + i) 4 + r % 4.  A column pass
+// (narrow tiles at these H) then reads and writes runs of 4 rows x its columns (64 - 128 contiguous
+// bytes) instead of one 16 - 32-byte piece per row; a row is read with a stride of 4 elements.
+// Fewer rows (small, L2-resident planes, where the strided row accesses cost more than the column
+// runs save) keep the row-major layout: element (r, i) at r M + i.  The column passes know H at
+// compile time, the row passes at run time.
+__host__ __device__ constexpr bool spec_interleaved(int H) { return H >= 1024; }
+__host__ __device__ __forceinline__ size_t spec_row_off(int row, int M, bool il) {   // start of row r
+  return il ? size_t(row >> 2) * 4 * size_t(M) + (row & 3) : size_t(row) * M;
 }
-__host__ __device__ __forceinline__ size_t spec_col_idx(int i, int M) {     // row i of a column
-  return size_t(i >> 2) * 4 * size_t(M) + (i & 3);
-}
-constexpr int kSpecColStride = 4;   // distance of adjacent columns (and of a row's elements)
 
 // ------------------------------------------------------------------------------ layouts
 // Row layout: element i of a row at base[i + (i >> 4)] (one pad slot per 16 elements keeps the

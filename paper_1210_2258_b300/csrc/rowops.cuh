@@ -168,25 +168,25 @@ __device__ __forceinline__ void block_minmax_store(float mn, float mx, double* o
 // zero beyond (the PSF spectrum is zero there, so is every product with it).  cb = W/2: all.
 template <int W>
 __device__ __forceinline__ void row_load(const RowLayout<W / 2>& x, const float2* __restrict__ src, int t, bool act,
-                                         int cb) {
+                                         int cb, bool il) {
   using G = RowGeo<W>;
   if (act) {
 #pragma unroll
     for (int q = 0; q < G::E; ++q) {
       const int i = t + q * G::T;
-      x(i) = i < cb ? src[kSpecColStride * i] : make_float2(0.0f, 0.0f);
+      x(i) = i < cb ? src[il ? 4 * i : i] : make_float2(0.0f, 0.0f);
     }
   }
 }
 template <int W>
 __device__ __forceinline__ void row_store(const RowLayout<W / 2>& x, float2* __restrict__ dst, int t, bool act,
-                                          int cb) {
+                                          int cb, bool il) {
   using G = RowGeo<W>;
   if (act) {
 #pragma unroll
     for (int q = 0; q < G::E; ++q) {
       const int i = t + q * G::T;
-      if (i < cb) dst[kSpecColStride * i] = x(i);
+      if (i < cb) dst[il ? 4 * i : i] = x(i);
     }
   }
 }
@@ -248,8 +248,8 @@ __device__ __forceinline__ void r2c_post(const RowLayout<W / 2>& x, int t, bool 
 // block writes each group as one contiguous run (4 rows x the band's columns), thread e taking row
 // e % 4, column e / 4.  s_rows[r] is row r's start in the plane (nullptr for a row beyond H).
 template <int W>
-__device__ __forceinline__ bool rows_grouped() {
-  return (blockDim.x / RowGeo<W>::T) % 4 == 0;
+__device__ __forceinline__ bool rows_grouped(bool il) {
+  return il && (blockDim.x / RowGeo<W>::T) % 4 == 0;
 }
 template <int W>
 __device__ __forceinline__ void rows_store_grouped(float2* const* s_rows, int cb) {
@@ -260,14 +260,14 @@ __device__ __forceinline__ void rows_store_grouped(float2* const* s_rows, int cb
     for (int e = threadIdx.x; e < 4 * cb; e += blockDim.x) {
       const int rr = e & 3, i = e >> 2;
       float2* p = s_rows[4 * g + rr];
-      if (p) p[kSpecColStride * i] = smem[(4 * g + rr) * G::PITCH + i + (i >> 4)];
+      if (p) p[4 * i] = smem[(4 * g + rr) * G::PITCH + i + (i >> 4)];
     }
 }
 // spectrum row (global) -> real values (times M) in shared memory; ends synchronised
 template <int W>
 __device__ __forceinline__ void row_spec_to_real(const RowLayout<W / 2>& x, const float2* src, int t, bool act,
-                                                 int cb = W / 2) {
-  row_load<W>(x, src, t, act, cb);   // (a block-cooperative load measured slower: K6 49 -> 72 us)
+                                                 bool il, int cb = W / 2) {
+  row_load<W>(x, src, t, act, cb, il);   // (a block-cooperative load measured slower: K6 49 -> 72 us)
   __syncthreads();
   c2r_pre<W>(x, t, act);
   __syncthreads();
@@ -276,18 +276,18 @@ __device__ __forceinline__ void row_spec_to_real(const RowLayout<W / 2>& x, cons
 // real values in shared memory -> spectrum row (global); starts with a barrier
 template <int W>
 __device__ __forceinline__ void row_real_to_spec(const RowLayout<W / 2>& x, float2* dst, int t, bool act,
-                                                 int cb = W / 2) {
+                                                 bool il, int cb = W / 2) {
   __syncthreads();
   fft_inplace<W / 2, false>(x, t, act);
   r2c_post<W>(x, t, act);
-  if (rows_grouped<W>()) {
+  if (rows_grouped<W>(il)) {
     __shared__ float2* s_rows[kRowBlock];
     if (t == 0) s_rows[threadIdx.x / RowGeo<W>::T] = act ? dst : nullptr;
     __syncthreads();
     rows_store_grouped<W>(s_rows, cb);
   } else {
     __syncthreads();
-    row_store<W>(x, dst, t, act, cb);
+    row_store<W>(x, dst, t, act, cb, il);
   }
   __syncthreads();
 }
@@ -318,7 +318,8 @@ __global__ void __launch_bounds__(kRowBlock) k_row_r2c(const float* __restrict__
         x(t + q * G::T) = z;
       }
     }
-    row_real_to_spec<W>(x, out + v * out_vs + spec_row_off(row, G::M), t, act);
+    const bool il = spec_interleaved(H);
+    row_real_to_spec<W>(x, out + v * out_vs + spec_row_off(row, G::M, il), t, act, il);
   }
 }
 
@@ -338,7 +339,8 @@ __global__ void __launch_bounds__(kRowBlock) k_row_c2r(const float2* __restrict_
     const int v = it / per_view;
     const int row = (it % per_view) * G::ROWS + r;
     const bool act = row < H;
-    row_spec_to_real<W>(x, in + v * in_vs + spec_row_off(row, G::M), t, act);
+    const bool il = spec_interleaved(H);
+    row_spec_to_real<W>(x, in + v * in_vs + spec_row_off(row, G::M, il), t, act, il);
     float2* dst = reinterpret_cast<float2*>(out + v * out_vs + size_t(row) * W);
     if (act) {
 #pragma unroll
@@ -467,7 +469,7 @@ __device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ i
     }
   }
   if (done == 0) {
-    row_real_to_spec<W>(x, spec_plane(d, j + 1) + spec_row_off(row, G::M), t, act, d.cb);
+    row_real_to_spec<W>(x, spec_plane(d, j + 1) + spec_row_off(row, G::M, spec_interleaved(d.H)), t, act, spec_interleaved(d.H), d.cb);
     block_sum_store<2, FP64>(acc, partv_of(d, it) + SLOT_KL);
   }
   if (arrive_last(d.ctrl, d.n_rv_items)) ctrl_sgp_begin<FP64>(d);
@@ -500,7 +502,7 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
     const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
-    row_spec_to_real<W>(x, spec_plane(d, 0) + spec_row_off(row, G::M), t, act, d.cb);
+    row_spec_to_real<W>(x, spec_plane(d, 0) + spec_row_off(row, G::M, spec_interleaved(d.H)), t, act, spec_interleaved(d.H), d.cb);
     KSum acc[4];
     if (act) {
       float* f = d.f[ke & 1];
@@ -612,7 +614,7 @@ __device__ __forceinline__ void b_sgp_y(const ImgDesc* __restrict__ imgs,
         }
       }
     }
-    row_real_to_spec<W>(x, spec_plane(d, 0) + spec_row_off(row, G::M), t, act, d.cb);
+    row_real_to_spec<W>(x, spec_plane(d, 0) + spec_row_off(row, G::M, spec_interleaved(d.H)), t, act, spec_interleaved(d.H), d.cb);
     block_sum_store<1, FP64>(acc, part_of(d, it) + SLOT_GTD);
   }
 }
@@ -676,7 +678,7 @@ __device__ __forceinline__ void b_sgp_ad_armijo(const ImgDesc* __restrict__ imgs
 #pragma unroll
   for (int l = 1; l < kArmMain; ++l) lam[l] = lam[l - 1] * th;
   KSum acc[kArmMain];
-  row_spec_to_real<W>(x, spec_plane(d, j + 1) + spec_row_off(row, G::M), t, act, d.cb);
+  row_spec_to_real<W>(x, spec_plane(d, j + 1) + spec_row_off(row, G::M, spec_interleaved(d.H)), t, act, spec_interleaved(d.H), d.cb);
   if (act) {
     const float* uj = d.u + size_t(j) * d.P;
     float* adj = d.Ad + size_t(j) * d.P;
@@ -782,9 +784,9 @@ __device__ __forceinline__ void b_rl_update(const ImgDesc* __restrict__ imgs,
     const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
-    float2* sp = spec_plane(d, 0) + spec_row_off(row, G::M);
+    float2* sp = spec_plane(d, 0) + spec_row_off(row, G::M, spec_interleaved(d.H));
     const bool osem = wview >= 0;
-    if (hv) row_spec_to_real<W>(x, osem ? spec_plane(d, wview + 1) + spec_row_off(row, G::M) : sp, t, act, d.cb);
+    if (hv) row_spec_to_real<W>(x, osem ? spec_plane(d, wview + 1) + spec_row_off(row, G::M, spec_interleaved(d.H)) : sp, t, act, spec_interleaved(d.H), d.cb);
     KSum acc[1];
     if (act) {
       const float* fo = d.f[k & 1];
@@ -809,7 +811,7 @@ __device__ __forceinline__ void b_rl_update(const ImgDesc* __restrict__ imgs,
         x(t + q * G::T) = f;
       }
     }
-    row_real_to_spec<W>(x, sp, t, act, d.cb);
+    row_real_to_spec<W>(x, sp, t, act, spec_interleaved(d.H), d.cb);
     block_sum_store<1, FP64>(acc, part_of(d, it) + SLOT_RHO);
   }
 }
@@ -841,8 +843,8 @@ __device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
   const bool act = row < d.H;
   const size_t off = size_t(row) * G::M;
   KSum acc[1];
-  float2* sp = spec_plane(d, j + 1) + spec_row_off(row, G::M);
-  row_spec_to_real<W>(x, sp, t, act, d.cb);
+  float2* sp = spec_plane(d, j + 1) + spec_row_off(row, G::M, spec_interleaved(d.H));
+  row_spec_to_real<W>(x, sp, t, act, spec_interleaved(d.H), d.cb);
   if (act) {
     float* uj = d.u + size_t(j) * d.P;
     const float* gj = d.g + size_t(j) * d.P;
@@ -858,7 +860,7 @@ __device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
       x(t + q * G::T) = rm;
     }
   }
-  row_real_to_spec<W>(x, sp, t, act, d.cb);
+  row_real_to_spec<W>(x, sp, t, act, spec_interleaved(d.H), d.cb);
   if (write_u == 2) {
     if (arrive_last(d.ctrl, d.n_row_items)) osem_tick(d.ctrl, 1);
     return;
@@ -889,7 +891,7 @@ __device__ __forceinline__ void b_rl_step_minmax(const ImgDesc* __restrict__ img
     const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
-    row_spec_to_real<W>(x, spec_plane(d, 0) + spec_row_off(row, G::M), t, act, d.cb);
+    row_spec_to_real<W>(x, spec_plane(d, 0) + spec_row_off(row, G::M, spec_interleaved(d.H)), t, act, spec_interleaved(d.H), d.cb);
     float mn = f_inf(), mx = 0.0f;
     if (act) {
       const float* f = d.f[d.ctrl->k & 1];
