@@ -28,6 +28,10 @@ CASES = [
     (32, 2048, 1, "center", False),
     (64, 64, 1, "center", True),
     (192, 192, 2, "center", True),
+    # planes of 1024 or more rows store the spectrum interleaved by groups of 4 rows
+    (1024, 192, 2, "corner", True),
+    (1536, 384, 2, "center", True),
+    (2048, 96, 1, "center", True),
 ]
 
 
