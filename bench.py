@@ -150,19 +150,48 @@ def make_scene(args, rank):
     return scenes.galaxy_scene(seed=args.seed + rank, N=args.N)
 
 
-def cpu_baseline(sc, iters=2):
-    """The FP64 oracle as it stands, timed on this host on a bounded sample of the workload."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_iteration_rate(sc, n_lo, n_hi, workers=None):
+    """The FP64 oracle as it stands, timed per SGP iteration on this host: the difference of two
+    runs from the same start (n_lo and n_hi fixed iterations) divided by n_hi - n_lo, so the
+    set-up of a run (the L1/L2 RL step, the first KL) is excluded.  workers: FFT threads (None:
+    numpy's single-threaded FFT).  Returns (iterations per second, seconds spent)."""
     from oracle import sgp_oracle as O
-    t0 = time.perf_counter()
     prob = O.Problem(sc.psfs.astype(np.float32).astype(np.float64), sc.g.astype(np.float32).astype(np.float64),
                      sc.b.astype(np.float64))
-    t1 = time.perf_counter()
-    res = O.sgp(prob, stop=O.StopRule("fixed", max_iter=iters))
-    t2 = time.perf_counter()
-    return {"value": res.iters / (t2 - t1), "unit": "iter/s", "cores": 1, "kind": "oracle",
-            "sample": f"{iters} SGP iterations (incl. the L1/L2 set-up RL step) of the {sc.g.shape[1]}x"
-                      f"{sc.g.shape[2]} workload, FP64 numpy oracle, single thread (pocketfft); problem "
-                      f"set-up {t1 - t0:.2f} s excluded"}
+    O.set_fft_workers(workers)
+    try:
+        t0 = time.perf_counter()
+        O.sgp(prob, stop=O.StopRule("fixed", max_iter=n_lo))
+        t1 = time.perf_counter()
+        O.sgp(prob, stop=O.StopRule("fixed", max_iter=n_hi))
+        t2 = time.perf_counter()
+    finally:
+        O.set_fft_workers(None)
+    per_it = max(((t2 - t1) - (t1 - t0)) / (n_hi - n_lo), 1e-9)
+    return 1.0 / per_it, t2 - t0
+
+
+def cpu_baseline(sc):
+    """Bounded sample of the workload on the host: 1 and 3 oracle iterations (difference = 2
+    iterations without set-up), on one core and with the FFTs on every core of this process."""
+    N = sc.g.shape[1]
+    one, t_one = oracle_iteration_rate(sc, 1, 3)
+    cores = host_cores()
+    many, t_many = oracle_iteration_rate(sc, 1, 3, workers=cores)
+    return {"value": many, "unit": "iter/s", "cores": cores, "kind": "oracle",
+            "sample": f"2 SGP iterations of the {N}x{N} workload (runs of 1 and 3 iterations from the constant "
+                      f"start, differenced: the set-up RL step and first KL excluded); FP64 numpy oracle with its "
+                      f"FFT primitive on {cores} threads (scipy.fft workers), other steps single-threaded numpy; "
+                      f"{t_many:.1f} s",
+            "single_core": {"value": one, "unit": "iter/s", "cores": 1,
+                            "sample": f"the same with numpy.fft on one thread; {t_one:.1f} s"}}
 
 
 def run_reference(args):
@@ -170,26 +199,22 @@ def run_reference(args):
     if rank != 0:
         return 0
     sc = make_scene(args, 0)
-    from oracle import sgp_oracle as O
-    prob = O.Problem(sc.psfs.astype(np.float32).astype(np.float64), sc.g.astype(np.float32).astype(np.float64),
-                     sc.b.astype(np.float64))
-    f = prob.initial()
-    # one step = one SGP iteration of the oracle (bounded sample of the workload)
-    for _ in range(args.warmup):
-        O.sgp(prob, f0=f, stop=O.StopRule("fixed", max_iter=1))
-    t0 = time.perf_counter()
-    its = 0
-    for _ in range(args.steps):
-        its += O.sgp(prob, f0=f, stop=O.StopRule("fixed", max_iter=1)).iters
-    dt = time.perf_counter() - t0
-    v = its / dt
+    cores = host_cores()
+    # the steps are oracle iterations: runs of W and W + K iterations from the same start,
+    # differenced, so K timed iterations without the set-up (W >= 1 untimed ones before them)
+    w = max(args.warmup, 1)
+    v, spent = oracle_iteration_rate(sc, w, w + args.steps, workers=cores)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"galaxy {args.N}x{args.N} SGP, one iteration per step",
-                                            "N": args.N},
-            "cpu_baseline": {"value": v, "unit": "iter/s", "cores": 1, "kind": "oracle",
-                             "sample": "one SGP iteration (with the L1/L2 set-up RL step) per step"},
+            "data": "synthetic",
+            "config": {"workload": f"galaxy+stars {args.N}x{args.N}, Airy PSF (pupil N/8), b=50, Poisson, seed "
+                                   f"{args.seed}; SGP iterations of the FP64 oracle from the constant start",
+                       "N": args.N, "p": 1, "parallelism": "single"},
+            "cpu_baseline": {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} SGP iterations (runs of {w} and {w + args.steps} iterations "
+                                       f"differenced: set-up excluded), FFT primitive on {cores} threads; "
+                                       f"{spent:.1f} s"},
             "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0

@@ -50,7 +50,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "prepare_psf", "conv_periodic", "corr_periodic", "Problem", "SGPParams", "StopRule",
+    "prepare_psf", "set_fft_workers", "conv_periodic", "corr_periodic", "Problem", "SGPParams", "StopRule",
     "sgp", "rl", "osem", "bb_steplengths", "choose_alpha", "adaptive_bounds",
     "flux_projection", "kl_terms", "mosaic_axis", "mosaic_split", "mosaic_stitch", "mosaic",
 ]
@@ -80,14 +80,40 @@ def prepare_psf(psf, origin: str = "center") -> np.ndarray:
     return K
 
 
+_FFT_WORKERS = None   # None: numpy.fft (one thread); n: scipy.fft with n worker threads
+
+
+def set_fft_workers(n: int | None) -> None:
+    """Run the FFT primitive of the two convolutions below on n host threads (scipy.fft, the same
+    pocketfft transform as numpy.fft, split over its rows and columns), or on one thread through
+    numpy.fft (None, the default).  Only the library primitive changes; every other step of the
+    oracle stays single-threaded numpy."""
+    global _FFT_WORKERS
+    _FFT_WORKERS = None if n is None or n <= 1 else int(n)
+
+
+def _fft2(x):
+    if _FFT_WORKERS is None:
+        return np.fft.fft2(x)
+    import scipy.fft
+    return scipy.fft.fft2(x, workers=_FFT_WORKERS)
+
+
+def _ifft2(x):
+    if _FFT_WORKERS is None:
+        return np.fft.ifft2(x)
+    import scipy.fft
+    return scipy.fft.ifft2(x, workers=_FFT_WORKERS)
+
+
 def conv_periodic(f: np.ndarray, K: np.ndarray) -> np.ndarray:
     """(K * f)(m) = sum_n K(m - n) f(n), indices modulo the array shape (FFT as a primitive)."""
-    return np.real(np.fft.ifft2(np.fft.fft2(K) * np.fft.fft2(f)))
+    return np.real(_ifft2(_fft2(K) * _fft2(f)))
 
 
 def corr_periodic(y: np.ndarray, K: np.ndarray) -> np.ndarray:
     """(K (x) y)(n) = sum_m K(m - n) y(m): the transpose of conv_periodic for real K."""
-    return np.real(np.fft.ifft2(np.conj(np.fft.fft2(K)) * np.fft.fft2(y)))
+    return np.real(_ifft2(np.conj(_fft2(K)) * _fft2(y)))
 
 
 def kl_terms(g: np.ndarray, u: np.ndarray) -> np.ndarray:

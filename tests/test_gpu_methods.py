@@ -2,6 +2,9 @@
 
 Tolerances (FP32 GPU vs FP64 oracle): after 200 iterations the KL value within 1e-5 relative and
 the reconstruction within 1e-3 relative l2; step-length and line-search decisions identical."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -62,16 +65,24 @@ def test_sgp_parity_within_horizon_stars_256(gpu, stars256):
 
 
 def test_sgp_200_iterations_stars_256(gpu, stars256):
-    """200 iterations: past the chaotic horizon the GPU must descend as far as the oracle does."""
+    """200 iterations: past the chaotic horizon the KL of the FP64 oracle itself moves by up to
+    4.1 % when the data move by 1e-7 (tests/golden/sgp_horizon.json, eight perturbed oracle runs),
+    so the GPU's KL must lie inside the envelope of those nine oracle runs, widened by a tenth of
+    their spread: a descent that stops 1 % short of the worst oracle run fails."""
     sc = stars256
+    with open(os.path.join(os.path.dirname(__file__), "golden", "sgp_horizon.json")) as fh:
+        hz = json.load(fh)
     orc = oracle_problem(sc)
     ref = O.sgp(orc, stop=O.StopRule("fixed", max_iter=200))
+    assert abs(ref.J - hz["J_ref"]) <= 1e-9 * ref.J          # the stored envelope is this run's
+    Js = [hz["J_ref"]] + [r["J"] for r in hz["runs"]]
+    margin = 0.1 * hz["max_rel_J"]
     prob = gpu_problem(gpu, sc)
     prob.sgp_iterate(200)
     info = prob.info()
     f = host(prob.get_f())
     assert info.k == 200 and np.all(f >= 0)
-    assert abs(info.J - ref.J) <= 5e-2 * ref.J
+    assert min(Js) * (1 - margin) <= info.J <= max(Js) * (1 + margin), (info.J, min(Js), max(Js))
     tr = prob.trace()
     assert np.all(np.diff(tr[:, 1]) <= 1e-9 * tr[0, 1])     # Armijo: monotone J
 
