@@ -255,8 +255,11 @@ SGP_API sgp_status sgp_set_tile(sgp_ctx* ctx, int rows_per_item);
  *     is needed between calls.  All calls share it: calls whose GPU work overlaps (other streams,
  *     other host threads) race and must be serialised by the caller.
  *   - The first call on a device looks up the address of that array (and initialises the library
- *     on the device); make that first call before any stream capture.
- *   - Synchronises `stream` once (to read the PSF sum).  Allocates nothing. */
+ *     on the device); concurrent first calls from several host threads are serialised.
+ *   - Every call synchronises `stream` once (to read the PSF sum) and copies small tables from
+ *     host memory, so it must never be called while `stream` is being captured into a CUDA
+ *     graph: it then returns SGP_ERR_STATE without doing anything.
+ *   - Allocates nothing.  SGP_ERR_ARG for a device ordinal of 64 or more. */
 SGP_API sgp_status sgp_convolve_noalloc(const float* psf, const float* f, float* out, int H, int W,
                                         int psf_origin, int transpose, void* stream);
 
@@ -287,6 +290,27 @@ SGP_API sgp_status sgp_mosaic_split(const sgp_mosaic* m, int p, const float* g, 
 
 /* recs: device (ny nx) x ext_h x ext_w reconstructions -> f: device H x W mosaic.  Asynchronous. */
 SGP_API sgp_status sgp_mosaic_stitch(const sgp_mosaic* m, const float* recs, float* f, void* stream);
+
+/* Verification aid for the precision of the library's sums (the KL value J_0 of Eq. KL, the
+ * numerators and denominators of the scaled BB rules Eq. BB1 / BB2, the Armijo differences of
+ * Algorithm 1, step 5).  For i < n it computes the pixel term t_i of one kind with the same device
+ * functions the iteration passes use, writes it to terms[i] (device float32, may be NULL) and sums
+ * the t_i with the passes' reduction: per-thread accumulation over 32 terms, warp and block sums,
+ * a fixed-order sum of the block partials.  reduce_fp64 = 1 selects the mixed variant (error-free
+ * FP32 two-sum accumulation and FP32 pairs, as with sgp_params.reduce_fp64 = 1), 0 plain FP32.
+ *   kind SGP_SUM_VALUES: t = a (any float32 values)
+ *        SGP_SUM_KL:     t = g ln(g/u) + u - g with g = a, u = b (u = A f + background)
+ *        SGP_SUM_ARMIJO: t = lambda A d - g ln(1 + lambda A d / u) with g = a, u = b, A d = c
+ *        SGP_SUM_BB0..3: s^2 / D^2, s z / D, s z D, z^2 D^2 with s = a, z = b, D = c (0 where D <= 0)
+ * a, b, c: device float32 arrays of n values (b, c unused by the kinds that do not name them).
+ * out: host, receives the sum as FP64.  workspace: device, 256-byte aligned, at least
+ * sgp_sum_terms_workspace_bytes(n) bytes, owned by the caller.  Synchronises `stream`.
+ * Errors: SGP_ERR_ARG, SGP_ERR_WORKSPACE, SGP_ERR_SIZE_UNSUPPORTED, SGP_ERR_CUDA. */
+enum { SGP_SUM_VALUES = 0, SGP_SUM_KL = 1, SGP_SUM_ARMIJO = 2, SGP_SUM_BB0 = 3, SGP_SUM_BB3 = 6 };
+SGP_API size_t sgp_sum_terms_workspace_bytes(size_t n);
+SGP_API sgp_status sgp_sum_terms(int kind, int reduce_fp64, const float* a, const float* b, const float* c,
+                                 size_t n, double lambda, float* terms, double* out, void* workspace,
+                                 size_t ws_bytes, void* stream);
 
 /* Release the context (not the workspace). */
 SGP_API sgp_status sgp_destroy(sgp_ctx* ctx);

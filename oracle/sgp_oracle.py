@@ -50,7 +50,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "prepare_psf", "set_fft_workers", "conv_periodic", "corr_periodic", "Problem", "SGPParams", "StopRule",
+    "prepare_psf", "set_fft_workers", "set_fft_single_precision", "conv_periodic", "corr_periodic", "Problem", "SGPParams", "StopRule",
     "sgp", "rl", "osem", "bb_steplengths", "choose_alpha", "adaptive_bounds",
     "flux_projection", "kl_terms", "mosaic_axis", "mosaic_split", "mosaic_stitch", "mosaic",
 ]
@@ -81,6 +81,7 @@ def prepare_psf(psf, origin: str = "center") -> np.ndarray:
 
 
 _FFT_WORKERS = None   # None: numpy.fft (one thread); n: scipy.fft with n worker threads
+_FFT_SINGLE = False   # True: the transforms in single precision (inputs rounded to float32)
 
 
 def set_fft_workers(n: int | None) -> None:
@@ -92,7 +93,18 @@ def set_fft_workers(n: int | None) -> None:
     _FFT_WORKERS = None if n is None or n <= 1 else int(n)
 
 
+def set_fft_single_precision(on: bool) -> None:
+    """Evaluate the two convolutions below with single-precision transforms (inputs rounded to
+    float32, numpy.fft in complex64, results returned as float64), or in double precision (the
+    default).  This models the rounding of FP32 transforms alone, for bounding how far an FP32
+    implementation of the method can drift from the FP64 oracle; every other step stays FP64."""
+    global _FFT_SINGLE
+    _FFT_SINGLE = bool(on)
+
+
 def _fft2(x):
+    if _FFT_SINGLE:
+        return np.fft.fft2(np.asarray(x).astype(np.complex64))
     if _FFT_WORKERS is None:
         return np.fft.fft2(x)
     import scipy.fft
@@ -100,6 +112,8 @@ def _fft2(x):
 
 
 def _ifft2(x):
+    if _FFT_SINGLE:
+        return np.fft.ifft2(np.asarray(x).astype(np.complex64))
     if _FFT_WORKERS is None:
         return np.fft.ifft2(x)
     import scipy.fft
@@ -108,12 +122,12 @@ def _ifft2(x):
 
 def conv_periodic(f: np.ndarray, K: np.ndarray) -> np.ndarray:
     """(K * f)(m) = sum_n K(m - n) f(n), indices modulo the array shape (FFT as a primitive)."""
-    return np.real(_ifft2(_fft2(K) * _fft2(f)))
+    return np.real(_ifft2(_fft2(K) * _fft2(f))).astype(np.float64)
 
 
 def corr_periodic(y: np.ndarray, K: np.ndarray) -> np.ndarray:
     """(K (x) y)(n) = sum_m K(m - n) y(m): the transpose of conv_periodic for real K."""
-    return np.real(_ifft2(np.conj(_fft2(K)) * _fft2(y)))
+    return np.real(_ifft2(np.conj(_fft2(K)) * _fft2(y))).astype(np.float64)
 
 
 def kl_terms(g: np.ndarray, u: np.ndarray) -> np.ndarray:

@@ -155,10 +155,11 @@ __device__ inline void sgp_accept(const ImgDesc& d, CtrlState* c, int nb, double
   c->arm_nl = nb == 0 ? 1 : (nb == 1 ? 2 : kArmMain);
   const int kn = c->k + 1;
   trace_push(d, c, kn, c->J_pred, c->alpha, lam, nb, c->branch, c->gTd);
-  bool stop = kn >= c->max_iter;
-  if (c->stop_kind == STOP_CONVERGENCE && fabs(c->J_pred - c->J) <= c->tol * c->J) stop = true;
+  bool rule = false;                  // the stop rule itself fired (not only the iteration cap)
+  if (c->stop_kind == STOP_CONVERGENCE && fabs(c->J_pred - c->J) <= c->tol * c->J) rule = true;
   if ((c->stop_kind == STOP_DISCREPANCY || c->stop_kind == STOP_LANDED) && 2.0 * c->J_pred * c->inv_pS <= c->eta) {
-    stop = true;
+    rule = true;
+    c->capped = 0;
     // landed stop: shorten this step so that the discrepancy ends in [eta (1 - tol), eta]
     const double Jt = c->eta * (1.0 - 0.5 * c->tol) / (2.0 * c->inv_pS);
     if (c->stop_kind == STOP_LANDED && c->J_pred < Jt && c->J > Jt) {
@@ -168,6 +169,8 @@ __device__ inline void sgp_accept(const ImgDesc& d, CtrlState* c, int nb, double
       return;                         // the landing passes decide lambda and set done
     }
   }
+  const bool stop = rule || kn >= c->max_iter;
+  c->capped = stop && !rule;
   if (stop) c->done = 1;
 }
 
@@ -280,9 +283,11 @@ __device__ void rl_decide(const ImgDesc& d, CtrlState* c, double kl, double rr) 
     if (c->k >= 1 && rho > c->rho_prev) { c->done = 2; c->result_prev = 1; c->have_v = 0; return; }
     c->rho_prev = rho;
   }
-  bool stop = c->k >= c->max_iter;
-  if (updated && c->stop_kind == STOP_CONVERGENCE && fabs(c->J - c->J_prev) <= c->tol * c->J_prev) stop = true;
-  if (c->stop_kind == STOP_DISCREPANCY && 2.0 * c->J * c->inv_pS <= c->eta) stop = true;
+  bool rule = false;                  // the stop rule itself fired (not only the iteration cap)
+  if (updated && c->stop_kind == STOP_CONVERGENCE && fabs(c->J - c->J_prev) <= c->tol * c->J_prev) rule = true;
+  if (c->stop_kind == STOP_DISCREPANCY && 2.0 * c->J * c->inv_pS <= c->eta) rule = true;
+  const bool stop = rule || c->k >= c->max_iter;
+  c->capped = stop && !rule;
   if (stop) { c->done = 2; c->have_v = 0; }
 }
 // OSEM bookkeeping (Algorithm 2), by one thread: an update h <- w_j h A_j^T r_j was applied when v

@@ -39,6 +39,7 @@ __global__ void k_ctrl_arm(const ImgDesc* __restrict__ imgs, int n, int kind, in
   CtrlState* c = imgs[i].ctrl;
   if (c->status != 0) return;          // a failed problem stays stopped
   c->stop_kind = kind;
+  c->capped = 0;
   c->max_iter = relative ? c->k + n_iter : n_iter;
   c->tol = tol;
   c->eta = eta;
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(kRowBlock) k_flux_pass(const ImgDesc* __restri
   const size_t base = size_t(row0) * d.W, n = size_t(rows) * d.W;
   double* out = part_of(d, it);
   if (mode == 0) {
-    KSum acc[3];   // sum x (D > 0), sum D (D > 0), sum x (D = 0)
+    Acc<FP64> acc[3];   // sum x (D > 0), sum D (D > 0), sum x (D = 0)
     float tmin = f_inf(), tmax = -f_inf();
     for (size_t q = threadIdx.x; q < n; q += blockDim.x) {
       float x, D;
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(kRowBlock) k_flux_pass(const ImgDesc* __restri
       out[SLOT_MAX] = b;
     }
   } else if (mode == 1) {
-    KSum acc[kFluxCand];
+    Acc<FP64> acc[kFluxCand];
     float mu[kFluxCand];
     const double lo = c->mu_lo, hi = c->mu_hi;
 #pragma unroll
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(kRowBlock) k_flux_pass(const ImgDesc* __restri
     }
     block_sum_store<kFluxCand, FP64>(acc, out + SLOT_ARMX);
   } else {
-    KSum acc[2];   // sum x, sum D over the pixels with t > mu_lo (active just above mu_lo)
+    Acc<FP64> acc[2];   // sum x, sum D over the pixels with t > mu_lo (active just above mu_lo)
     const float a = float(c->mu_lo);
     for (size_t q = threadIdx.x; q < n; q += blockDim.x) {
       float x, D;
@@ -250,9 +251,9 @@ __global__ void __launch_bounds__(256) k_stats_partial(const float* __restrict__
   const float* a = x + size_t(plane) * P;
   const float* bj = b ? b + size_t(plane) * P : nullptr;
   const float bc = bconst ? bconst[plane] : 0.0f;
-  // per thread: compensated FP32 sums (FP64 arithmetic is slow on this GPU) and FP32 max / min /
-  // counts (exact: a thread sees fewer than 2^24 pixels); FP64 from the block level up
-  KSum k0, k1;
+  // per thread: error-free FP32 two-sum accumulation (FP64 arithmetic is slow on this GPU) and FP32
+  // max / min / counts (exact: a thread sees fewer than 2^24 pixels); FP64 from the block level up
+  Acc<true> k0, k1;
   float m1 = mode ? 0.0f : -INFINITY, m2 = mode ? 0.0f : INFINITY, n2 = 0.0f, n3 = 0.0f;
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < P; i += size_t(gridDim.x) * blockDim.x) {
     const float v = a[i];
@@ -264,8 +265,8 @@ __global__ void __launch_bounds__(256) k_stats_partial(const float* __restrict__
       k0.add(v); k1.add(bj ? bj[i] : bc); n2 += 1.0f;
     }
   }
-  const double s0 = double(k0.s) - double(k0.c), s3 = n3;
-  const double s1 = mode ? double(k1.s) - double(k1.c) : double(m1), s2 = mode ? double(n2) : double(m2);
+  const double s0 = double(k0.hi) + double(k0.lo), s3 = n3;
+  const double s1 = mode ? double(k1.hi) + double(k1.lo) : double(m1), s2 = mode ? double(n2) : double(m2);
   __shared__ double r[4][256];
   r[0][threadIdx.x] = s0; r[1][threadIdx.x] = s1; r[2][threadIdx.x] = s2; r[3][threadIdx.x] = s3;
   __syncthreads();

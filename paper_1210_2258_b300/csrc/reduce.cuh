@@ -1,10 +1,14 @@
 // Reductions of the row passes and of the controllers.
 //
-// Per thread: compensated FP32 (Kahan) accumulation over the thread's pixels.  Above the thread,
-// the "mixed" variant carries every sum as an unevaluated pair of FP32 values (hi + lo, combined
-// with the error-free two-sum of Knuth), i.e. about 48 significand bits, and converts to FP64
-// only for the controller's scalar logic: FP64 arithmetic is slow on this part, FP32 is not.
-// The plain-FP32 variant sums single FP32 values throughout.
+// Per thread, the "mixed" variant (FP64 = true) accumulates its pixel terms error-free: each term
+// is added to a running FP32 value hi with Knuth's two-sum, which also yields the exact rounding
+// error of that addition, and the errors are summed in a second FP32 value lo.  The pair hi + lo
+// is the sum to about (n u)^2 of the sum of |terms| (u = 2^-24, n <= 48 terms a thread), far below
+// the 1e-12 an FP64 sum of the same FP32 terms carries.  Above the thread every sum travels as an
+// unevaluated pair of FP32 values (hi + lo, combined with the same two-sum: about 48 significand
+// bits) and is converted to FP64 only for the controller's scalar logic: FP64 arithmetic is slow
+// on this part, FP32 is not.  The plain-FP32 variant (FP64 = false) sums single FP32 values from
+// the thread up and takes the decisions in FP32.
 //
 // A block stores its NS sums as float2 (hi, lo) in consecutive 8-byte slots of its item's
 // partial-sum record; the controller of a problem adds the records of all its items in a fixed
@@ -16,19 +20,31 @@
 
 namespace sgp {
 
-struct KSum {
-  float s = 0.0f, c = 0.0f;   // value = s - c
-  __device__ __forceinline__ void add(float x) {
-    const float y = x - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-};
-
 // value hi + lo with |lo| <= ulp(hi)/2 after ff_add
 struct FF {
   float hi, lo;
+};
+
+// Per-thread accumulator of pixel terms (see the top of this file).
+template <bool FP64> struct Acc;
+template <> struct Acc<true> {
+  float hi = 0.0f, lo = 0.0f;   // value hi + lo
+  __device__ __forceinline__ void add(float x) {
+    const float s = hi + x;                          // two-sum: s + e = hi + x exactly
+    const float bv = s - hi;
+    const float e = (hi - (s - bv)) + (x - bv);
+    lo += e;
+    hi = s;
+  }
+  __device__ __forceinline__ FF pair() const {      // renormalised: |lo| <= ulp(hi)/2
+    const float s = hi + lo, bv = s - hi;
+    return FF{s, (hi - (s - bv)) + (lo - bv)};
+  }
+};
+template <> struct Acc<false> {
+  float hi = 0.0f;
+  __device__ __forceinline__ void add(float x) { hi += x; }
+  __device__ __forceinline__ FF pair() const { return FF{hi, 0.0f}; }
 };
 __device__ __forceinline__ FF ff_add(FF a, FF b) {
   const float s = a.hi + b.hi;                       // two-sum: s + e = a.hi + b.hi exactly
@@ -64,14 +80,14 @@ __device__ __forceinline__ FF slot_load(const double* slot) {
 
 // Sum NS per-thread values over the block; thread 0 stores them to out[0..NS).
 template <int NS, bool FP64>
-__device__ __forceinline__ void block_sum_store(const KSum (&loc)[NS], double* out) {
+__device__ __forceinline__ void block_sum_store(const Acc<FP64> (&loc)[NS], double* out) {
   __shared__ FF red[NS][kRowBlock / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     FF v;
-    if (FP64) v = ff_warp_sum(FF{loc[s].s, -loc[s].c});
-    else v = FF{warp_sum(loc[s].s - loc[s].c), 0.0f};
+    if (FP64) v = ff_warp_sum(loc[s].pair());
+    else v = FF{warp_sum(loc[s].pair().hi), 0.0f};
     if (lane == 0) red[s][wid] = v;
   }
   __syncthreads();

@@ -90,10 +90,22 @@ __device__ __forceinline__ float kl_ratio(float g, float u0, float& rm1) {
   }
   return dlt - g * logf(fdiv(u0, g));
 }
+// One Armijo pixel term J(f + lam d) - J(f) at a pixel with g > 0 and u0 = A f + b > 0, from
+// qb = A d / u0 and gm = u0 - g: (u0 - g) q + g phi(q), q = lam qb (+inf when u0 + lam A d <= 0).
+__device__ __forceinline__ float armijo_term(float lam, float qb, float gm, float g) {
+  const float q = lam * qb;                   // u0 + lam ad <= 0  <=>  q <= -1
+  return q <= -1.0f ? f_inf() : fmaf(gm, q, g * phi_t(q));
+}
+// The four pixel terms of the scaled BB sums (Eq. BB1, BB2) at a pixel with D > 0:
+// s^2 / D^2, s z / D, s z D, z^2 D^2.
+__device__ __forceinline__ void bb_terms(float s, float z, float D, float (&t)[4]) {
+  const float sd = s / D, zd = z * D;
+  t[0] = sd * sd; t[1] = sd * z; t[2] = s * zd; t[3] = zd * zd;
+}
 // Armijo pixel terms J(f + lam d) - J(f) for the step lengths lam[0..N) at one pixel, u0 = A f + b,
 // ad = A d; q = lam ad / u0 shares one division over the step lengths
-template <int N>
-__device__ __forceinline__ void armijo_add(KSum (&acc)[N], const float (&lam)[N], float g, float u0, float ad) {
+template <int N, class A>
+__device__ __forceinline__ void armijo_add(A (&acc)[N], const float (&lam)[N], float g, float u0, float ad) {
   if (g < 0.0f) return;                       // outside S
   if (g == 0.0f) {
 #pragma unroll
@@ -107,15 +119,12 @@ __device__ __forceinline__ void armijo_add(KSum (&acc)[N], const float (&lam)[N]
   }
   const float qb = fdiv(ad, u0), gm = u0 - g;
 #pragma unroll
-  for (int l = 0; l < N; ++l) {
-    const float q = lam[l] * qb;              // u0 + lam ad <= 0  <=>  q <= -1
-    acc[l].add(q <= -1.0f ? f_inf() : fmaf(gm, q, g * phi_t(q)));
-  }
+  for (int l = 0; l < N; ++l) acc[l].add(armijo_term(lam[l], qb, gm, g));
 }
 // the same for the step lengths lam0 th^l (GEOM) or lam0 + l th (arithmetic), l = 0..N-1, as
 // running products or sums (few registers)
-template <int N, bool GEOM>
-__device__ __forceinline__ void armijo_add_prog(KSum (&acc)[N], float lam0, float th, float g, float u0, float ad) {
+template <int N, bool GEOM, class A>
+__device__ __forceinline__ void armijo_add_prog(A (&acc)[N], float lam0, float th, float g, float u0, float ad) {
   if (g < 0.0f) return;
   float a;
   if (g == 0.0f) a = ad;                      // q = lam A d here
@@ -400,7 +409,7 @@ __device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ i
   const int row = item_row(item) + r;
   const bool act = row < d.H;
   const size_t off = size_t(row) * G::M;
-  KSum acc[2];
+  Acc<FP64> acc[2];
   const float lam = float(c->lambda);
   if (j == 0 && act) {
     float* fcur = d.f[ke & 1];
@@ -503,7 +512,7 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
     row_spec_to_real<W>(x, spec_plane(d, 0) + spec_row_off(row, G::M, spec_interleaved(d.H)), t, act, spec_interleaved(d.H), d.cb);
-    KSum acc[4];
+    Acc<FP64> acc[4];
     if (act) {
       float* f = d.f[ke & 1];
       const float* fp = d.f[(ke + 1) & 1];
@@ -547,13 +556,14 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
           const float2 fc = fcv[b], fo = fov[b], go = gov[b];
           const float sx = fc.x - fo.x, sy = fc.y - fo.y, zx = gr.x - go.x, zy = gr.y - go.y;
           const float Dx = w.x * clipf(fc.x, L1, L2), Dy = w.y * clipf(fc.y, L1, L2);
+          float tb[4];
           if (Dx > 0.0f) {
-            const float sd = sx / Dx, zd = zx * Dx;
-            acc[0].add(sd * sd); acc[1].add(sd * zx); acc[2].add(sx * zd); acc[3].add(zd * zd);
+            bb_terms(sx, zx, Dx, tb);
+            acc[0].add(tb[0]); acc[1].add(tb[1]); acc[2].add(tb[2]); acc[3].add(tb[3]);
           }
           if (Dy > 0.0f) {
-            const float sd = sy / Dy, zd = zy * Dy;
-            acc[0].add(sd * sd); acc[1].add(sd * zy); acc[2].add(sy * zd); acc[3].add(zd * zd);
+            bb_terms(sy, zy, Dy, tb);
+            acc[0].add(tb[0]); acc[1].add(tb[1]); acc[2].add(tb[2]); acc[3].add(tb[3]);
           }
         }
         }
@@ -589,7 +599,7 @@ __device__ __forceinline__ void b_sgp_y(const ImgDesc* __restrict__ imgs,
     const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
-    KSum acc[1];
+    Acc<FP64> acc[1];
     if (act) {
       const float* f = d.f[k & 1];
       const float* gr = d.grad[k & 1];
@@ -626,12 +636,12 @@ __global__ void __launch_bounds__(kRowBlock) k_sgp_y(const ImgDesc* __restrict__
 
 // K6 pixel loop for the first N step lengths (the other sums stay 0): stores A d, adds the Armijo
 // terms
-template <int W, int N>
-__device__ __forceinline__ void sgp_armijo_rows(const RowLayout<W / 2>& x, KSum (&acc)[kArmMain],
+template <int W, int N, class A>
+__device__ __forceinline__ void sgp_armijo_rows(const RowLayout<W / 2>& x, A (&acc)[kArmMain],
                                                 const float (&lam)[kArmMain], const float* uj, float* adj,
                                                 const float* gj, const ImgDesc& d, int j, size_t off, int t) {
   using G = RowGeo<W>;
-  KSum (&accN)[N] = reinterpret_cast<KSum (&)[N]>(acc);
+  A (&accN)[N] = reinterpret_cast<A (&)[N]>(acc);
   const float (&lamN)[N] = reinterpret_cast<const float (&)[N]>(lam);
   constexpr int B = batch_of<G::E, 4>();
 #pragma unroll 1
@@ -677,7 +687,7 @@ __device__ __forceinline__ void b_sgp_ad_armijo(const ImgDesc* __restrict__ imgs
   lam[0] = 1.0f;
 #pragma unroll
   for (int l = 1; l < kArmMain; ++l) lam[l] = lam[l - 1] * th;
-  KSum acc[kArmMain];
+  Acc<FP64> acc[kArmMain];
   row_spec_to_real<W>(x, spec_plane(d, j + 1) + spec_row_off(row, G::M, spec_interleaved(d.H)), t, act, spec_interleaved(d.H), d.cb);
   if (act) {
     const float* uj = d.u + size_t(j) * d.P;
@@ -728,7 +738,7 @@ __device__ __forceinline__ void b_sgp_lambda_scan(const ImgDesc* __restrict__ im
       const int nl = arm_count(c);
       for (int l = 0; l < nl; ++l) lam0 *= step;
     }
-    KSum acc[kArmExtra];
+    Acc<FP64> acc[kArmExtra];
     if (act) {
       for (int j = 0; j < d.p; ++j) {
         const float* uj = d.u + size_t(j) * d.P;
@@ -787,7 +797,7 @@ __device__ __forceinline__ void b_rl_update(const ImgDesc* __restrict__ imgs,
     float2* sp = spec_plane(d, 0) + spec_row_off(row, G::M, spec_interleaved(d.H));
     const bool osem = wview >= 0;
     if (hv) row_spec_to_real<W>(x, osem ? spec_plane(d, wview + 1) + spec_row_off(row, G::M, spec_interleaved(d.H)) : sp, t, act, spec_interleaved(d.H), d.cb);
-    KSum acc[1];
+    Acc<FP64> acc[1];
     if (act) {
       const float* fo = d.f[k & 1];
       float* fn = d.f[ke & 1];
@@ -842,7 +852,7 @@ __device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
   const int row = item_row(item) + r;
   const bool act = row < d.H;
   const size_t off = size_t(row) * G::M;
-  KSum acc[1];
+  Acc<FP64> acc[1];
   float2* sp = spec_plane(d, j + 1) + spec_row_off(row, G::M, spec_interleaved(d.H));
   row_spec_to_real<W>(x, sp, t, act, spec_interleaved(d.H), d.cb);
   if (act) {

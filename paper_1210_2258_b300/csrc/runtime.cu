@@ -17,6 +17,7 @@
 #include "mosaic.cuh"
 #include "registry.h"
 #include "state.cuh"
+#include "sumcheck.cuh"
 
 using namespace sgp;
 
@@ -798,10 +799,12 @@ sgp_status prepare(sgp_ctx* c, int mode) {
   int failed = 0, first = -1;
   for (int i = 0; i < c->n; ++i)
     if (c->h_ctrl[i].status) { ++failed; if (first < 0) first = i; }
+  // the context counts as prepared either way: the state (status, start) stays readable, and a
+  // later solve returns the failed problems' status at once, until new data or a new start
+  c->mode = mode;
   if (failed == c->n)
     return fail(sgp_status(c->h_ctrl[first].status), "set-up failed for problem " + std::to_string(first) +
                                                          " (no positive pixel after one RL step, or non-finite J)");
-  c->mode = mode;
   return SGP_OK;
 }
 
@@ -872,7 +875,8 @@ sgp_status run_until(sgp_ctx* c, bool sgp, const sgp_stop_rule* rule, int* iters
     const CtrlState& h = c->h_ctrl[i];
     if (iters) iters[i] = h.k - h.result_prev;
     if (h.status && res == SGP_OK) res = fail(sgp_status(h.status), "problem " + std::to_string(i) + " stopped with an error");
-    if (res == SGP_OK && h.done < 1) res = fail(SGP_ERR_TIMEOUT, "stop rule not reached");
+    if (res == SGP_OK && (h.done < 1 || (rule->kind != STOP_FIXED && h.capped)))
+      res = fail(SGP_ERR_TIMEOUT, "problem " + std::to_string(i) + ": stop rule not reached within max_iter");
   }
   return res;
 }
@@ -1373,7 +1377,7 @@ sgp_status sgp_get_info(sgp_ctx* c, int image, sgp_info* o) {
   memset(o, 0, sizeof(*o));
   o->k = h.k - h.result_prev;
   o->status = h.status;
-  o->stopped = h.done >= 1;
+  o->stopped = h.done >= 1 && !(h.capped && h.stop_kind != STOP_FIXED);
   o->trace_n = h.trace_n;
   o->J = h.J;
   o->D = 2.0 * h.J * h.inv_pS;
@@ -1633,6 +1637,44 @@ sgp_status sgp_mosaic_stitch(const sgp_mosaic* m, const float* recs, float* f, v
   return SGP_OK;
 }
 
+size_t sgp_sum_terms_workspace_bytes(size_t n) {
+  const size_t blocks = (n + size_t(kRowBlock) * kSumPerThread - 1) / (size_t(kRowBlock) * kSumPerThread);
+  return 2048 + std::max<size_t>(blocks, 1) * kPartStride * sizeof(double);
+}
+
+sgp_status sgp_sum_terms(int kind, int reduce_fp64, const float* a, const float* b, const float* c, size_t n,
+                         double lambda, float* terms, double* out, void* workspace, size_t ws_bytes, void* stream) {
+  if (!out || !a || n == 0) return fail(SGP_ERR_ARG, "out and a must be non-NULL and n positive");
+  if (kind < SGP_SUM_VALUES || kind > SGP_SUM_BB3) return fail(SGP_ERR_ARG, "unknown term kind");
+  if ((kind == SGP_SUM_KL || kind >= SGP_SUM_ARMIJO) && !b) return fail(SGP_ERR_ARG, "b is NULL");
+  if (kind >= SGP_SUM_ARMIJO && !c) return fail(SGP_ERR_ARG, "c is NULL");
+  const size_t per_block = size_t(kRowBlock) * kSumPerThread;
+  const size_t blocks = (n + per_block - 1) / per_block;
+  if (blocks > size_t(1) << 30) return fail(SGP_ERR_SIZE_UNSUPPORTED, "too many terms");
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || ws_bytes < sgp_sum_terms_workspace_bytes(n))
+    return fail(SGP_ERR_WORKSPACE, "workspace missing, misaligned or smaller than sgp_sum_terms_workspace_bytes(n)");
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  sgp_status st = ensure_device_ready(dev);
+  if (st) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(workspace);
+  CtrlState* cs = reinterpret_cast<CtrlState*>(w);
+  double* dout = reinterpret_cast<double*>(w + 1024);
+  double* part = reinterpret_cast<double*>(w + 2048);
+  static_assert(sizeof(CtrlState) <= 1024, "controller record larger than its slot");
+  CU(cudaMemsetAsync(cs, 0, sizeof(CtrlState), s));
+  int nb = int(blocks);
+  float lam = float(lambda);
+  void* args[] = {(void*)&kind, (void*)&a, (void*)&b, (void*)&c, (void*)&n, (void*)&lam, (void*)&terms,
+                  (void*)&part, (void*)&cs, (void*)&nb, (void*)&dout};
+  const void* fn = reduce_fp64 ? (const void*)&k_sum_terms<true> : (const void*)&k_sum_terms<false>;
+  if ((st = launch(fn, nb, kRowBlock, 0, s, args))) return st;
+  CU(cudaMemcpyAsync(out, dout, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  return SGP_OK;
+}
+
 sgp_status sgp_destroy(sgp_ctx* c) {
   if (!c) return SGP_OK;
   if (c->s) cudaStreamSynchronize(c->s);
@@ -1665,7 +1707,9 @@ constexpr size_t kNoAllocItemsOff = kNoAllocJobsOff + 64 * (sizeof(ColJob) / siz
 constexpr size_t kNoAllocFloats = kNoAllocItemsOff + 2 * 4096;
 
 static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
-float* g_noalloc_ptr[64] = {nullptr};
+constexpr int kNoAllocDevices = 64;
+float* g_noalloc_ptr[kNoAllocDevices] = {nullptr};   // device address of the array, per device
+std::mutex g_noalloc_mu;                              // serialises the per-device set-up
 
 }  // namespace
 
@@ -1677,16 +1721,26 @@ extern "C" sgp_status sgp_convolve_noalloc(const float* psf, const float* f, flo
   if (st) return st;
   if (size_t(H) * W > kNoAllocMaxPixels)
     return fail(SGP_ERR_SIZE_UNSUPPORTED, "sgp_convolve_noalloc supports at most 262144 pixels (e.g. 512 x 512)");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // the call synchronises the stream and copies from host memory, neither of which a capture allows
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CU(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(SGP_ERR_STATE, "sgp_convolve_noalloc must not be called while its stream is being captured");
   int dev = 0;
   CU(cudaGetDevice(&dev));
-  if ((st = ensure_device_ready(dev))) return st;
-  if (!g_noalloc_ptr[dev]) {   // once per device: the device address of the fixed scratch array
-    void* p = nullptr;
-    CU(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = static_cast<float*>(p);
+  if (dev < 0 || dev >= kNoAllocDevices) return fail(SGP_ERR_ARG, "device ordinal beyond the library's table (64)");
+  float* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if ((st = ensure_device_ready(dev))) return st;
+    if (!g_noalloc_ptr[dev]) {   // once per device: the device address of the fixed scratch array
+      void* p = nullptr;
+      CU(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_ptr[dev] = static_cast<float*>(p);
+    }
+    base = g_noalloc_ptr[dev];
   }
-  float* base = g_noalloc_ptr[dev];
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t P = size_t(H) * W;
   const int M = W / 2;
   float2* khat = reinterpret_cast<float2*>(base);
@@ -1733,23 +1787,22 @@ extern "C" sgp_status sgp_convolve_noalloc(const float* psf, const float* f, flo
   const float* psrc = psf;
   float2* sp1 = reinterpret_cast<float2*>(spec1);
   void* a1[] = {(void*)&psrc, (void*)&ivs, (void*)&sp1, (void*)&ovs, (void*)&Hh, (void*)&one, (void*)&clamp};
-  CU(cudaLaunchKernel(g_reg.row[ROP_R2C][0][si], dim3(per_view), dim3(kRowBlock), a1, g_reg.row_smem[si], s));
+  if ((st = launch(g_reg.row[ROP_R2C][0][si], per_view, kRowBlock, g_reg.row_smem[si], s, a1))) return st;
   const ColJob* j0 = jobs;
   const int2* it0 = items;
   int n0 = nc;
   void* a2[] = {(void*)&j0, (void*)&it0, (void*)&n0};
-  CU(cudaLaunchKernel(g_reg.col[COL_KHAT][sc], dim3(n0), dim3(kColBlock), a2, g_reg.col_smem[sc], s));
+  if ((st = launch(g_reg.col[COL_KHAT][sc], n0, kColBlock, g_reg.col_smem[sc], s, a2))) return st;
   // f -> spectrum plane 0 -> (times PSF spectrum) plane 1 -> out
   float2* sp0 = reinterpret_cast<float2*>(spec0);
   void* a3[] = {(void*)&f, (void*)&ivs, (void*)&sp0, (void*)&ovs, (void*)&Hh, (void*)&one, (void*)&noclamp};
-  CU(cudaLaunchKernel(g_reg.row[ROP_R2C][0][si], dim3(per_view), dim3(kRowBlock), a3, g_reg.row_smem[si], s));
+  if ((st = launch(g_reg.row[ROP_R2C][0][si], per_view, kRowBlock, g_reg.row_smem[si], s, a3))) return st;
   const int2* it1 = items + nc;
   void* a4[] = {(void*)&j0, (void*)&it1, (void*)&n0};
-  CU(cudaLaunchKernel(g_reg.col[transpose ? COL_1TOP_CONJ : COL_1TOP][sc], dim3(n0), dim3(kColBlock), a4,
-                      g_reg.col_smem[sc], s));
+  if ((st = launch(g_reg.col[transpose ? COL_1TOP_CONJ : COL_1TOP][sc], n0, kColBlock, g_reg.col_smem[sc], s, a4)))
+    return st;
   const float2* csp1 = sp1;
   float sc1 = 1.0f;
   void* a5[] = {(void*)&csp1, (void*)&ovs, (void*)&out, (void*)&ivs, (void*)&Hh, (void*)&one, (void*)&sc1};
-  CU(cudaLaunchKernel(g_reg.row[ROP_C2R][0][si], dim3(per_view), dim3(kRowBlock), a5, g_reg.row_smem[si], s));
-  return SGP_OK;
+  return launch(g_reg.row[ROP_C2R][0][si], per_view, kRowBlock, g_reg.row_smem[si], s, a5);
 }

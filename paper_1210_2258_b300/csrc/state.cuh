@@ -70,6 +70,7 @@ struct CtrlState {
   int land_pass;    // landed discrepancy stop: 0 idle; n > 0 landing the last step, n - 1 passes done
   int f_pending;    // SGP: K1 left f^(k+1) = f^(k) + lambda d to the gradient pass, which forms it
                     // from f^(k) and grad^(k) and stores it (see f_update_in_k1)
+  int capped;       // 1 when the last stop came from the iteration cap, not from the stop rule
   double land_lo, land_hi, land_Jlo, land_Jhi, land_Jt;   // bracket of lambda, J at its ends, target
   double J;         // J_0 at the current iterate
   double J_pred;    // J_0 at the accepted trial point

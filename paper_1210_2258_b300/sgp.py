@@ -101,6 +101,8 @@ def load() -> C.CDLL:
         "sgp_mosaic_geometry": (st, [C.POINTER(Mosaic), C.POINTER(i)]),
         "sgp_mosaic_split": (st, [C.POINTER(Mosaic), i, vp, vp, vp, vp]),
         "sgp_mosaic_stitch": (st, [C.POINTER(Mosaic), vp, vp, vp]),
+        "sgp_sum_terms_workspace_bytes": (C.c_size_t, [C.c_size_t]),
+        "sgp_sum_terms": (st, [i, i, vp, vp, vp, C.c_size_t, d, vp, C.POINTER(d), vp, C.c_size_t, vp]),
         "sgp_destroy": (st, [vp]),
         "sgp_last_error": (C.c_char_p, []),
     }
@@ -311,6 +313,26 @@ class Problems:
             self.close()
         except Exception:
             pass
+
+
+SUM_VALUES, SUM_KL, SUM_ARMIJO, SUM_BB0 = 0, 1, 2, 3
+
+
+def sum_terms(kind: int, a, b=None, c=None, lam: float = 1.0, reduce_fp64: int = 1, want_terms: bool = True,
+              stream=None):
+    """Pixel terms of one kind and their sum through the library's reduction (sgp_sum_terms).
+    a, b, c: float32 CUDA tensors of equal size.  Returns (sum as float, terms tensor or None)."""
+    import torch
+    lib = load()
+    n = a.numel()
+    ws = torch.empty(lib.sgp_sum_terms_workspace_bytes(n) + 256, dtype=torch.uint8, device=a.device)
+    base = (ws.data_ptr() + 255) & ~255
+    terms = torch.empty_like(a) if want_terms else None
+    out = C.c_double()
+    _check(lib.sgp_sum_terms(kind, reduce_fp64, a.data_ptr(), _ptr(b), _ptr(c), n, lam, _ptr(terms),
+                             C.byref(out), C.c_void_p(base), ws.numel() - (base - ws.data_ptr()),
+                             _stream_ptr(stream)))
+    return out.value, terms
 
 
 def single(psf, g, b, mask=None, params: Params | None = None, stream=None) -> Problems:

@@ -36,3 +36,15 @@ def gpu_problem(lib, sc, params=None):
                      dev(sc.mask) if sc.mask is not None else None, params)
     p.set_data(0, dev(np.asarray(sc.g, np.float32)))
     return p
+
+
+def fp32_envelope():
+    """Per-iteration bound on the KL deviation of an FP32 SGP run from the FP64 oracle on the
+    256^2 star field (tests/golden/sgp_fp32_envelope.json, written from the oracle alone): the
+    largest deviation that single-precision transforms cause in the oracle itself, floored at the
+    1e-5 operator-level tolerance."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "sgp_fp32_envelope.json")) as fh:
+        env = json.load(fh)
+    return env, [max(1e-5, x) for x in env["max_rel_J_per_k"]]

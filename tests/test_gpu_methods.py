@@ -10,7 +10,7 @@ import pytest
 
 from oracle import sgp_oracle as O
 from paper_1210_2258_b300 import scenes
-from tests.gpu_util import dev, gpu_problem, host, oracle_problem, rel_l2
+from tests.gpu_util import dev, fp32_envelope, gpu_problem, host, oracle_problem, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -46,19 +46,28 @@ def _decisions(tr, ref, n):
 def test_sgp_parity_within_horizon_stars_256(gpu, stars256):
     """SGP is chaotic on this scene beyond ~60 iterations even in FP64 (a 1e-7 perturbation of the
     data grows to 0.3 in f by iteration 200; see test_oracle_pins.test_sgp_trajectory_sensitivity),
-    so element-wise parity is checked where the oracle itself is stable."""
+    so element-wise parity is checked over the first 30 iterations.  The KL of every iterate must
+    agree with the oracle within 1e-5, or within the deviation that single-precision transforms
+    alone cause in the oracle at that iteration where that is larger (tests/golden/
+    sgp_fp32_envelope.json: below 1e-5 up to k = 27, 1.9e-4 at k = 30, where the trajectory's
+    sensitivity jumps)."""
     sc = stars256
     n = 30
+    env, tolJ = fp32_envelope()
     orc = oracle_problem(sc)
     ref = O.sgp(orc, stop=O.StopRule("fixed", max_iter=n))
+    assert np.allclose([t["J"] for t in ref.trace], env["J_ref"], rtol=1e-12, atol=0)
     prob = gpu_problem(gpu, sc)
     prob.sgp_iterate(n)
     info = prob.info()
     assert info.k == n
     assert abs(info.L1 - ref.L1) <= 1e-4 * ref.L1 and abs(info.L2 - ref.L2) <= 1e-4 * ref.L2
-    assert abs(info.J - ref.J) <= 1e-5 * ref.J, (info.J, ref.J)
+    assert abs(info.J - ref.J) <= tolJ[-1] * ref.J, (info.J, ref.J)
     assert rel_l2(host(prob.get_f()), ref.f) <= 1e-3
     tr = prob.trace()
+    Jo = np.array([t["J"] for t in ref.trace])
+    dev = np.abs(tr[:n, 1] - Jo) / Jo
+    assert np.all(dev <= np.array(tolJ)), np.array2string(dev / np.array(tolJ), precision=2)
     assert _decisions(tr, ref, n)
     al = np.array([t["alpha"] for t in ref.trace])
     assert np.max(np.abs(tr[:, 3] - al) / al) <= 1e-2

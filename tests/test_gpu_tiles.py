@@ -1,12 +1,12 @@
 """The autotuned row tile: every candidate tile gives the oracle's iteration (parity within the SGP
-horizon, RL over 200 iterations), the autotuner picks a candidate, and contexts of one size share
+horizon with the KL bound of the FP32-transform envelope, RL over 200 iterations at 1e-5), the autotuner picks a candidate, and contexts of one size share
 its choice (so a batch and a single problem still agree bit for bit)."""
 import numpy as np
 import pytest
 
 from oracle import sgp_oracle as O
 from paper_1210_2258_b300 import scenes
-from tests.gpu_util import gpu_problem, host, oracle_problem, rel_l2
+from tests.gpu_util import fp32_envelope, gpu_problem, host, oracle_problem, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -30,7 +30,7 @@ def test_every_row_tile_matches_the_oracle(gpu, stars256):
         assert prob.tile() == (R, R * T)
         prob.sgp_iterate(n)
         assert prob.info().k == n
-        assert abs(prob.kl_value() - ref.J) <= 1e-5 * ref.J, (R, prob.kl_value(), ref.J)
+        assert abs(prob.kl_value() - ref.J) <= fp32_envelope()[1][n - 1] * ref.J, (R, prob.kl_value(), ref.J)
         f = host(prob.get_f())
         assert rel_l2(f, ref.f) <= 1e-3
         seen.append(f)

@@ -85,6 +85,20 @@ def test_threaded_fft_primitive_gives_the_same_convolutions():
     np.testing.assert_allclose(c16, _direct_conv(f16, K16), rtol=1e-12, atol=1e-14)
 
 
+def test_single_precision_transforms_round_at_fp32_level():
+    rng = scenes.rng_for(12)
+    K = _rand_psf(rng, 32, 48)
+    f = rng.random((32, 48)) * 100.0
+    ref = O.conv_periodic(f, K)
+    try:
+        O.set_fft_single_precision(True)
+        lo = O.conv_periodic(f, K)
+    finally:
+        O.set_fft_single_precision(False)
+    err = np.linalg.norm(lo - ref) / np.linalg.norm(ref)
+    assert 1e-9 < err < 1e-6
+
+
 def test_convolution_matches_scipy_wrap_convolve():
     from scipy import ndimage
     rng = scenes.rng_for(3)
