@@ -4,11 +4,14 @@
 Workload: a synthetic galaxy (5 Sersic profiles, peak 1e4) plus 500 log-uniform stars, blurred by
 the Airy PSF of a circular pupil of diameter N/8, background 50, Poisson noise (seeded).  One step
 is one SGP solve from the constant starting point to the discrepancy-principle stop (eta = 1),
-with FP64-accumulated reductions.  `value` is SGP iterations per second over the timed steps
+with FP64-grade reductions (error-free FP32 two-sum pairs).  `value` is SGP iterations per second over the timed steps
 (inputs resident in HBM, L2 flushed before each step by writing a 512 MB buffer); `e2e` is the same
 metric through the public API with host buffers: the PSF's context is prepared once, and every
 step copies its image in from pinned host memory, solves and copies the reconstruction out
 (`e2e.new_context_per_step`: the same with the PSF copied in and a new context every step).
+`warm_start`: the learned warm start (network trained here on other scenes' SGP solutions, its
+forward pass timed with the solve) against the flat mixed and plain-FP32 starts, all to the same
+landed discrepancy stop; `unbanded`: the headline solve with every spectrum column transformed.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -61,6 +64,8 @@ def parse():
     ap.add_argument("--N", type=int, default=2048)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-warm", action="store_true", help="skip the warm-start arm (network training + timing)")
+    ap.add_argument("--warm-train", type=int, default=32, help="training images of the warm-start arm")
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling driver: set up the workload, run this many SGP iterations, exit")
     ap.add_argument("--workload", default="galaxy2048",
@@ -148,6 +153,137 @@ def dist_setup(args):
 def make_scene(args, rank):
     from paper_1210_2258_b300 import scenes
     return scenes.galaxy_scene(seed=args.seed + rank, N=args.N)
+
+
+def _galaxy_data(args):
+    seed, N = args
+    from paper_1210_2258_b300 import scenes
+    return scenes.galaxy_scene(seed=seed, N=N).g[0].astype(np.float32)
+
+
+def warm_training_images(n, N, seed0):
+    """Data of n galaxy scenes like the headline's (other seeds), generated in spawned worker
+    processes before this process touches the GPU."""
+    import multiprocessing as mp
+    workers = max(1, min(n, host_cores(), 16))
+    jobs = [(seed0 + i, N) for i in range(n)]
+    if workers == 1:
+        return [_galaxy_data(j) for j in jobs]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_galaxy_data, jobs)
+
+
+def warm_arm(torch, lib, psf_d, g_d, b, train_imgs, flush, reps):
+    """Time-to-stop of the warm-started form against the flat starts on the headline image, every
+    arm to the same landed discrepancy stop (final discrepancy in [1 - 1e-5, 1], so equal final
+    KL): the network (include/warmstart.h) is trained here on SGP solutions of other galaxy scenes
+    (flat start, discrepancy stop) and its forward pass is inside the warm arm's timed region.
+    Final KLs are evaluated at one precision (the mixed reductions) from each arm's result."""
+    from paper_1210_2258_b300 import warmstart as ws
+    N = g_d.shape[-1]
+    t0 = time.perf_counter()
+    tr = lib.Problems(psf_d, [b])
+    gt = torch.stack([torch.from_numpy(x) for x in train_imgs]).cuda()
+    ft = torch.empty_like(gt)
+    its = []
+    for i in range(gt.shape[0]):
+        tr.set_data(0, gt[i:i + 1])
+        its.append(tr.solve_until(lib.STOP_DISCREPANCY, max_iter=20000, eta=1.0, raise_on_error=False)[0])
+        tr.get_f(0, out=ft[i])
+    tr.close()
+    bt = torch.full((gt.shape[0],), b, dtype=torch.float32, device="cuda")
+    net = ws.WarmStartNet(seed=0)
+    losses = ws.train_crops(net, gt, ft, bt, steps=240, crop=512, batch=8, lr=2e-3, seed=0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del gt, ft
+    bvec = torch.full((1,), b, dtype=torch.float32, device="cuda")
+    ctx = lib.Problems(psf_d, [b])
+    ctx.set_data(0, g_d)
+    ctx32 = lib.Problems(psf_d, [b], params=lib.default_params(reduce_fp64=0))
+    ctx32.set_data(0, g_d)
+    land = dict(max_iter=20000, eta=1.0, tol=1e-5)
+
+    def flat():
+        ctx.set_start(0, lib.START_CONSTANT)
+        return ctx.solve_until(lib.STOP_LANDED, **land)[0]
+
+    def warm():
+        f0 = net.predict(g_d, bvec)
+        ctx.set_start(0, lib.START_USER, f0[0])
+        return ctx.solve_until(lib.STOP_LANDED, **land)[0]
+
+    def plain():
+        ctx32.set_start(0, lib.START_CONSTANT)
+        return ctx32.solve_until(lib.STOP_LANDED, **land)[0]
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, fn, pr in (("warm", warm, ctx), ("flat_mixed", flat, ctx), ("plain_fp32", plain, ctx32)):
+        fn()
+        ms, it = [], 0
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev0.record()
+            it = fn()
+            ev1.record()
+            torch.cuda.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+        out[name] = {"time_to_stop_ms": float(np.median(ms)), "iterations": int(it), "f": pr.get_f(0).clone(),
+                     "status": int(pr.info(0).status)}
+    # network forward alone (inside the warm arm's time)
+    net.predict(g_d, bvec)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        net.predict(g_d, bvec)
+    ev1.record()
+    torch.cuda.synchronize()
+    net_ms = ev0.elapsed_time(ev1) / reps
+    # final KL of each result with the mixed reductions
+    ev_ctx = lib.Problems(psf_d, [b])
+    ev_ctx.set_data(0, g_d)
+    for v in out.values():
+        ev_ctx.set_start(0, lib.START_USER, v.pop("f"))
+        v["final_kl"] = ev_ctx.kl_value(0)
+    for pr in (ctx, ctx32, ev_ctx):
+        pr.close()
+    Jp = out["plain_fp32"]["final_kl"]
+    for k in ("warm", "flat_mixed"):
+        out[k]["kl_rel_vs_plain_fp32"] = abs(out[k]["final_kl"] - Jp) / Jp
+    out["warm"]["net_forward_ms"] = net_ms
+    out["warm"]["faster_than_plain_fp32"] = out["warm"]["time_to_stop_ms"] < out["plain_fp32"]["time_to_stop_ms"]
+    out["stop"] = "landed discrepancy stop: eta = 1, final discrepancy in [1 - 1e-5, 1]"
+    out["training"] = {"images": len(train_imgs), "side": N, "sgp_mean_iterations": float(np.mean(its)),
+                       "steps": len(losses), "crop": 512, "batch": 8, "loss_first_last": [losses[0], losses[-1]],
+                       "seconds": t_train}
+    return out
+
+
+def unbanded_rate(torch, lib, psf_d, g_d, b, flush, reps):
+    """The headline solve with the PSF band off (band_tol = 0: every spectrum column transformed)."""
+    pr = lib.Problems(psf_d, [b], params=lib.default_params(band_tol=0.0))
+    pr.set_data(0, g_d)
+
+    def solve():
+        pr.set_start(0, lib.START_CONSTANT)
+        return pr.solve_until(lib.STOP_DISCREPANCY, max_iter=20000, eta=1.0)[0]
+    solve()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, its = 0.0, 0
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev0.record()
+        its += solve()
+        ev1.record()
+        torch.cuda.synchronize()
+        ms += ev0.elapsed_time(ev1)
+    out = {"value": its / (ms / 1e3), "unit": "iter/s", "time_to_stop_ms": ms / reps, "iterations": its // reps,
+           "band_cols": int(pr.info(0).band_cols)}
+    pr.close()
+    return out
 
 
 def host_cores() -> int:
@@ -333,9 +469,11 @@ def cufft_sgp_baseline(torch, psf_d, g_d, b, max_iter=3000):
 
 
 def run_ours(args):
-    import torch
     if args.profile:
         return run_profile(args)
+    want_warm = not args.no_warm and int(os.environ.get("RANK", "0")) == 0
+    train_imgs = warm_training_images(args.warm_train, args.N, 1000) if want_warm else None
+    import torch
     ws, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
     from paper_1210_2258_b300 import sgp as lib
@@ -416,6 +554,10 @@ def run_ours(args):
     plain_info = plain.info()
     plain.close()
 
+    warm = warm_arm(torch, lib, psf_d, g_d, float(sc.b[0]), train_imgs, flush, max(3, min(args.steps, 10))) \
+        if train_imgs is not None else None
+    unbanded = unbanded_rate(torch, lib, psf_d, g_d, float(sc.b[0]), flush, max(2, min(args.steps, 5)))
+
     cufft = cufft_comparison(torch, lib, prob, psf_d, g_d)
     cufft_sgp_baseline(torch, psf_d, g_d, float(sc.b[0]))          # warm-up (cuFFT plans)
     it_c, ms_c, D_c = cufft_sgp_baseline(torch, psf_d, g_d, float(sc.b[0]))
@@ -475,13 +617,17 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"galaxy+stars {N}x{N}, Airy PSF (pupil N/8), b=50, Poisson, seed {args.seed}; "
-                                   "SGP from the constant start to the discrepancy stop eta=1, FP64 reductions",
+                                   "SGP from the constant start to the discrepancy stop eta=1; KL/BB/Armijo sums "
+                                   "accumulated as error-free FP32 two-sum pairs (FP64-grade, within 4e-15 of the "
+                                   f"exact sums); PSF band on ({int(info.band_cols)} of {N // 2} spectrum columns, "
+                                   "see 'unbanded' for the rate without it)",
                        "N": N, "p": 1, "l2": "flushed (512 MB write) before each step",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "time_to_stop_ms": total_ms / args.steps, "iterations_per_solve": total_it / args.steps,
             "final_kl": info.J, "final_discrepancy": info.D,
             "plain_fp32": {"time_to_stop_ms": plain_ms, "iterations": it_plain, "final_kl": plain_info.J,
                            "final_discrepancy": plain_info.D, "iters_per_s": it_plain / (plain_ms / 1e3)},
+            "warm_start": warm, "unbanded": unbanded,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "cufft_comparison": cufft,
             "clocks": clocks}

@@ -20,7 +20,8 @@
  *
  * Layouts: conv32 weights bf16 [co][tap][ci] (tap = 3 dy + dx), conv_in weights fp32 [co][tap],
  * conv_out weights fp32 [tap][ci]; activations bf16 [b][y][x][c]; every 3x3 convolution uses zero
- * ("same") padding.  ws_conv32 needs H % 8 == 0 and W % 16 == 0.  All pointers are device pointers
+ * ("same") padding.  ws_conv32 needs H % 16 == 0 and W % 8 == 0, ws_conv32_wgrad H % 8 == 0 and
+ * W % 16 == 0, the pooling and upsampling calls even H and W.  All pointers are device pointers
  * owned by the caller; `stream` is a cudaStream_t.  Every call is asynchronous and returns 0, or 1 for
  * an invalid size, 4 for a CUDA launch error.  Gradient accumulators (dw, db, loss) are added to:
  * the caller zeroes them before a step.
@@ -40,11 +41,16 @@ extern "C" {
 #define WS_API
 #endif
 
-/* 32 -> 32 3x3 convolution on the tensor cores.  mode 0: y = relu(conv + bias); 1: y = conv + bias;
- * 2: y = conv * (mask > 0) (data gradient with the ReLU mask of the layer below; pass the flipped
- * weights of ws_flip_weights); 3: y = conv. */
+/* 32 -> 32 3x3 convolution on the 5th-generation tensor cores (tcgen05.mma, bf16 operands staged in
+ * shared memory, FP32 accumulators in tensor memory), persistent blocks over 16 x 8 pixel tiles.
+ * mode 0: y = relu(conv + bias); 1: y = conv + bias; 2: y = conv * (mask > 0) (data gradient with the
+ * ReLU mask of the layer below; pass the flipped weights of ws_flip_weights); 3: y = conv.
+ * A wait for the tensor cores that exceeds its iteration limit sets the flag that ws_error reads. */
 WS_API int ws_conv32(const void* x, const void* w, const float* bias, const void* mask, void* y, int B, int H, int W,
                      int mode, void* stream);
+/* Reads and clears the device-side error flag of the warm-start kernels (1: a bounded wait for the
+ * tensor cores gave up and the output of that call is undefined).  Synchronous. */
+WS_API int ws_error(int* out);
 /* dw[co][tap][ci] += sum_p dy[p][co] x[p + off(tap)][ci]  (x is the layer input) */
 WS_API int ws_conv32_wgrad(const void* dy, const void* x, float* dw, int B, int H, int W, void* stream);
 /* wt[ci][tap][co] = w[co][8 - tap][ci] */
@@ -83,7 +89,8 @@ WS_API int ws_prep(const float* g, const float* f, const float* b, const float* 
 /* f0 = s expm1(clamp(z + log(1 + max(x, 0)), 0, 20)) */
 WS_API int ws_start(const float* z, const float* x, const float* s, float* f0, int B, size_t P, void* stream);
 
-/* s[b] = 1 + mean over the image of max(g - b, 0): the per-image input scale */
+/* s[b] = 1 + mean over the image of max(g - b, 0): the per-image input scale (B <= 1024; calls that
+ * overlap on the GPU must not share the library's per-image accumulator, i.e. run them in order) */
 WS_API int ws_scale(const float* g, const float* b, float* s, int B, size_t P, void* stream);
 /* zero `bytes` bytes at p (gradient accumulators) */
 WS_API int ws_zero(void* p, size_t bytes, void* stream);

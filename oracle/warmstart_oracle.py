@@ -86,3 +86,20 @@ class Net:
         _, dw1, g["b1"] = conv_backward(x0[..., None], p["w1"][:, :, None], dz1)
         g["w1"] = dw1[:, :, 0]
         return loss, g
+
+
+def adam(p, g_steps, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """Adam (Kingma and Ba) on parameters p for the gradient sequence g_steps: moments
+    m = b1 m + (1 - b1) g and v = b2 v + (1 - b2) g^2, bias-corrected m / (1 - b1^t) and
+    v / (1 - b2^t), step p -= lr m_hat / (sqrt(v_hat) + eps), t = 1, 2, ...  Returns (p, m, v)."""
+    p = np.array(p, np.float64, copy=True)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for t, g in enumerate(g_steps, start=1):
+        g = np.asarray(g, np.float64)
+        m = b1 * m + (1.0 - b1) * g
+        v = b2 * v + (1.0 - b2) * g * g
+        mh = m / (1.0 - b1 ** t)
+        vh = v / (1.0 - b2 ** t)
+        p = p - lr * mh / (np.sqrt(vh) + eps)
+    return p, m, v

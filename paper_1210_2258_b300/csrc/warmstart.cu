@@ -10,6 +10,8 @@
 //   wgrad    dW[co][tap][ci] = sum_p dY[p][co] X[p + off(tap)][ci]
 // with "same" zero padding.  The 1 -> 32 input layer and the 32 -> 1 output layer are small and run on
 // the FP32 pipes.  All declarations and contracts: include/warmstart.h.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -51,72 +53,205 @@ __device__ __forceinline__ void stage_tile(const bf16* __restrict__ x, bf16* sx,
   }
 }
 
+// ------------------------------------------------------------------------------ tcgen05 convolution
+// Forward (and data-gradient) 32 -> 32 3x3 convolution as an implicit GEMM on the 5th-generation
+// tensor cores: a tile of M = 128 output pixels (16 image rows x 8 columns) times N = 32 output
+// channels, K = 9 taps x 32 input channels, as 18 tcgen05.mma (kind::f16, bf16 in, FP32 accumulate
+// in tensor memory) of K = 16 each, issued by one thread.
+//
+// Operands in shared memory, no swizzle, K-major "core matrices" of 8 rows x 16 bytes:
+//   A: the tile's halo (18 x 10 pixels) stored [kc][halo pixel][8 channels] (kc = channel group of 8),
+//      so that for tap (dy, dx) the 8-row group r (image row r of the tile, 8 consecutive pixels) starts
+//      at halo pixel (r + dy) * 10 + dx: M-groups 160 bytes apart, K core matrices 180 * 16 bytes
+//      apart -- every tap is the same buffer read at another start address, no copy per tap;
+//   B: the weights stored [tap][kc][co][8 channels] (loaded once per block).
+// Persistent blocks walk the tiles; the halo of tile i + 2 is fetched with cp.async (zero fill
+// outside the image) while tile i is multiplied and tile i - 1 leaves tensor memory through the
+// epilogue (two 32-column accumulators alternate).  Every wait on the MMA completion barrier has an
+// iteration limit; a block that gives up records the error flag and still releases its tensor
+// memory.
+constexpr int TCR = 16, TCC = 8;                // output tile: 16 rows x 8 columns (M = 128)
+constexpr int THC = TCC + 2;                    // halo columns
+constexpr int THP = (TCR + 2) * THC;            // halo pixels (180)
+constexpr int TA_BYTES = 4 * THP * 16;          // one A stage
+constexpr int TB_BYTES = 9 * 4 * 32 * 16;       // weights
+constexpr int TSTAGES = 3;
+constexpr int TC_SMEM = TB_BYTES + TSTAGES * TA_BYTES;
+constexpr int TC_BLOCKS_PER_SM = 4;             // 4 x 53 KB shared memory, 4 x 64 tensor-memory columns
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+// tcgen05 shared-memory matrix descriptor: start address, byte distance between core matrices along
+// K (leading) and along M/N (stride), the fixed version bits 46-48 = 0b001, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lead, uint32_t stride) {
+  return uint64_t((addr & 0x3FFFF) >> 4) | (uint64_t((lead >> 4) & 0x3FFF) << 16) |
+         (uint64_t((stride >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
+}
+// instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B bf16 (bits 7-9, 10-12 = 1),
+// both K-major, N = 32 (bits 17-22 = N / 8), M = 128 (bits 24-28 = M / 16)
+constexpr uint32_t kConvIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t* m, uint32_t parity) {
+  const uint32_t a = smem_u32(m);
+  for (int i = 0; i < (1 << 22); ++i) {
+    uint32_t ok;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tile_origin(int tile, int tiles_x, int tiles_yx, int& b, int& y0, int& x0) {
+  b = tile / tiles_yx;
+  const int rem = tile - b * tiles_yx;
+  y0 = (rem / tiles_x) * TCR;
+  x0 = (rem % tiles_x) * TCC;
+}
+
+// cp.async of one tile's halo into an A stage, 16 bytes per copy, zero fill outside the image
+__device__ __forceinline__ void halo_async(const bf16* __restrict__ x, uint8_t* sa, int b, int y0, int x0, int H, int W) {
+  const uint32_t base = smem_u32(sa);
+  for (int i = threadIdx.x; i < THP * 4; i += blockDim.x) {
+    const int hp = i >> 2, kc = i & 3;
+    const int yy = y0 + hp / THC - 1, xx = x0 + hp % THC - 1;
+    const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+    const bf16* src = in ? x + ((size_t(b) * H + yy) * W + xx) * 32 + kc * 8 : x;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(base + (kc * THP + hp) * 16), "l"(src),
+                 "r"(in ? 16 : 0) : "memory");
+  }
+}
+
 // MODE: 0 bias + ReLU, 1 bias (linear), 2 multiply by (mask > 0), 3 plain
 template <int MODE>
-__global__ void __launch_bounds__(128) k_conv32(const bf16* __restrict__ x, const bf16* __restrict__ w,
-                                               const float* __restrict__ bias, const bf16* __restrict__ mask,
-                                               bf16* __restrict__ y, int H, int W) {
-  __shared__ __align__(16) bf16 sx[HY * HX * CP];
-  __shared__ __align__(16) bf16 sw[32 * WP];
-  const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH, b = blockIdx.z;
-  for (int i = threadIdx.x; i < 32 * 9 * 4; i += blockDim.x) {   // 32 co x 9 taps x 4 x 8 ci
-    const int co = i / 36, r = i % 36;
-    *reinterpret_cast<int4*>(sw + co * WP + r * 8) = reinterpret_cast<const int4*>(w)[i];
+__global__ void __launch_bounds__(128, TC_BLOCKS_PER_SM) k_conv32(const bf16* __restrict__ x, const bf16* __restrict__ w,
+                                                                 const float* __restrict__ bias,
+                                                                 const bf16* __restrict__ mask, bf16* __restrict__ y,
+                                                                 int B, int H, int W, int* __restrict__ err) {
+  extern __shared__ __align__(128) uint8_t dsm[];
+  uint8_t* sB = dsm;
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t s_tmem;
+  const int tiles_x = W / TCC, tiles_yx = tiles_x * (H / TCR), ntiles = tiles_yx * B;
+  if (int(blockIdx.x) >= ntiles) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(&s_tmem))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  stage_tile(x, sx, b, y0, x0, H, W);
+  if (threadIdx.x == 32) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = threadIdx.x; i < 32 * 9 * 4; i += blockDim.x) {   // w[co][tap][ci] -> sB[tap][kc][co][8]
+    const int co = i / 36, r = i % 36, tap = r >> 2, kc = r & 3;
+    *reinterpret_cast<int4*>(sB + ((tap * 4 + kc) * 32 + co) * 16) = reinterpret_cast<const int4*>(w)[i];
+  }
+  // prologue: halos of this block's first two tiles
+  for (int q = 0; q < 2; ++q) {
+    const int tile = blockIdx.x + q * gridDim.x;
+    if (tile < ntiles) {
+      int b, y0, x0;
+      tile_origin(tile, tiles_x, tiles_yx, b, y0, x0);
+      halo_async(x, dsm + TB_BYTES + q * TA_BYTES, b, y0, x0, H, W);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  float acc[2][4][4];
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  bool ok = true;
+  int prev_b = 0, prev_y0 = 0, prev_x0 = 0;
+  int i = 0;
+  auto epilogue = [&](int k, int b, int y0, int x0) {
+    uint32_t v[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(tmem + uint32_t((k & 1) * 32) + (uint32_t(32 * warp) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int m = 32 * warp + lane;
+    const size_t pix = (size_t(b) * H + y0 + m / TCC) * W + x0 + m % TCC;
+    int4 mk[4];
+    if (MODE == 2) {
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.0f;
-#pragma unroll
-  for (int tap = 0; tap < 9; ++tap) {
-    const int dy = tap / 3, dx = tap % 3;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      uint32_t bf[4][2];
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const bf16* wp = sw + (8 * nt + g) * WP + tap * 32 + 16 * h + 2 * t;
-        bf[nt][0] = ld32(wp);
-        bf[nt][1] = ld32(wp + 8);
-      }
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int r = 2 * warp + mt;
-        const bf16* p0 = sx + ((r + dy) * HX + g + dx) * CP + 16 * h + 2 * t;
-        const bf16* p1 = p0 + 8 * CP;
-        const uint32_t a0 = ld32(p0), a1 = ld32(p1), a2 = ld32(p0 + 8), a3 = ld32(p1 + 8);
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) mma16816(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
-      }
+      for (int q = 0; q < 4; ++q) mk[q] = reinterpret_cast<const int4*>(mask + pix * 32)[q];
     }
-  }
+    uint32_t pk[16];
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
-    const int yy = y0 + 2 * warp + mt;
+    for (int c = 0; c < 32; c += 2) {
+      float v0 = __uint_as_float(v[c]), v1 = __uint_as_float(v[c + 1]);
+      if (MODE <= 1) { v0 += bias[c]; v1 += bias[c + 1]; }
+      if (MODE == 0) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
+      if (MODE == 2) {
+        const uint32_t mw = reinterpret_cast<const uint32_t*>(mk)[c / 2];
+        if (!(__bfloat162float(__ushort_as_bfloat16(uint16_t(mw & 0xffff))) > 0.0f)) v0 = 0.0f;
+        if (!(__bfloat162float(__ushort_as_bfloat16(uint16_t(mw >> 16))) > 0.0f)) v1 = 0.0f;
+      }
+      pk[c / 2] = pack2(__float2bfloat16(v0), __float2bfloat16(v1));
+    }
+    int4* dst = reinterpret_cast<int4*>(y + pix * 32);
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int xx = x0 + g + 8 * half;
-      const size_t pix = (size_t(b) * H + yy) * W + xx;
+    for (int q = 0; q < 4; ++q) dst[q] = make_int4(int(pk[4 * q]), int(pk[4 * q + 1]), int(pk[4 * q + 2]), int(pk[4 * q + 3]));
+  };
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+    int b, y0, x0;
+    tile_origin(tile, tiles_x, tiles_yx, b, y0, x0);
+    // the halo of tile i has landed (only the group of tile i + 1 may still be in flight)
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (threadIdx.x == 0) {
+      const uint32_t a0 = smem_u32(dsm + TB_BYTES + (i % TSTAGES) * TA_BYTES), b0 = smem_u32(sB);
+      const uint32_t d = tmem + uint32_t((i & 1) * 32);
+#pragma unroll 1
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int co = 8 * nt + 2 * t;
-        float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
-        if (MODE <= 1) { v0 += bias[co]; v1 += bias[co + 1]; }
-        if (MODE == 0) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
-        if (MODE == 2) {
-          const bf16* m = mask + pix * 32 + co;
-          if (!(__bfloat162float(m[0]) > 0.0f)) v0 = 0.0f;
-          if (!(__bfloat162float(m[1]) > 0.0f)) v1 = 0.0f;
+        for (int ks = 0; ks < 2; ++ks) {
+          const uint64_t ad = umma_desc(a0 + ((2 * ks) * THP + dy * THC + dx) * 16, THP * 16, THC * 16);
+          const uint64_t bd = umma_desc(b0 + (tap * 4 + 2 * ks) * 32 * 16, 32 * 16, 8 * 16);
+          const uint32_t accum = (tap | ks) ? 1u : 0u;
+          asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }"
+                       ::"r"(d), "l"(ad), "l"(bd), "r"(kConvIdesc), "r"(accum) : "memory");
         }
-        *reinterpret_cast<uint32_t*>(y + pix * 32 + co) = pack2(__float2bfloat16(v0), __float2bfloat16(v1));
       }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(smem_u32(&mbar[i & 1])) : "memory");
     }
+    if (i >= 1) {   // tile i - 1: its products are done, its stage is free, its accumulator is read out
+      ok = ok && mbar_wait_parity(&mbar[(i - 1) & 1], uint32_t(((i - 1) >> 1) & 1));
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    const int nt = tile + 2 * int(gridDim.x);
+    if (nt < ntiles) {
+      int nb, ny0, nx0;
+      tile_origin(nt, tiles_x, tiles_yx, nb, ny0, nx0);
+      halo_async(x, dsm + TB_BYTES + ((i + 2) % TSTAGES) * TA_BYTES, nb, ny0, nx0, H, W);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    if (i >= 1) epilogue(i - 1, prev_b, prev_y0, prev_x0);
+    prev_b = b; prev_y0 = y0; prev_x0 = x0;
+  }
+  ok = ok && mbar_wait_parity(&mbar[(i - 1) & 1], uint32_t(((i - 1) >> 1) & 1));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  epilogue(i - 1, prev_b, prev_y0, prev_x0);
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (!ok && lane == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
   }
 }
 
@@ -191,62 +326,109 @@ __global__ void k_flip_weights(const bf16* __restrict__ w, bf16* __restrict__ wt
   wt[i] = w[(co * 9 + (8 - tap)) * 32 + ci];
 }
 
-// input layer 1 -> 32: Y[p][co] = relu(sum_tap X[p + off] W[co][tap] + b[co]), X fp32 single channel
-__global__ void k_conv_in(const float* __restrict__ x, const float* __restrict__ w, const float* __restrict__ bias,
-                          bf16* __restrict__ y, int B, int H, int W) {
-  const size_t n = size_t(B) * H * W * 32;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
-    const int co = int(i & 31);
-    const size_t p = i >> 5;
-    const int xx = int(p % W), yy = int((p / W) % H);
-    const size_t bb = p / (size_t(W) * H);
-    float s = bias[co];
+// Pixel kernels: grid (ceil(W / 128), H, B), one thread per pixel (b, yy, xx); activations move as
+// 64-byte rows of 32 bf16 channels (four 16-byte vectors).
+__device__ __forceinline__ bool pix_of(int W, int& b, int& yy, int& xx) {
+  xx = blockIdx.x * blockDim.x + threadIdx.x;
+  yy = blockIdx.y;
+  b = blockIdx.z;
+  return xx < W;
+}
+__device__ __forceinline__ void load32(const bf16* p, float (&v)[32]) {
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int u = yy + tap / 3 - 1, v = xx + tap % 3 - 1;
-      if (u >= 0 && u < H && v >= 0 && v < W) s += x[(bb * H + u) * W + v] * w[co * 9 + tap];
+  for (int q = 0; q < 4; ++q) {
+    const int4 t = reinterpret_cast<const int4*>(p)[q];
+    const uint32_t w4[4] = {uint32_t(t.x), uint32_t(t.y), uint32_t(t.z), uint32_t(t.w)};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[8 * q + 2 * k] = __bfloat162float(__ushort_as_bfloat16(uint16_t(w4[k] & 0xffff)));
+      v[8 * q + 2 * k + 1] = __bfloat162float(__ushort_as_bfloat16(uint16_t(w4[k] >> 16)));
     }
-    y[i] = __float2bfloat16(fmaxf(s, 0.0f));
   }
+}
+__device__ __forceinline__ void store32(bf16* p, const float (&v)[32]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    reinterpret_cast<int4*>(p)[q] = make_int4(
+        int(pack2(__float2bfloat16(v[8 * q]), __float2bfloat16(v[8 * q + 1]))),
+        int(pack2(__float2bfloat16(v[8 * q + 2]), __float2bfloat16(v[8 * q + 3]))),
+        int(pack2(__float2bfloat16(v[8 * q + 4]), __float2bfloat16(v[8 * q + 5]))),
+        int(pack2(__float2bfloat16(v[8 * q + 6]), __float2bfloat16(v[8 * q + 7]))));
+}
+dim3 pix_grid(int B, int H, int W) { return dim3((W + 127) / 128, H, B); }
+
+// input layer 1 -> 32: Y[p][co] = relu(sum_tap X[p + off] W[co][tap] + b[co]), X fp32 single channel
+__global__ void __launch_bounds__(128) k_conv_in(const float* __restrict__ x, const float* __restrict__ w,
+                                                const float* __restrict__ bias, bf16* __restrict__ y, int H, int W) {
+  __shared__ float sw[32 * 9 + 32];
+  for (int i = threadIdx.x; i < 32 * 9 + 32; i += blockDim.x) sw[i] = i < 288 ? w[i] : bias[i - 288];
+  __syncthreads();
+  int b, yy, xx;
+  if (!pix_of(W, b, yy, xx)) return;
+  float xv[9];
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) {
+    const int u = yy + tap / 3 - 1, v = xx + tap % 3 - 1;
+    xv[tap] = (u >= 0 && u < H && v >= 0 && v < W) ? x[(size_t(b) * H + u) * W + v] : 0.0f;
+  }
+  float o[32];
+#pragma unroll
+  for (int co = 0; co < 32; ++co) {
+    float s = sw[288 + co];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) s = fmaf(xv[tap], sw[co * 9 + tap], s);
+    o[co] = fmaxf(s, 0.0f);
+  }
+  store32(y + ((size_t(b) * H + yy) * W + xx) * 32, o);
 }
 
 // output layer 32 -> 1: Z[p] = sum_{tap, ci} X[p + off][ci] W[tap][ci] + b (FP32 out)
-__global__ void k_conv_out(const bf16* __restrict__ x, const float* __restrict__ w, const float* __restrict__ bias,
-                           float* __restrict__ z, int B, int H, int W) {
-  const size_t n = size_t(B) * H * W;
-  for (size_t p = blockIdx.x * size_t(blockDim.x) + threadIdx.x; p < n; p += size_t(gridDim.x) * blockDim.x) {
-    const int xx = int(p % W), yy = int((p / W) % H);
-    const size_t bb = p / (size_t(W) * H);
-    float s = bias[0];
-    for (int tap = 0; tap < 9; ++tap) {
-      const int u = yy + tap / 3 - 1, v = xx + tap % 3 - 1;
-      if (u < 0 || u >= H || v < 0 || v >= W) continue;
-      const bf16* xp = x + ((bb * H + u) * W + v) * 32;
+__global__ void __launch_bounds__(128) k_conv_out(const bf16* __restrict__ x, const float* __restrict__ w,
+                                                 const float* __restrict__ bias, float* __restrict__ z, int H, int W) {
+  __shared__ float sw[288];
+  for (int i = threadIdx.x; i < 288; i += blockDim.x) sw[i] = w[i];
+  __syncthreads();
+  int b, yy, xx;
+  if (!pix_of(W, b, yy, xx)) return;
+  float s = bias[0];
+  for (int tap = 0; tap < 9; ++tap) {
+    const int u = yy + tap / 3 - 1, v = xx + tap % 3 - 1;
+    if (u < 0 || u >= H || v < 0 || v >= W) continue;
+    float a[32];
+    load32(x + ((size_t(b) * H + u) * W + v) * 32, a);
 #pragma unroll
-      for (int ci = 0; ci < 32; ++ci) s += __bfloat162float(xp[ci]) * w[tap * 32 + ci];
-    }
-    z[p] = s;
+    for (int ci = 0; ci < 32; ++ci) s = fmaf(a[ci], sw[tap * 32 + ci], s);
   }
+  z[(size_t(b) * H + yy) * W + xx] = s;
 }
 
 // data gradient of the output layer, times the ReLU mask of its input:
 // dX[q][ci] = (X[q][ci] > 0) sum_tap dZ[q - off(tap)] W[tap][ci]
-__global__ void k_conv_out_dgrad(const float* __restrict__ dz, const float* __restrict__ w,
-                                 const bf16* __restrict__ xin, bf16* __restrict__ dx, int B, int H, int W) {
-  const size_t n = size_t(B) * H * W * 32;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
-    const int ci = int(i & 31);
-    const size_t q = i >> 5;
-    const int xx = int(q % W), yy = int((q / W) % H);
-    const size_t bb = q / (size_t(W) * H);
-    float s = 0.0f;
+__global__ void __launch_bounds__(128) k_conv_out_dgrad(const float* __restrict__ dz, const float* __restrict__ w,
+                                                       const bf16* __restrict__ xin, bf16* __restrict__ dx, int H,
+                                                       int W) {
+  __shared__ float sw[288];
+  for (int i = threadIdx.x; i < 288; i += blockDim.x) sw[i] = w[i];
+  __syncthreads();
+  int b, yy, xx;
+  if (!pix_of(W, b, yy, xx)) return;
+  float acc[32];
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int u = yy - (tap / 3 - 1), v = xx - (tap % 3 - 1);
-      if (u >= 0 && u < H && v >= 0 && v < W) s += dz[(bb * H + u) * W + v] * w[tap * 32 + ci];
-    }
-    dx[i] = __float2bfloat16(__bfloat162float(xin[i]) > 0.0f ? s : 0.0f);
+  for (int ci = 0; ci < 32; ++ci) acc[ci] = 0.0f;
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) {
+    const int u = yy - (tap / 3 - 1), v = xx - (tap % 3 - 1);
+    if (u < 0 || u >= H || v < 0 || v >= W) continue;
+    const float d = dz[(size_t(b) * H + u) * W + v];
+#pragma unroll
+    for (int ci = 0; ci < 32; ++ci) acc[ci] = fmaf(d, sw[tap * 32 + ci], acc[ci]);
   }
+  const size_t q = ((size_t(b) * H + yy) * W + xx) * 32;
+  float m[32];
+  load32(xin + q, m);
+#pragma unroll
+  for (int ci = 0; ci < 32; ++ci) acc[ci] = m[ci] > 0.0f ? acc[ci] : 0.0f;
+  store32(dx + q, acc);
 }
 
 // Weight and bias gradients of the small layers, one thread per weight, blocks over pixel chunks:
@@ -309,66 +491,74 @@ __global__ void __launch_bounds__(256) k_bias_grad(const bf16* __restrict__ dy, 
   }
 }
 
-// 2x2 average pooling (forward) and its adjoint
-__global__ void k_pool2(const bf16* __restrict__ x, bf16* __restrict__ y, int B, int H, int W) {
+// 2x2 average pooling (forward); grid over the half-resolution pixels
+__global__ void __launch_bounds__(128) k_pool2(const bf16* __restrict__ x, bf16* __restrict__ y, int H, int W) {
   const int h = H / 2, w = W / 2;
-  const size_t n = size_t(B) * h * w * 32;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
-    const int c = int(i & 31);
-    const size_t q = i >> 5;
-    const int xx = int(q % w), yy = int((q / w) % h);
-    const size_t bb = q / (size_t(w) * h);
-    const size_t base = ((bb * H + 2 * yy) * W + 2 * xx) * 32 + c;
-    const float s = __bfloat162float(x[base]) + __bfloat162float(x[base + 32]) + __bfloat162float(x[base + size_t(W) * 32]) +
-                    __bfloat162float(x[base + size_t(W) * 32 + 32]);
-    y[i] = __float2bfloat16(0.25f * s);
+  int b, yy, xx;
+  if (!pix_of(w, b, yy, xx)) return;
+  float s[32], a[32];
+  const size_t base = (size_t(b) * H + 2 * yy) * W + 2 * xx;
+  load32(x + base * 32, s);
+  const size_t nb[3] = {base + 1, base + W, base + W + 1};
+  for (int k = 0; k < 3; ++k) {
+    load32(x + nb[k] * 32, a);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) s[c] += a[c];
   }
+#pragma unroll
+  for (int c = 0; c < 32; ++c) s[c] *= 0.25f;
+  store32(y + ((size_t(b) * h + yy) * w + xx) * 32, s);
 }
 
-// nearest 2x upsampling (forward) of x (B, H/2, W/2) added to skip (B, H, W): y = up(x) + skip
-__global__ void k_up2_add(const bf16* __restrict__ x, const bf16* __restrict__ skip, bf16* __restrict__ y, int B, int H,
-                          int W) {
-  const size_t n = size_t(B) * H * W * 32;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
-    const int c = int(i & 31);
-    const size_t p = i >> 5;
-    const int xx = int(p % W), yy = int((p / W) % H);
-    const size_t bb = p / (size_t(W) * H);
-    const float v = __bfloat162float(x[((bb * (H / 2) + yy / 2) * (W / 2) + xx / 2) * 32 + c]) + __bfloat162float(skip[i]);
-    y[i] = __float2bfloat16(v);
-  }
+// nearest 2x upsampling of x (B, H/2, W/2) added to skip (B, H, W): y = up(x) + skip
+__global__ void __launch_bounds__(128) k_up2_add(const bf16* __restrict__ x, const bf16* __restrict__ skip,
+                                                bf16* __restrict__ y, int H, int W) {
+  int b, yy, xx;
+  if (!pix_of(W, b, yy, xx)) return;
+  float s[32], a[32];
+  const size_t p = ((size_t(b) * H + yy) * W + xx) * 32;
+  load32(skip + p, s);
+  load32(x + ((size_t(b) * (H / 2) + yy / 2) * (W / 2) + xx / 2) * 32, a);
+#pragma unroll
+  for (int c = 0; c < 32; ++c) s[c] += a[c];
+  store32(y + p, s);
 }
 
-// backward of the skip / pooling junction at full resolution:
-// dZ2 = (dS5 + pool^T(dP2)) * (A2 > 0);  also dU = up^T(dS5) at half resolution (mode 1)
-__global__ void k_junction_bwd(const bf16* __restrict__ ds5, const bf16* __restrict__ dp2, const bf16* __restrict__ a2,
-                               bf16* __restrict__ dz2, int B, int H, int W) {
-  const size_t n = size_t(B) * H * W * 32;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
-    const int c = int(i & 31);
-    const size_t p = i >> 5;
-    const int xx = int(p % W), yy = int((p / W) % H);
-    const size_t bb = p / (size_t(W) * H);
-    float v = __bfloat162float(ds5[i]) + 0.25f * __bfloat162float(dp2[((bb * (H / 2) + yy / 2) * (W / 2) + xx / 2) * 32 + c]);
-    dz2[i] = __float2bfloat16(__bfloat162float(a2[i]) > 0.0f ? v : 0.0f);
-  }
+// backward of the skip / pooling junction at full resolution: dZ2 = (dS5 + pool^T(dP2)) * (A2 > 0)
+__global__ void __launch_bounds__(128) k_junction_bwd(const bf16* __restrict__ ds5, const bf16* __restrict__ dp2,
+                                                     const bf16* __restrict__ a2, bf16* __restrict__ dz2, int H, int W) {
+  int b, yy, xx;
+  if (!pix_of(W, b, yy, xx)) return;
+  float s[32], a[32], m[32];
+  const size_t p = ((size_t(b) * H + yy) * W + xx) * 32;
+  load32(ds5 + p, s);
+  load32(dp2 + ((size_t(b) * (H / 2) + yy / 2) * (W / 2) + xx / 2) * 32, a);
+  load32(a2 + p, m);
+#pragma unroll
+  for (int c = 0; c < 32; ++c) s[c] = m[c] > 0.0f ? s[c] + 0.25f * a[c] : 0.0f;
+  store32(dz2 + p, s);
 }
 
-// dA4 = up^T(dS5) (sum over each 2x2 block), times the ReLU mask of A4
-__global__ void k_up2_bwd_mask(const bf16* __restrict__ ds5, const bf16* __restrict__ a4, bf16* __restrict__ dz4,
-                               int B, int H, int W) {
+// dA4 = up^T(dS5) (sum over each 2x2 block), times the ReLU mask of A4; grid over half resolution
+__global__ void __launch_bounds__(128) k_up2_bwd_mask(const bf16* __restrict__ ds5, const bf16* __restrict__ a4,
+                                                     bf16* __restrict__ dz4, int H, int W) {
   const int h = H / 2, w = W / 2;
-  const size_t n = size_t(B) * h * w * 32;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
-    const int c = int(i & 31);
-    const size_t q = i >> 5;
-    const int xx = int(q % w), yy = int((q / w) % h);
-    const size_t bb = q / (size_t(w) * h);
-    const size_t base = ((bb * H + 2 * yy) * W + 2 * xx) * 32 + c;
-    const float s = __bfloat162float(ds5[base]) + __bfloat162float(ds5[base + 32]) +
-                    __bfloat162float(ds5[base + size_t(W) * 32]) + __bfloat162float(ds5[base + size_t(W) * 32 + 32]);
-    dz4[i] = __float2bfloat16(__bfloat162float(a4[i]) > 0.0f ? s : 0.0f);
+  int b, yy, xx;
+  if (!pix_of(w, b, yy, xx)) return;
+  float s[32], a[32];
+  const size_t base = (size_t(b) * H + 2 * yy) * W + 2 * xx;
+  load32(ds5 + base * 32, s);
+  const size_t nb[3] = {base + 1, base + W, base + W + 1};
+  for (int k = 0; k < 3; ++k) {
+    load32(ds5 + nb[k] * 32, a);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) s[c] += a[c];
   }
+  const size_t q = ((size_t(b) * h + yy) * w + xx) * 32;
+  load32(a4 + q, a);
+#pragma unroll
+  for (int c = 0; c < 32; ++c) s[c] = a[c] > 0.0f ? s[c] : 0.0f;
+  store32(dz4 + q, s);
 }
 
 // squared-error loss between the output z and the target t; dz = 2 (z - t) / n; loss sum in out[0]
@@ -410,34 +600,37 @@ __global__ void k_to_bf16(const float* __restrict__ x, bf16* __restrict__ y, int
 }
 
 // input normalisation x = (g - b) / s and target t = log(1 + max(f, 0) / s) - log(1 + max(x, 0)):
-// the network predicts a correction to the log-transformed data (s per image)
+// the network predicts a correction to the log-transformed data (s per image); grid (chunks, B)
 __global__ void k_prep(const float* __restrict__ g, const float* __restrict__ f, const float* __restrict__ bvec,
-                       const float* __restrict__ svec, float* __restrict__ x, float* __restrict__ t, int B, size_t P) {
-  const size_t n = size_t(B) * P;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
-    const size_t bb = i / P;
-    const float s = svec[bb];
-    const float xi = (g[i] - bvec[bb]) / s;
-    x[i] = xi;
-    if (f) t[i] = log1pf(fmaxf(f[i], 0.0f) / s) - log1pf(fmaxf(xi, 0.0f));
+                       const float* __restrict__ svec, float* __restrict__ x, float* __restrict__ t, size_t P) {
+  const size_t o = size_t(blockIdx.y) * P;
+  const float s = svec[blockIdx.y], bb = bvec[blockIdx.y];
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < P; i += size_t(gridDim.x) * blockDim.x) {
+    const float xi = (g[o + i] - bb) / s;
+    x[o + i] = xi;
+    if (f) t[o + i] = log1pf(fmaxf(f[o + i], 0.0f) / s) - log1pf(fmaxf(xi, 0.0f));
   }
 }
 
 // f0 = s expm1(clamp(z + log(1 + max(x, 0)), 0, 20)) (the inverse of the target transform, bounded)
 __global__ void k_start(const float* __restrict__ z, const float* __restrict__ x, const float* __restrict__ svec,
-                        float* __restrict__ f0, int B, size_t P) {
-  const size_t n = size_t(B) * P;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
-    f0[i] = svec[i / P] * expm1f(fminf(fmaxf(z[i] + log1pf(fmaxf(x[i], 0.0f)), 0.0f), 20.0f));
+                        float* __restrict__ f0, size_t P) {
+  const size_t o = size_t(blockIdx.y) * P;
+  const float s = svec[blockIdx.y];
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < P; i += size_t(gridDim.x) * blockDim.x)
+    f0[o + i] = s * expm1f(fminf(fmaxf(z[o + i] + log1pf(fmaxf(x[o + i], 0.0f)), 0.0f), 20.0f));
 }
 
-// s[b] = 1 + mean over the image of max(g - b, 0) (input scale of the network), one block per image
-__global__ void __launch_bounds__(256) k_scale(const float* __restrict__ g, const float* __restrict__ bvec,
-                                              float* __restrict__ s, size_t P) {
-  const float* gb = g + size_t(blockIdx.x) * P;
-  const float bb = bvec[blockIdx.x];
-  double acc = 0.0;
-  for (size_t i = threadIdx.x; i < P; i += blockDim.x) acc += fmaxf(gb[i] - bb, 0.0f);
+// s[b] = 1 + mean over the image of max(g - b, 0) (input scale of the network): blocks (chunks, B)
+// add FP64 block sums of FP32 per-thread sums into a per-image accumulator; k_scale_final divides.
+constexpr int kScaleImages = 1024;            // images per ws_scale call
+__device__ double g_scale_acc[kScaleImages];
+__global__ void __launch_bounds__(256) k_scale(const float* __restrict__ g, const float* __restrict__ bvec, size_t P) {
+  const float* gb = g + size_t(blockIdx.y) * P;
+  const float bb = bvec[blockIdx.y];
+  float acc = 0.0f;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < P; i += size_t(gridDim.x) * blockDim.x)
+    acc += fmaxf(gb[i] - bb, 0.0f);
   __shared__ double r[256];
   r[threadIdx.x] = acc;
   __syncthreads();
@@ -445,8 +638,21 @@ __global__ void __launch_bounds__(256) k_scale(const float* __restrict__ g, cons
     if (threadIdx.x < o) r[threadIdx.x] += r[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) s[blockIdx.x] = float(1.0 + r[0] / double(P));
+  if (threadIdx.x == 0) atomicAdd(&g_scale_acc[blockIdx.y], r[0]);
 }
+__global__ void k_scale_final(float* __restrict__ s, int B, size_t P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  s[i] = float(1.0 + g_scale_acc[i] / double(P));
+  g_scale_acc[i] = 0.0;
+}
+
+// device-side error flag of the warm-start kernels: 1 when a bounded wait for the tensor cores
+// gave up (the results of that call are then undefined); read and cleared by ws_error
+__device__ int g_ws_err;
+
+int g_tc_ready[64] = {0};
+int g_sm_count[64] = {0};
 
 int grid1(size_t n) {
   const size_t g = (n + 255) / 256;
@@ -459,20 +665,43 @@ extern "C" {
 
 int ws_conv32(const void* x, const void* w, const float* bias, const void* mask, void* y, int B, int H, int W, int mode,
               void* stream) {
-  if (H % TH || W % TW || B <= 0 || mode < 0 || mode > 3) return 1;
-  const dim3 grid(W / TW, H / TH, B);
+  if (H % TCR || W % TCC || H <= 0 || W <= 0 || B <= 0 || mode < 0 || mode > 3) return 1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 4;
+  if (!g_tc_ready[dev]) {   // once per device: the kernels' shared-memory size and the SM count
+    if (cudaFuncSetAttribute(k_conv32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(k_conv32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(k_conv32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(k_conv32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g_sm_count[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return 4;
+    g_tc_ready[dev] = 1;
+  }
+  const long long ntiles = (long long)(W / TCC) * (H / TCR) * B;
+  if (ntiles > (1ll << 30)) return 1;
+  const int grid = int(std::min<long long>(ntiles, (long long)g_sm_count[dev] * TC_BLOCKS_PER_SM));
+  int* err = nullptr;
+  if (cudaGetSymbolAddress(reinterpret_cast<void**>(&err), g_ws_err) != cudaSuccess) return 4;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bf16* xb = static_cast<const bf16*>(x);
   const bf16* wb = static_cast<const bf16*>(w);
   const bf16* mb = static_cast<const bf16*>(mask);
   bf16* yb = static_cast<bf16*>(y);
   switch (mode) {
-    case 0: k_conv32<0><<<grid, 128, 0, s>>>(xb, wb, bias, mb, yb, H, W); break;
-    case 1: k_conv32<1><<<grid, 128, 0, s>>>(xb, wb, bias, mb, yb, H, W); break;
-    case 2: k_conv32<2><<<grid, 128, 0, s>>>(xb, wb, bias, mb, yb, H, W); break;
-    default: k_conv32<3><<<grid, 128, 0, s>>>(xb, wb, bias, mb, yb, H, W); break;
+    case 0: k_conv32<0><<<grid, 128, TC_SMEM, s>>>(xb, wb, bias, mb, yb, B, H, W, err); break;
+    case 1: k_conv32<1><<<grid, 128, TC_SMEM, s>>>(xb, wb, bias, mb, yb, B, H, W, err); break;
+    case 2: k_conv32<2><<<grid, 128, TC_SMEM, s>>>(xb, wb, bias, mb, yb, B, H, W, err); break;
+    default: k_conv32<3><<<grid, 128, TC_SMEM, s>>>(xb, wb, bias, mb, yb, B, H, W, err); break;
   }
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
+}
+
+int ws_error(int* out) {
+  int v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_ws_err, sizeof(int)) != cudaSuccess) return 4;
+  if (cudaMemcpyToSymbol(g_ws_err, &zero, sizeof(int)) != cudaSuccess) return 4;
+  if (out) *out = v;
+  return 0;
 }
 
 int ws_conv32_wgrad(const void* dy, const void* x, float* dw, int B, int H, int W, void* stream) {
@@ -490,18 +719,21 @@ int ws_flip_weights(const void* w, void* wt, void* stream) {
 }
 
 int ws_conv_in(const float* x, const float* w, const float* bias, void* y, int B, int H, int W, void* stream) {
-  k_conv_in<<<grid1(size_t(B) * H * W * 32), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, w, bias, static_cast<bf16*>(y), B, H, W);
+  if (B <= 0 || H <= 0 || W <= 0) return 1;
+  k_conv_in<<<pix_grid(B, H, W), 128, 0, static_cast<cudaStream_t>(stream)>>>(x, w, bias, static_cast<bf16*>(y), H, W);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
 }
 
 int ws_conv_out(const void* x, const float* w, const float* bias, float* z, int B, int H, int W, void* stream) {
-  k_conv_out<<<grid1(size_t(B) * H * W), 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const bf16*>(x), w, bias, z, B, H, W);
+  if (B <= 0 || H <= 0 || W <= 0) return 1;
+  k_conv_out<<<pix_grid(B, H, W), 128, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const bf16*>(x), w, bias, z, H, W);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
 }
 
 int ws_conv_out_dgrad(const float* dz, const float* w, const void* xin, void* dx, int B, int H, int W, void* stream) {
-  k_conv_out_dgrad<<<grid1(size_t(B) * H * W * 32), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      dz, w, static_cast<const bf16*>(xin), static_cast<bf16*>(dx), B, H, W);
+  if (B <= 0 || H <= 0 || W <= 0) return 1;
+  k_conv_out_dgrad<<<pix_grid(B, H, W), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+      dz, w, static_cast<const bf16*>(xin), static_cast<bf16*>(dx), H, W);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
 }
 
@@ -521,27 +753,31 @@ int ws_bias_grad(const void* dy, float* db, int B, int H, int W, void* stream) {
 }
 
 int ws_pool2(const void* x, void* y, int B, int H, int W, void* stream) {
-  k_pool2<<<grid1(size_t(B) * H * W * 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      static_cast<const bf16*>(x), static_cast<bf16*>(y), B, H, W);
+  if (B <= 0 || H < 2 || W < 2 || H % 2 || W % 2) return 1;
+  k_pool2<<<pix_grid(B, H / 2, W / 2), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+      static_cast<const bf16*>(x), static_cast<bf16*>(y), H, W);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
 }
 
 int ws_up2_add(const void* x, const void* skip, void* y, int B, int H, int W, void* stream) {
-  k_up2_add<<<grid1(size_t(B) * H * W * 32), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      static_cast<const bf16*>(x), static_cast<const bf16*>(skip), static_cast<bf16*>(y), B, H, W);
+  if (B <= 0 || H < 2 || W < 2 || H % 2 || W % 2) return 1;
+  k_up2_add<<<pix_grid(B, H, W), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+      static_cast<const bf16*>(x), static_cast<const bf16*>(skip), static_cast<bf16*>(y), H, W);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
 }
 
 int ws_junction_bwd(const void* ds5, const void* dp2, const void* a2, void* dz2, int B, int H, int W, void* stream) {
-  k_junction_bwd<<<grid1(size_t(B) * H * W * 32), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+  if (B <= 0 || H < 2 || W < 2 || H % 2 || W % 2) return 1;
+  k_junction_bwd<<<pix_grid(B, H, W), 128, 0, static_cast<cudaStream_t>(stream)>>>(
       static_cast<const bf16*>(ds5), static_cast<const bf16*>(dp2), static_cast<const bf16*>(a2), static_cast<bf16*>(dz2),
-      B, H, W);
+      H, W);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
 }
 
 int ws_up2_bwd_mask(const void* ds5, const void* a4, void* dz4, int B, int H, int W, void* stream) {
-  k_up2_bwd_mask<<<grid1(size_t(B) * H * W * 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      static_cast<const bf16*>(ds5), static_cast<const bf16*>(a4), static_cast<bf16*>(dz4), B, H, W);
+  if (B <= 0 || H < 2 || W < 2 || H % 2 || W % 2) return 1;
+  k_up2_bwd_mask<<<pix_grid(B, H / 2, W / 2), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+      static_cast<const bf16*>(ds5), static_cast<const bf16*>(a4), static_cast<bf16*>(dz4), H, W);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
 }
 
@@ -564,17 +800,24 @@ int ws_to_bf16(const float* x, void* y, int n, void* stream) {
 
 int ws_prep(const float* g, const float* f, const float* b, const float* s, float* x, float* t, int B, size_t P,
             void* stream) {
-  k_prep<<<grid1(size_t(B) * P), 256, 0, static_cast<cudaStream_t>(stream)>>>(g, f, b, s, x, t, B, P);
+  if (B <= 0 || B > 65535 || P == 0) return 1;
+  k_prep<<<dim3(unsigned((P + 255) / 256 < 1024 ? (P + 255) / 256 : 1024), B), 256, 0,
+           static_cast<cudaStream_t>(stream)>>>(g, f, b, s, x, t, P);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
 }
 
 int ws_start(const float* z, const float* x, const float* s, float* f0, int B, size_t P, void* stream) {
-  k_start<<<grid1(size_t(B) * P), 256, 0, static_cast<cudaStream_t>(stream)>>>(z, x, s, f0, B, P);
+  if (B <= 0 || B > 65535 || P == 0) return 1;
+  k_start<<<dim3(unsigned((P + 255) / 256 < 1024 ? (P + 255) / 256 : 1024), B), 256, 0,
+            static_cast<cudaStream_t>(stream)>>>(z, x, s, f0, P);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
 }
 
 int ws_scale(const float* g, const float* b, float* s, int B, size_t P, void* stream) {
-  k_scale<<<B, 256, 0, static_cast<cudaStream_t>(stream)>>>(g, b, s, P);
+  if (B <= 0 || B > kScaleImages || P == 0) return 1;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  k_scale<<<dim3(unsigned((P + 255) / 256 < 64 ? (P + 255) / 256 : 64), B), 256, 0, st>>>(g, b, P);
+  k_scale_final<<<(B + 127) / 128, 128, 0, st>>>(s, B, P);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
 }
 

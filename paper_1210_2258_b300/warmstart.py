@@ -50,6 +50,7 @@ def _lib():
         "ws_start": [vp, vp, vp, vp, i, sz, vp],
         "ws_scale": [vp, vp, vp, i, sz, vp],
         "ws_zero": [vp, sz, vp],
+        "ws_error": [C.POINTER(C.c_int)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -62,6 +63,13 @@ def _lib():
 def _ok(rc: int, what: str) -> None:
     if rc != 0:
         raise RuntimeError(f"{what} failed with code {rc}")
+
+
+def device_error() -> int:
+    """Read and clear the device-side error flag of the warm-start kernels (ws_error)."""
+    v = C.c_int()
+    _ok(_lib().ws_error(C.byref(v)), "ws_error")
+    return v.value
 
 
 def _p(t):
@@ -276,6 +284,33 @@ def train(net: WarmStartNet, g, f, b, epochs: int = 3, batch: int = 32, lr: floa
         if log:
             log(f"epoch {ep}: loss {losses[-1]:.4e}")
     return losses
+
+
+def train_crops(net: WarmStartNet, g, f, b, steps: int = 200, crop: int = 512, batch: int = 8, lr: float = 2e-3,
+                seed: int = 0) -> list[float]:
+    """Adam on random crop x crop windows of (g, f) pairs of larger images (B, H, W CUDA tensors):
+    the network is local (3 x 3 convolutions, one 2 x 2 pooling level), so windows of the images
+    teach it the same mapping at a fraction of the cost of whole images.  lr halves at 1/2 and 3/4
+    of the steps.  Returns the loss of each step."""
+    import torch
+    n, H, W = g.shape
+    rng = np.random.default_rng(seed)
+    losses = []
+    gb = torch.empty((batch, crop, crop), dtype=torch.float32, device=g.device)
+    fb = torch.empty_like(gb)
+    bb = torch.empty(batch, dtype=torch.float32, device=g.device)
+    for step in range(steps):
+        for k in range(batch):
+            i = int(rng.integers(n))
+            y0, x0 = int(rng.integers(0, H - crop + 1)), int(rng.integers(0, W - crop + 1))
+            gb[k].copy_(g[i, y0:y0 + crop, x0:x0 + crop])
+            fb[k].copy_(f[i, y0:y0 + crop, x0:x0 + crop])
+            bb[k] = b[i]
+        bf = net.prepare(gb, bb, fb)
+        net.loss_and_grad(bf, batch, crop, crop)
+        net.adam(lr * (0.5 if step >= steps // 2 else 1.0) * (0.5 if step >= 3 * steps // 4 else 1.0))
+        losses.append(bf["loss"].clone())
+    return [float(x.item()) / (batch * crop * crop) for x in losses]
 
 
 LAND_TOL = 1e-5   # both starts end with the discrepancy in [1 - LAND_TOL, 1]: equal final KL

@@ -56,3 +56,29 @@ def test_trained_warm_start_reduces_iterations(gpu):
     done = (ev["flat_iters"] < 2000) & (ev["warm_iters"] < 2000)
     assert done.sum() >= 12
     assert ev["warm_iters"][done].mean() < ev["flat_iters"][done].mean()
+
+
+def test_adam_kernel_matches_oracle(gpu):
+    """ws_adam (FP32) against the FP64 Adam of the oracle over four steps of varied gradients."""
+    import torch
+    from paper_1210_2258_b300 import warmstart as W
+    rng = np.random.default_rng(5)
+    n = 9000
+    p0 = rng.standard_normal(n).astype(np.float32)
+    gs = [(rng.standard_normal(n) * 10.0 ** rng.uniform(-4, 1, n)).astype(np.float32) for _ in range(4)]
+    p = torch.from_numpy(p0.copy()).cuda()
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    L = W._lib()
+    for t, g in enumerate(gs, start=1):
+        gd = torch.from_numpy(g).cuda()
+        assert L.ws_adam(p.data_ptr(), m.data_ptr(), v.data_ptr(), gd.data_ptr(), n, 1e-3, 0.9, 0.999, 1e-8, t,
+                         torch.cuda.current_stream().cuda_stream) == 0
+    torch.cuda.synchronize()
+    # the kernel receives lr, beta1, beta2 and eps as float32: the oracle runs with those values
+    f32 = lambda x: float(np.float32(x))
+    rp, rm, rv = WO.adam(p0.astype(np.float64), [g.astype(np.float64) for g in gs], f32(1e-3), b1=f32(0.9),
+                         b2=f32(0.999), eps=f32(1e-8))
+    assert np.max(np.abs(p.double().cpu().numpy() - rp)) <= 1e-6 * np.max(np.abs(rp)) + 1e-7
+    assert rel_l2(m.double().cpu().numpy(), rm) <= 1e-6
+    assert rel_l2(v.double().cpu().numpy(), rv) <= 1e-6
