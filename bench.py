@@ -193,7 +193,7 @@ def warm_arm(torch, lib, psf_d, g_d, b, train_imgs, flush, reps):
     tr.close()
     bt = torch.full((gt.shape[0],), b, dtype=torch.float32, device="cuda")
     net = ws.WarmStartNet(seed=0)
-    losses = ws.train_crops(net, gt, ft, bt, steps=240, crop=512, batch=8, lr=2e-3, seed=0)
+    losses = ws.train_crops(net, gt, ft, bt, steps=1600, crop=512, batch=8, lr=2e-3, seed=0)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del gt, ft
@@ -256,7 +256,8 @@ def warm_arm(torch, lib, psf_d, g_d, b, train_imgs, flush, reps):
     out["warm"]["faster_than_plain_fp32"] = out["warm"]["time_to_stop_ms"] < out["plain_fp32"]["time_to_stop_ms"]
     out["stop"] = "landed discrepancy stop: eta = 1, final discrepancy in [1 - 1e-5, 1]"
     out["training"] = {"images": len(train_imgs), "side": N, "sgp_mean_iterations": float(np.mean(its)),
-                       "steps": len(losses), "crop": 512, "batch": 8, "loss_first_last": [losses[0], losses[-1]],
+                       "steps": len(losses), "crop": 512, "batch": 8,
+                       "loss_first_last_10": [float(np.mean(losses[:10])), float(np.mean(losses[-10:]))],
                        "seconds": t_train}
     return out
 
@@ -677,13 +678,17 @@ def run_other_workload(args):
         pr = lib.Problems(dev(sc.psfs), list(map(float, sc.b)))
         pr.set_data(0, dev(sc.g))
 
+        # Eq. (convergence) with tol = 1e-5, the rule of the paper's multi-view star-cluster runs
+        # (Sect. 4, Table 7): this scene's discrepancy never falls to 1 (the band-limited PSFs
+        # leave the noise outside their support unfitted), so the discrepancy rule would not fire
         def solve():
             pr.set_start(0, lib.START_CONSTANT)
-            return pr.solve_until(lib.STOP_DISCREPANCY, max_iter=5000, eta=1.0, raise_on_error=False)[0]
+            return pr.solve_until(lib.STOP_CONVERGENCE, max_iter=5000, tol=1e-5, raise_on_error=False)[0]
         for _ in range(args.warmup):
             solve()
         ms, it = _timed(torch, solve, args.steps)
         D_sgp = pr.info().D
+        stopped = int(pr.info().stopped)
         # multiple RL and OSEM (Algorithm 2, 4p transforms per iteration) from the same start, a fixed
         # count each (the paper compares the three methods on this kind of workload, Table 5)
         n_fix = 50
@@ -697,8 +702,8 @@ def run_other_workload(args):
             ms_m, _ = _timed(torch, run, args.steps)
             fixed[method] = {"iterations": n_fix, "ms_incl_setup": ms_m, "us_per_iteration": 1e3 * ms_m / n_fix,
                              "iters_per_s": n_fix / (ms_m / 1e3), "final_discrepancy": pr.info().D}
-        line.update({"metric": "3 x 1024^2 multi-view SGP to the discrepancy stop", "unit": "iter/s",
-                     "value": it / (ms / 1e3), "time_to_stop_ms": ms, "iterations": it,
+        line.update({"metric": "3 x 1024^2 multi-view SGP to the convergence stop (tol 1e-5)", "unit": "iter/s",
+                     "value": it / (ms / 1e3), "time_to_stop_ms": ms, "iterations": it, "stopped": stopped,
                      "final_discrepancy": D_sgp, "tile": pr.tile(), "rl": fixed["rl"], "osem": fixed["osem"],
                      "config": {"N": 1024, "p": 3, "psf": "two-pupil |FFT|^2 at 0/60/120 deg", "b": 20}})
     elif args.workload == "mosaic256":
@@ -743,17 +748,17 @@ def run_other_workload(args):
         def solve():
             for i in range(len(scs)):
                 pr.set_start(i, lib.START_CONSTANT)
-            return pr.solve_until(lib.STOP_DISCREPANCY, max_iter=3000, eta=1.0, raise_on_error=False)
+            return pr.solve_until(lib.STOP_CONVERGENCE, max_iter=3000, tol=1e-5, raise_on_error=False)
         for _ in range(args.warmup):
             solve()
         ms, its = _timed(torch, solve, args.steps)
         px = sum(int(np.prod(s.g.shape[-2:])) for s in scs)
         pix_it = sum(int(np.prod(s.g.shape[-2:])) * k for s, k in zip(scs, its))
-        line.update({"metric": "batch of 64 boundary problems (sides 128..1024 padded), discrepancy stop",
+        line.update({"metric": "batch of 64 boundary problems (sides 128..1024 padded), convergence stop (tol 1e-5)",
                      "unit": "Mpixel-iterations/s", "value": pix_it / (ms / 1e3) / 1e6,
                      "time_to_all_stopped_ms": ms, "iterations_min_max_mean": [int(min(its)), int(max(its)),
                                                                               float(np.mean(its))],
-                     "padded_pixels": px, "not_stopped": int(sum(k >= 3000 for k in its)),
+                     "padded_pixels": px, "not_stopped": int(sum(1 - pr.info(i).stopped for i in range(len(scs)))),
                      "config": {"count": 64, "sides": [128, 256, 384, 512, 768, 1024], "psf": "Gaussian sigma U[1,4]",
                                 "b": "U[5,50]", "mask": "0/1 M_S, extended domain"}})
     print(json.dumps(line))

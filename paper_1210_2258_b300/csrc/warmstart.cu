@@ -382,23 +382,48 @@ __global__ void __launch_bounds__(128) k_conv_in(const float* __restrict__ x, co
   store32(y + ((size_t(b) * H + yy) * W + xx) * 32, o);
 }
 
-// output layer 32 -> 1: Z[p] = sum_{tap, ci} X[p + off][ci] W[tap][ci] + b (FP32 out)
-__global__ void __launch_bounds__(128) k_conv_out(const bf16* __restrict__ x, const float* __restrict__ w,
+// output layer 32 -> 1: Z[p] = sum_{tap, ci} X[p + off][ci] W[tap][ci] + b (FP32 out), written as
+// Z[p] = b + sum_tap u_tap[p + off(tap)] with u_tap[q] = X[q] . W[tap]: a block of 16 x 16 output
+// pixels loads each pixel of its 18 x 18 halo once, forms its nine dot products in shared memory,
+// and every output pixel adds the nine of its neighbours.
+constexpr int OT = 16, OH = OT + 2;
+__global__ void __launch_bounds__(256) k_conv_out(const bf16* __restrict__ x, const float* __restrict__ w,
                                                  const float* __restrict__ bias, float* __restrict__ z, int H, int W) {
   __shared__ float sw[288];
+  __shared__ float u[9][OH * OH];
   for (int i = threadIdx.x; i < 288; i += blockDim.x) sw[i] = w[i];
   __syncthreads();
-  int b, yy, xx;
-  if (!pix_of(W, b, yy, xx)) return;
-  float s = bias[0];
-  for (int tap = 0; tap < 9; ++tap) {
-    const int u = yy + tap / 3 - 1, v = xx + tap % 3 - 1;
-    if (u < 0 || u >= H || v < 0 || v >= W) continue;
-    float a[32];
-    load32(x + ((size_t(b) * H + u) * W + v) * 32, a);
+  const int x0 = blockIdx.x * OT, y0 = blockIdx.y * OT, b = blockIdx.z;
+  for (int hp = threadIdx.x; hp < OH * OH; hp += blockDim.x) {
+    const int yy = y0 + hp / OH - 1, xx = x0 + hp % OH - 1;
+    float d[9];
 #pragma unroll
-    for (int ci = 0; ci < 32; ++ci) s = fmaf(a[ci], sw[tap * 32 + ci], s);
+    for (int t = 0; t < 9; ++t) d[t] = 0.0f;
+    if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+      const int4* src = reinterpret_cast<const int4*>(x + ((size_t(b) * H + yy) * W + xx) * 32);
+#pragma unroll 1
+      for (int q = 0; q < 4; ++q) {          // 8 channels at a time
+        const int4 v = src[q];
+        const uint32_t w4[4] = {uint32_t(v.x), uint32_t(v.y), uint32_t(v.z), uint32_t(v.w)};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const uint16_t h = uint16_t(k & 1 ? w4[k >> 1] >> 16 : w4[k >> 1] & 0xffff);
+          const float a = __bfloat162float(__ushort_as_bfloat16(h));
+#pragma unroll
+          for (int t = 0; t < 9; ++t) d[t] = fmaf(a, sw[t * 32 + 8 * q + k], d[t]);
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 9; ++t) u[t][hp] = d[t];
   }
+  __syncthreads();
+  const int ty = threadIdx.x / OT, tx = threadIdx.x % OT;
+  const int yy = y0 + ty, xx = x0 + tx;
+  if (yy >= H || xx >= W) return;
+  float s = bias[0];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) s += u[t][(ty + t / 3) * OH + tx + t % 3];
   z[(size_t(b) * H + yy) * W + xx] = s;
 }
 
@@ -726,7 +751,9 @@ int ws_conv_in(const float* x, const float* w, const float* bias, void* y, int B
 
 int ws_conv_out(const void* x, const float* w, const float* bias, float* z, int B, int H, int W, void* stream) {
   if (B <= 0 || H <= 0 || W <= 0) return 1;
-  k_conv_out<<<pix_grid(B, H, W), 128, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const bf16*>(x), w, bias, z, H, W);
+  if (B > 65535) return 1;
+  k_conv_out<<<dim3((W + OT - 1) / OT, (H + OT - 1) / OT, B), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      static_cast<const bf16*>(x), w, bias, z, H, W);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
 }
 
@@ -816,7 +843,9 @@ int ws_start(const float* z, const float* x, const float* s, float* f0, int B, s
 int ws_scale(const float* g, const float* b, float* s, int B, size_t P, void* stream) {
   if (B <= 0 || B > kScaleImages || P == 0) return 1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  k_scale<<<dim3(unsigned((P + 255) / 256 < 64 ? (P + 255) / 256 : 64), B), 256, 0, st>>>(g, b, P);
+  const size_t per_image = (P + 255) / 256 < 1024 ? (P + 255) / 256 : 1024;
+  const size_t chunks = std::max<size_t>(1, std::min<size_t>(per_image, (size_t(148) * 8 + B - 1) / B));
+  k_scale<<<dim3(unsigned(chunks), B), 256, 0, st>>>(g, b, P);
   k_scale_final<<<(B + 127) / 128, 128, 0, st>>>(s, B, P);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 4;
 }
