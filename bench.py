@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling driver: set up the workload, run this many SGP iterations, exit")
     ap.add_argument("--workload", default="galaxy2048",
-                    choices=["galaxy2048", "stars256", "multiview1024", "batch64", "mosaic256"],
+                    choices=["galaxy2048", "stars256", "multiview1024", "batch64", "mosaic256", "warmnet"],
                     help="galaxy2048: the headline line (default); the others print one line each for the "
                          "other configurations (256^2 star field RL/SGP 200 iterations, 3 x 1024^2 multi-view "
                          "SGP to the discrepancy stop, a batch of 64 boundary problems of mixed sizes)")
@@ -657,6 +657,8 @@ def run_other_workload(args):
     lib.load()
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(np.asarray(a, np.float32))).cuda()
     line = {"workload": args.workload, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic"}
+    if args.workload == "warmnet":
+        return run_warmnet(args, torch, lib, line)
     if args.workload == "stars256":
         sc = scenes.stars_scene(seed=args.seed, N=256)
         out = {}
@@ -761,6 +763,71 @@ def run_other_workload(args):
                      "padded_pixels": px, "not_stopped": int(sum(1 - pr.info(i).stopped for i in range(len(scs)))),
                      "config": {"count": 64, "sides": [128, 256, 384, 512, 768, 1024], "psf": "Gaussian sigma U[1,4]",
                                 "b": "U[5,50]", "mask": "0/1 M_S, extended domain"}})
+    print(json.dumps(line))
+    return 0
+
+
+def run_warmnet(args, torch, lib, line):
+    """The warm-start network's 32 -> 32 convolutions (include/warmstart.h) on their own: forward
+    (tcgen05, bias + ReLU), data gradient (tcgen05, ReLU mask of the layer below) and weight
+    gradient, at the benchmark arm's shape (one 2048^2 image) and at a training batch (32 x 256^2),
+    plus the whole forward pass.  FLOPs 2 x pixels x 32 x 288; algorithmic bytes = the activation
+    read and written once (64 B + 64 B per pixel; the mask adds 64 B for the data gradient, the
+    weight gradient reads two activations and writes 37 KB)."""
+    from paper_1210_2258_b300 import warmstart as ws
+    peak_tf = None
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as fh:
+            peak_tf = float(json.load(fh)["bf16_tflops"])
+    hbm, hbm_kind = measured_peaks()
+    net = ws.WarmStartNet(seed=0)
+    L = ws._lib()
+    s = torch.cuda.current_stream().cuda_stream
+    shapes = {}
+    for B, H in ((1, 2048), (32, 256)):
+        bf = net.buffers(B, H, H)
+        for k in ("a1", "d5", "s5"):
+            bf[k].copy_((torch.rand(bf[k].shape, device="cuda") - 0.3).to(torch.bfloat16))
+        wb, wt = net.wb["w2"], net.wt["w2"]
+        bias = net.view(net.p, "b2")
+        gw = net.view(net.g, "w2")
+        ops = {
+            "forward": (lambda: L.ws_conv32(bf["a1"].data_ptr(), wb.data_ptr(), bias.data_ptr(), None,
+                                            bf["a2"].data_ptr(), B, H, H, 0, s), 128),
+            "dgrad": (lambda: L.ws_conv32(bf["d5"].data_ptr(), wt.data_ptr(), None, bf["a1"].data_ptr(),
+                                          bf["ds5"].data_ptr(), B, H, H, 2, s), 192),
+            "wgrad": (lambda: L.ws_conv32_wgrad(bf["d5"].data_ptr(), bf["s5"].data_ptr(), gw.data_ptr(), B, H, H, s),
+                      128),
+        }
+        npx = B * H * H
+        res = {}
+        for name, (fn, bpp) in ops.items():
+            for _ in range(args.warmup):
+                assert fn() == 0
+            ms, _ = _timed(torch, lambda: fn(), max(args.steps, 5))
+            tf = 2.0 * npx * 32 * 288 / (ms * 1e9)
+            gbs = bpp * npx / (ms * 1e6)
+            res[name] = {"us": 1e3 * ms, "tflops": tf, "gbs": gbs, "frac_hbm": gbs / hbm,
+                         "frac_bf16": (tf / peak_tf) if peak_tf else None}
+        g = (torch.rand((B, H, H), device="cuda") * 100 + 50).contiguous()
+        bv = torch.full((B,), 50.0, device="cuda")
+        for _ in range(args.warmup):
+            net.predict(g, bv)
+        ms, _ = _timed(torch, lambda: net.predict(g, bv), max(args.steps, 5))
+        res["forward_pass_ms"] = ms
+        shapes[f"{B}x{H}^2"] = res
+        del bf
+        net._bufs.clear()
+    assert ws.device_error() == 0
+    f = shapes["1x2048^2"]["forward"]
+    line.update({"metric": "warm-start network: 32->32 conv (tcgen05) and forward pass", "unit": "TFLOP/s",
+                 "value": f["tflops"], "higher_is_better": True, "dtype": "bf16 (FP32 accumulation)",
+                 "shapes": shapes,
+                 "roofline": {"bound": "hbm", "kernel": "k_conv32<0> (forward, 1 x 2048^2)", "achieved": f["gbs"],
+                              "peak": hbm, "unit": "GB/s", "frac": f["frac_hbm"], "peak_source": hbm_kind,
+                              "tensor_tflops": f["tflops"], "tensor_frac_of_bf16_burst": f["frac_bf16"]},
+                 "config": {"layer": "3x3, 32 -> 32 channels, bf16 NHWC, same padding", "tile": "16 x 8 pixels"}})
     print(json.dumps(line))
     return 0
 
