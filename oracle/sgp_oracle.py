@@ -41,6 +41,10 @@ Readings of places where the paper is silent or garbled (all stated again in the
   * flux-constrained projection (the paper defers it to Bonettini et al.): the D^-1-weighted
     projection onto {y >= 0, sum y = c}, y_i = max(0, x_i - mu D_i), mu solved exactly from the
     sorted breakpoints.
+  * regularised SGP (Sect. 5 names the extension and the split-gradient scaling of Lanteri et al.,
+    no regulariser): J_0 + beta/2 ||f||^2 (Tikhonov); split grad = V - U with V = sum_j A_j^T 1 +
+    beta f, U = sum_j A_j^T r_j, scaling D = clip(f)/V_bar with V_bar = sum_j A_j^T 1 + beta clip(f);
+    the Armijo test and the convergence rule use J_0 + R, the discrepancy rule J_0 alone.
 """
 from __future__ import annotations
 
@@ -262,6 +266,7 @@ class SGPParams:
     L2: float = 1e10
     max_backtracks: int = 30
     flux: float | None = None      # None: non-negativity only; else the flux constraint sum f = flux
+    reg_beta: float = 0.0          # > 0: minimise J_0 + reg_beta/2 ||f||^2 (Tikhonov, SGM scaling)
 
 
 @dataclass
@@ -366,6 +371,36 @@ def flux_projection(x: np.ndarray, D: np.ndarray, c: float) -> np.ndarray:
     return y
 
 
+# ----------------------------------------------------------------------------- regularisation (Sect. 5)
+def reg_value(f: np.ndarray, beta: float) -> float:
+    """Tikhonov term J_R = beta/2 sum f^2 (reading of the regularised SGP of Sect. 5: the paper names
+    no regularisation function; this is the simplest one whose split-gradient scaling is explicit)."""
+    return 0.5 * beta * float(np.sum(f * f))
+
+
+def sgm_split(prob: "Problem", f: np.ndarray, beta: float):
+    """Split-gradient decomposition grad J = V - U with V, U >= 0 for f >= 0 (Lanteri et al., cited in
+    Sect. 5): for J_0, V_0 = sum_j A_j^T 1 and U_0 = sum_j A_j^T (g_j/(A_j f + b_j)) (Eq. KLgrad); for
+    beta/2 ||f||^2, V_R = beta f and U_R = 0.  Returns (V, U)."""
+    V = np.zeros((prob.H, prob.W))
+    U = np.zeros((prob.H, prob.W))
+    ones = np.ones((prob.H, prob.W))
+    for j in range(prob.p):
+        V += prob.AT(j, ones)
+        U += prob.AT(j, prob.ratio(j, prob.A(j, f)))
+    return V + beta * f, U
+
+
+def sgm_scaling(prob: "Problem", f: np.ndarray, L1: float, L2: float, beta: float) -> np.ndarray:
+    """SGP scaling built from the split: D = c / V_bar with c = clip(f, L1, L2) and
+    V_bar = (sum_j A_j^T 1) + beta c, i.e. D = w c / (1 + beta w c) with w = M_R/alpha (1/p periodic),
+    0 outside R.  With beta = 0 it is w clip(f, L1, L2), the scaling of Eq. (Dk)/(Dkbound)."""
+    c = np.minimum(L2, np.maximum(L1, f))
+    if beta == 0.0:
+        return prob.w * c
+    return prob.w * c / (1.0 + beta * prob.w * c)
+
+
 # ----------------------------------------------------------------------------- SGP
 @dataclass
 class Result:
@@ -425,7 +460,9 @@ def sgp(prob: Problem, f0: np.ndarray | None = None, P: SGPParams | None = None,
     else:
         L1, L2 = P.L1, P.L2
     Afs = [prob.A(j, f) for j in range(prob.p)]
+    beta_r = P.reg_beta
     J = prob.kl(f, Afs)
+    R = reg_value(f, beta_r)               # the objective is J + R (R = 0 without regularisation)
     trace = []
     st = AlphaState(alpha_prev=P.alpha0, tau=P.tau1)
     g_prev = f_prev = None
@@ -434,9 +471,9 @@ def sgp(prob: Problem, f0: np.ndarray | None = None, P: SGPParams | None = None,
         return Result(f, 0, J, trace, L1=L1, L2=L2)
     k = 0
     while k < stop.max_iter:
-        grad = prob.grad(f)
-        # step 1: scaling Eq. (Dk)/(Dkbound) and step length
-        D = prob.w * np.minimum(L2, np.maximum(L1, f))
+        grad = prob.grad(f) + beta_r * f
+        # step 1: scaling Eq. (Dk)/(Dkbound) (with a regulariser: the split-gradient scaling) and step length
+        D = sgm_scaling(prob, f, L1, L2, beta_r)
         if k == 0:
             alpha, branch = P.alpha0, 0
             st.alpha_prev = alpha
@@ -454,7 +491,8 @@ def sgp(prob: Problem, f0: np.ndarray | None = None, P: SGPParams | None = None,
             fl = f + lam * d
             Afl = [prob.A(j, fl) for j in range(prob.p)]
             Jn = prob.kl(fl, Afl)
-            if Jn <= J + P.beta * lam * gTd:
+            Rn = reg_value(fl, beta_r)
+            if Jn + Rn <= J + R + P.beta * lam * gTd:
                 break
             nb += 1
             if nb > P.max_backtracks:
@@ -462,20 +500,22 @@ def sgp(prob: Problem, f0: np.ndarray | None = None, P: SGPParams | None = None,
             lam *= P.theta
         if stop.kind == "landed" and prob.discrepancy(Jn) <= stop.eta:
             lam, Jn, fl = _land(prob, f, d, J, lam, Jn, stop)
+            Rn = reg_value(fl, beta_r)
         # step 6
         f_prev, g_prev = f, grad
         f = fl
-        J_old, J = J, Jn
+        J0_old, J_old = J, J + R             # J_0 and the objective J_0 + R before the step
+        J, R = Jn, Rn
         k += 1
         trace.append(dict(k=k, J=J, D=prob.discrepancy(J), alpha=alpha, lam=lam,
-                          backtracks=nb, branch=branch, gTd=gTd))
+                          backtracks=nb, branch=branch, gTd=gTd, R=R))
         if stop.kind == "min_error":
             rho = _rel_err(f, stop.f_true)
             trace[-1]["rho"] = rho
             if rho > rho_prev:
-                return Result(f_prev, k - 1, J_old, trace, L1=L1, L2=L2)
+                return Result(f_prev, k - 1, J0_old, trace, L1=L1, L2=L2)
             rho_prev = rho
-        if _stop_check(stop, k, J_old, J, prob.discrepancy(J)):
+        if _stop_check(stop, k, J_old, J + R, prob.discrepancy(J)):
             break
     return Result(f, k, J, trace, L1=L1, L2=L2)
 
