@@ -109,6 +109,12 @@ typedef struct {
                          * optical transfer function vanishes beyond the pupil's autocorrelation)
                          * a large saving; the dropped entries lie below the FP32 transforms' own
                          * rounding.  0 keeps every column. */
+  double reg_beta;      /* regularised SGP (Sect. 5 names the extension and its split-gradient scaling;
+                         * the regulariser is this library's reading): 0 = the method above (default);
+                         * > 0 minimises J_0 + reg_beta/2 ||f||^2 with the split-gradient scaling
+                         * D = w c / (1 + reg_beta w c), c = clip(f, L1, L2), the gradient J_0' + reg_beta f;
+                         * the Armijo test and the convergence rule use J_0 + R, R = reg_beta/2 ||f||^2,
+                         * the discrepancy rules J_0 alone.  RL and OSEM calls return SGP_ERR_ARG. */
 } sgp_params;
 
 typedef struct {
@@ -137,6 +143,7 @@ typedef struct {
   double nS;             /* |S| (pixels of the detected image) */
   double flux_c;         /* constant start value c of Sect. 3.1 */
   int band_cols;         /* spectrum columns processed by the iteration (W/2 = all; see band_tol) */
+  double reg;            /* reg_beta/2 ||f||^2 at the current iterate (0 without regularisation) */
 } sgp_info;
 
 /* Fill *out with the parameter values of Sect. 3.2. */

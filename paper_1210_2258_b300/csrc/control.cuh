@@ -93,6 +93,7 @@ __device__ void sgp_begin_decide(CtrlState* c, const double (&kl)[2]) {
     c->k += 1;
     c->fresh = 1;
     c->f_pending = f_update_in_k1(c, done) ? 0 : 1;
+    c->R = c->R_pred;                 // the Tikhonov term moves with the step (exact in lambda)
   }
   if (done == 1) { c->done = 2; c->J = c->J_pred; return; }
   if (!isfinite(kl[0])) {   // stop at the last stored iterate (a pending f^(k) is not formed)
@@ -145,18 +146,27 @@ __device__ void ctrl_sgp_alpha(const ImgDesc& d) {
   CtrlCopy::write_back(s, d.ctrl);
 }
 
+// Change of the Tikhonov term beta/2 ||f||^2 along the step: R(f + lam d) - R(f) =
+// beta (lam f'd + lam^2/2 d'd), exact in lam (0 without regularisation)
+__device__ __forceinline__ double reg_delta(const CtrlState* c, double lam) {
+  return c->reg_beta > 0.0 ? c->reg_beta * (lam * c->reg_fd + 0.5 * lam * lam * c->reg_dd) : 0.0;
+}
+
 __device__ inline void sgp_accept(const ImgDesc& d, CtrlState* c, int nb, double lam, double dJ) {
   c->lambda = lam;
   c->backtracks = nb;
   c->dJ = dJ;
   c->J_pred = c->J + dJ;
+  c->R_pred = c->R + reg_delta(c, lam);
   c->fresh = 0;                       // f^(k+1) = f^(k) + lambda d is applied by the next K1
   c->need_more = 0;
   c->arm_nl = nb == 0 ? 1 : (nb == 1 ? 2 : kArmMain);
   const int kn = c->k + 1;
   trace_push(d, c, kn, c->J_pred, c->alpha, lam, nb, c->branch, c->gTd);
   bool rule = false;                  // the stop rule itself fired (not only the iteration cap)
-  if (c->stop_kind == STOP_CONVERGENCE && fabs(c->J_pred - c->J) <= c->tol * c->J) rule = true;
+  // Eq. (convergence) on the objective J_0 + R (R = 0 without regularisation)
+  if (c->stop_kind == STOP_CONVERGENCE &&
+      fabs((c->J_pred + c->R_pred) - (c->J + c->R)) <= c->tol * (c->J + c->R)) rule = true;
   if ((c->stop_kind == STOP_DISCREPANCY || c->stop_kind == STOP_LANDED) && 2.0 * c->J_pred * c->inv_pS <= c->eta) {
     rule = true;
     c->capped = 0;
@@ -196,6 +206,7 @@ __device__ inline void sgp_land_decide(const ImgDesc& d, CtrlState* c, const dou
   c->lambda = lam;
   c->dJ = Jp - c->J;
   c->J_pred = Jp;
+  c->R_pred = c->R + reg_delta(c, lam);
   c->land_pass = 0;
   c->done = 1;
   if (c->trace_n >= 1 && c->trace_n <= c->trace_cap) {   // the record sgp_accept wrote
@@ -221,8 +232,9 @@ __device__ void sgp_lambda_decide(const ImgDesc& d, CtrlState* c, double gTd, co
   double lam = 1.0;
   const int nl = arm_count(c);
   for (int i = 0; i < nl && i <= c->max_backtracks; ++i) {
-    const bool ok = FP64 ? (arm[i] <= c->beta * lam * gTd)
-                         : (float(arm[i]) <= float(c->beta) * float(lam) * float(gTd));
+    const double dobj = arm[i] + reg_delta(c, lam);   // change of J_0 + R
+    const bool ok = FP64 ? (dobj <= c->beta * lam * gTd)
+                         : (float(dobj) <= float(c->beta) * float(lam) * float(gTd));
     if (ok) { sgp_accept(d, c, i, lam, arm[i]); return; }
     lam *= c->theta;
   }
@@ -232,11 +244,16 @@ template <bool FP64>
 __device__ void ctrl_sgp_lambda(const ImgDesc& d) {
   __shared__ CtrlState s;
   const CtrlCopy cp(d.ctrl);
-  double g[1], arm[kArmMain];
+  double g[1], arm[kArmMain], rg[2] = {0.0, 0.0};
   ctrl_sum<1, FP64>(d, SLOT_GTD, g, false);
   ctrl_sum<kArmMain, FP64>(d, SLOT_ARM, arm, true);
+  if (d.reg_beta > 0.0f) ctrl_sum<2, FP64>(d, SLOT_REG, rg, false);   // f'd, d'd of this direction
   cp.to_shared(s);
-  if (threadIdx.x == 0) sgp_lambda_decide<FP64>(d, &s, g[0], arm);
+  if (threadIdx.x == 0) {
+    s.reg_fd = rg[0];
+    s.reg_dd = rg[1];
+    sgp_lambda_decide<FP64>(d, &s, g[0], arm);
+  }
   CtrlCopy::write_back(s, d.ctrl);
 }
 
@@ -247,8 +264,9 @@ __device__ void sgp_lambda_extra_decide(const ImgDesc& d, CtrlState* c, const do
   for (int i = 0; i < nl; ++i) lam *= c->theta;
   const double gTd = c->gTd;
   for (int i = 0; i < kArmExtra && nl + i <= 30 && nl + i <= c->max_backtracks; ++i) {
-    const bool ok = FP64 ? (arm[i] <= c->beta * lam * gTd)
-                         : (float(arm[i]) <= float(c->beta) * float(lam) * float(gTd));
+    const double dobj = arm[i] + reg_delta(c, lam);
+    const bool ok = FP64 ? (dobj <= c->beta * lam * gTd)
+                         : (float(dobj) <= float(c->beta) * float(lam) * float(gTd));
     if (ok) { sgp_accept(d, c, nl + i, lam, arm[i]); return; }
     lam *= c->theta;
   }

@@ -20,7 +20,11 @@ __global__ void __launch_bounds__(kCtrlBlock) k_ctrl_setup(const ImgDesc* __rest
   ctrl_sum<1, FP64>(d, SLOT_KL, s, true);
   double mn = 0.0, mx = 0.0;
   if (want_bounds) ctrl_minmax(d, mn, mx);
+  double q[1] = {0.0};
+  if (d.reg_beta > 0.0f) ctrl_sum<1, FP64>(d, SLOT_FSQ, q, false);   // f'f of the start
   if (threadIdx.x != 0) return;
+  c->R = 0.5 * c->reg_beta * q[0];
+  c->R_pred = c->R;
   c->J = s[0];
   c->J_prev = s[0];
   if (!isfinite(s[0])) { c->status = 8; c->done = 2; return; }
@@ -58,7 +62,7 @@ __global__ void k_ctrl_arm(const ImgDesc* __restrict__ imgs, int n, int kind, in
 __device__ __forceinline__ void flux_xd(const ImgDesc& d, const CtrlState* c, size_t i, float& x, float& D) {
   const float f = d.f[c->k & 1][i], gr = d.grad[c->k & 1][i];
   const float w = d.w ? d.w[i] : d.w_scalar;
-  D = w * clipf(f, float(c->L1), float(c->L2));
+  D = scale_of(f, w, float(c->L1), float(c->L2), d.reg_beta);
   x = f - float(c->alpha) * D * gr;
 }
 

@@ -369,9 +369,17 @@ __device__ __forceinline__ float2 w_pair(const ImgDesc& d, size_t i) {
 __device__ __forceinline__ float2 b_pair(const ImgDesc& d, int j, size_t i) {
   return d.b ? ld2(d.b + size_t(j) * d.P, i) : make_float2(d.bs[j], d.bs[j]);
 }
-// y = P(f - alpha D grad), D = w clip(f): non-negativity (mu = 0) or flux (mu from the search)
-__device__ __forceinline__ float proj_step(float f, float gr, float w, float alpha, float mu, float L1, float L2) {
-  const float D = w * clipf(f, L1, L2);
+// Scaling of the SGP step: D = w clip(f, L1, L2), Eq. (Dk)/(Dkbound) (w = 1/p, or M_R/alpha with a
+// boundary); with the Tikhonov term beta/2 ||f||^2 the split-gradient scaling D = w c / (1 + beta w c),
+// c = clip(f, L1, L2) (the split grad = V - U with V = sum_j A_j^T 1 + beta f, D = c / V(c)).
+__device__ __forceinline__ float scale_of(float f, float w, float L1, float L2, float beta) {
+  const float c = w * clipf(f, L1, L2);
+  return beta > 0.0f ? c / fmaf(beta, c, 1.0f) : c;
+}
+// y = P(f - alpha D grad): non-negativity (mu = 0) or flux (mu from the search)
+__device__ __forceinline__ float proj_step(float f, float gr, float w, float alpha, float mu, float L1, float L2,
+                                          float beta) {
+  const float D = scale_of(f, w, L1, L2, beta);
   return fmaxf(f - D * fmaf(alpha, gr, mu), 0.0f);
 }
 __device__ __forceinline__ float2* spec_plane(const ImgDesc& d, int plane) {
@@ -430,8 +438,8 @@ __device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ i
 #pragma unroll
         for (int b = 0; b < B; ++b) {
           float2 fn;
-          fn.x = fmaf(lam, proj_step(f[b].x, gr[b].x, w[b].x, alpha, mu, L1, L2) - f[b].x, f[b].x);
-          fn.y = fmaf(lam, proj_step(f[b].y, gr[b].y, w[b].y, alpha, mu, L1, L2) - f[b].y, f[b].y);
+          fn.x = fmaf(lam, proj_step(f[b].x, gr[b].x, w[b].x, alpha, mu, L1, L2, d.reg_beta) - f[b].x, f[b].x);
+          fn.y = fmaf(lam, proj_step(f[b].y, gr[b].y, w[b].y, alpha, mu, L1, L2, d.reg_beta) - f[b].y, f[b].y);
           st2(fcur, off + t + (q0 + b) * G::T, fn);
         }
       }
@@ -521,6 +529,8 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
       const float L1 = float(c->L1), L2 = float(c->L2);
       const bool bb = ke >= 1;
       const bool pend = c->f_pending != 0;
+      const float rb = d.reg_beta;                  // the gradient gains beta f with regularisation
+      const bool need_f = bb || rb > 0.0f;
       const float lam = float(c->lambda), alpha = float(c->alpha), mu = float(c->mu);
       constexpr int B = batch_of<G::E, 4>();
 #pragma unroll 1
@@ -531,15 +541,15 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
           const size_t i = off + t + (q0 + b) * G::T;
           wv[b] = w_pair(d, i);
           const float2 z2 = make_float2(0.0f, 0.0f);
-          fcv[b] = bb && !pend ? ld2(f, i) : z2; fov[b] = bb ? ld2(fp, i) : z2; gov[b] = bb ? ld2(gp, i) : z2;
+          fcv[b] = need_f && !pend ? ld2(f, i) : z2; fov[b] = bb ? ld2(fp, i) : z2; gov[b] = bb ? ld2(gp, i) : z2;
         }
         if (pend) {   // f^(k) = f^(k-1) + lambda (P(f^(k-1) - alpha D grad^(k-1)) - f^(k-1)), as K1 forms it
 #pragma unroll
           for (int b = 0; b < B; ++b) {
             const float2 fo = fov[b], go = gov[b], w = wv[b];
             float2 fn;
-            fn.x = fmaf(lam, proj_step(fo.x, go.x, w.x, alpha, mu, L1, L2) - fo.x, fo.x);
-            fn.y = fmaf(lam, proj_step(fo.y, go.y, w.y, alpha, mu, L1, L2) - fo.y, fo.y);
+            fn.x = fmaf(lam, proj_step(fo.x, go.x, w.x, alpha, mu, L1, L2, rb) - fo.x, fo.x);
+            fn.y = fmaf(lam, proj_step(fo.y, go.y, w.y, alpha, mu, L1, L2, rb) - fo.y, fo.y);
             fcv[b] = fn;
             st2(f, off + t + (q0 + b) * G::T, fn);
           }
@@ -549,13 +559,18 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
         const size_t i = off + t + (q0 + b) * G::T;
         const float2 v = x(t + (q0 + b) * G::T), w = wv[b];   // v = sum_j A_j^T (r_j - 1)
         float2 gr;
-        gr.x = w.x > 0.0f ? -v.x : 0.0f;
-        gr.y = w.y > 0.0f ? -v.y : 0.0f;
+        if (rb > 0.0f) {                            // grad J_0 + beta f on R
+          gr.x = w.x > 0.0f ? fmaf(rb, fcv[b].x, -v.x) : 0.0f;
+          gr.y = w.y > 0.0f ? fmaf(rb, fcv[b].y, -v.y) : 0.0f;
+        } else {
+          gr.x = w.x > 0.0f ? -v.x : 0.0f;
+          gr.y = w.y > 0.0f ? -v.y : 0.0f;
+        }
         st2(gn, i, gr);
         if (bb) {
           const float2 fc = fcv[b], fo = fov[b], go = gov[b];
           const float sx = fc.x - fo.x, sy = fc.y - fo.y, zx = gr.x - go.x, zy = gr.y - go.y;
-          const float Dx = w.x * clipf(fc.x, L1, L2), Dy = w.y * clipf(fc.y, L1, L2);
+          const float Dx = scale_of(fc.x, w.x, L1, L2, rb), Dy = scale_of(fc.y, w.y, L1, L2, rb);
           float tb[4];
           if (Dx > 0.0f) {
             bb_terms(sx, zx, Dx, tb);
@@ -599,7 +614,8 @@ __device__ __forceinline__ void b_sgp_y(const ImgDesc* __restrict__ imgs,
     const int row = item_row(item) + r;
     const bool act = row < d.H;
     const size_t off = size_t(row) * G::M;
-    Acc<FP64> acc[1];
+    Acc<FP64> acc[1], accr[2];                      // g'd; f'd and d'd with regularisation
+    const float rb = d.reg_beta;
     if (act) {
       const float* f = d.f[k & 1];
       const float* gr = d.grad[k & 1];
@@ -615,17 +631,22 @@ __device__ __forceinline__ void b_sgp_y(const ImgDesc* __restrict__ imgs,
         }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-          const float yx = proj_step(fv[b].x, gv[b].x, w[b].x, alpha, mu, L1, L2);
-          const float yy = proj_step(fv[b].y, gv[b].y, w[b].y, alpha, mu, L1, L2);
+          const float yx = proj_step(fv[b].x, gv[b].x, w[b].x, alpha, mu, L1, L2, rb);
+          const float yy = proj_step(fv[b].y, gv[b].y, w[b].y, alpha, mu, L1, L2, rb);
           const float dx = yx - fv[b].x, dy = yy - fv[b].y;
           acc[0].add(gv[b].x * dx);
           acc[0].add(gv[b].y * dy);
+          if (rb > 0.0f) {
+            accr[0].add(fv[b].x * dx); accr[0].add(fv[b].y * dy);
+            accr[1].add(dx * dx); accr[1].add(dy * dy);
+          }
           x(t + (q0 + b) * G::T) = make_float2(dx, dy);   // A d is transformed directly (no A y - A f cancellation)
         }
       }
     }
     row_real_to_spec<W>(x, spec_plane(d, 0) + spec_row_off(row, G::M, spec_interleaved(d.H)), t, act, spec_interleaved(d.H), d.cb);
     block_sum_store<1, FP64>(acc, part_of(d, it) + SLOT_GTD);
+    if (rb > 0.0f) block_sum_store<2, FP64>(accr, part_of(d, it) + SLOT_REG);
   }
 }
 template <int W, bool FP64>
@@ -797,7 +818,8 @@ __device__ __forceinline__ void b_rl_update(const ImgDesc* __restrict__ imgs,
     float2* sp = spec_plane(d, 0) + spec_row_off(row, G::M, spec_interleaved(d.H));
     const bool osem = wview >= 0;
     if (hv) row_spec_to_real<W>(x, osem ? spec_plane(d, wview + 1) + spec_row_off(row, G::M, spec_interleaved(d.H)) : sp, t, act, spec_interleaved(d.H), d.cb);
-    Acc<FP64> acc[1];
+    Acc<FP64> acc[1], accq[1];                      // rho; f'f for the Tikhonov term at set-up
+    const bool fsq = d.reg_beta > 0.0f;
     if (act) {
       const float* fo = d.f[k & 1];
       float* fn = d.f[ke & 1];
@@ -818,11 +840,13 @@ __device__ __forceinline__ void b_rl_update(const ImgDesc* __restrict__ imgs,
           const float2 ft = ld2(d.ftrue, i);
           acc[0].add((f.x - ft.x) * (f.x - ft.x) + (f.y - ft.y) * (f.y - ft.y));
         }
+        if (fsq) { accq[0].add(f.x * f.x); accq[0].add(f.y * f.y); }
         x(t + q * G::T) = f;
       }
     }
     row_real_to_spec<W>(x, sp, t, act, spec_interleaved(d.H), d.cb);
     block_sum_store<1, FP64>(acc, part_of(d, it) + SLOT_RHO);
+    if (fsq) block_sum_store<1, FP64>(accq, part_of(d, it) + SLOT_FSQ);
   }
 }
 template <int W, bool FP64>

@@ -673,6 +673,7 @@ sgp_status reset_ctrl(sgp_ctx* c) {
     z.trace_cap = P.trace_cap;
     z.stop_kind = STOP_FIXED; z.max_iter = 0;
     z.M_alpha = P.M_alpha; z.warmup = P.warmup_iters; z.max_backtracks = P.max_backtracks;
+    z.reg_beta = double(float(P.reg_beta));   // the value the passes use
     z.fp64 = c->fp64; z.constraint = P.constraint;
     z.flux_c = P.flux_c > 0.0 ? P.flux_c : c->c_const[i] * c->nS[i];
     z.alpha = P.alpha0; z.alpha_prev = P.alpha0; z.tau = P.tau1; z.lambda = 1.0;
@@ -955,6 +956,7 @@ void sgp_params_default(sgp_params* o) {
   o->adaptive_L = 1; o->max_backtracks = 30; o->L1 = 1e-10; o->L2 = 1e10; o->sigma_R = 1e-2;
   o->constraint = 0; o->flux_c = 0.0; o->reduce_fp64 = 1; o->trace_cap = 4096;
   o->band_tol = 1e-6;
+  o->reg_beta = 0.0;
 }
 
 const char* sgp_last_error(void) { return g_err.c_str(); }
@@ -1005,6 +1007,7 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
   if (params) P = *params; else sgp_params_default(&P);
   if (P.M_alpha < 1 || P.M_alpha > kMaxHist) return fail(SGP_ERR_ARG, "M_alpha must be 1..16");
   if (P.max_backtracks < 0 || P.max_backtracks > 30) return fail(SGP_ERR_ARG, "max_backtracks must be 0..30");
+  if (!(P.reg_beta >= 0.0) || !(P.reg_beta < 1e30)) return fail(SGP_ERR_ARG, "reg_beta must be finite and >= 0");
   if (!(P.theta > 0 && P.theta < 1) || !(P.beta > 0 && P.beta < 1)) return fail(SGP_ERR_ARG, "beta, theta must lie in (0,1)");
   if (!(P.alpha_min > 0 && P.alpha_min < P.alpha_max)) return fail(SGP_ERR_ARG, "need 0 < alpha_min < alpha_max");
   if (!P.adaptive_L && !(P.L1 > 0 && P.L1 < P.L2)) return fail(SGP_ERR_ARG, "need 0 < L1 < L2");
@@ -1060,6 +1063,7 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
     c->col_count[i] = int(c->col.size()) - c->col_begin[i];
     d.w_scalar = 1.0f / float(d.p);
     d.a1_scalar = float(d.p);
+    d.reg_beta = float(P.reg_beta);
     for (int j = 0; j < kMaxViews; ++j) d.bs[j] = j < d.p ? in[i].b_const[j] : 0.0f;
     d.ftrue = nullptr;
   }
@@ -1328,6 +1332,7 @@ sgp_status sgp_set_truth(sgp_ctx* c, int image, const float* f_true) {
 
 sgp_status rl_iterate(sgp_ctx* c, int n) {
   if (!c) return fail(SGP_ERR_ARG, "ctx is NULL");
+  if (c->prm.reg_beta > 0.0) return fail(SGP_ERR_ARG, "reg_beta applies to SGP only");
   sgp_status st = enter(c);
   if (st || (st = run_fixed(c, false, n))) return st;
   return leave(c);
@@ -1335,6 +1340,7 @@ sgp_status rl_iterate(sgp_ctx* c, int n) {
 
 sgp_status osem_iterate(sgp_ctx* c, int n) {
   if (!c) return fail(SGP_ERR_ARG, "ctx is NULL");
+  if (c->prm.reg_beta > 0.0) return fail(SGP_ERR_ARG, "reg_beta applies to SGP only");
   sgp_status st = enter(c);
   if (st || (st = run_osem(c, n))) return st;
   return leave(c);
@@ -1358,6 +1364,7 @@ sgp_status sgp_solve_until(sgp_ctx* c, const sgp_stop_rule* rule, int* iters) {
 
 sgp_status rl_solve_until(sgp_ctx* c, const sgp_stop_rule* rule, int* iters) {
   if (!c) return fail(SGP_ERR_ARG, "ctx is NULL");
+  if (c->prm.reg_beta > 0.0) return fail(SGP_ERR_ARG, "reg_beta applies to SGP only");
   sgp_status st = enter(c);
   if (st) return st;
   const sgp_status res = run_until(c, false, rule, iters);
@@ -1385,6 +1392,7 @@ sgp_status sgp_get_info(sgp_ctx* c, int image, sgp_info* o) {
   o->nS = c->nS[image];
   o->flux_c = c->c_const[image];
   o->band_cols = c->L.d[image].cb;
+  o->reg = h.R;
   return leave(c);
 }
 

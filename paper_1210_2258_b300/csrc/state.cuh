@@ -34,6 +34,8 @@ enum Slot {
   SLOT_MIN = 42,      // min over positive pixels (set-up)
   SLOT_MAX = 43,      // max (set-up)
   SLOT_PROJ = 44,     // flux projection search sums (5)
+  SLOT_REG = 50,      // regularised SGP: 2 slots, f'd and d'd (Armijo change of the Tikhonov term)
+  SLOT_FSQ = 52,      // regularised SGP set-up: f'f of the starting point
 };
 // The main Armijo pass evaluates arm_count() step lengths 1, theta, ..: one after an iteration that
 // accepted lambda = 1, two after one backtrack, kArmMain after more.
@@ -81,6 +83,9 @@ struct CtrlState {
   double beta, theta, alpha0, tau1, alpha_min, alpha_max;
   double tol, eta, inv_pS, ftrue_norm2, flux_c;
   double mu_lo, mu_hi, phi_lo, phi_hi;
+  double reg_beta;  // weight of the Tikhonov term beta/2 ||f||^2 (0: the unregularised method)
+  double R, R_pred; // beta/2 ||f||^2 at the current iterate and at the accepted trial point
+  double reg_fd, reg_dd;   // f'd and d'd of the current direction
   double scratch[8];
 };
 // The pending SGP update f^(k+1) = f^(k) + lambda d (Alg. 1, step 6) is applied by K1 when the stop
@@ -106,6 +111,7 @@ struct ImgDesc {
                                 // and load only columns < cb, the others are zero (band-limited PSF)
   float w_scalar;               // periodic: 1/p (RL factor, SGP scaling factor)
   float a1_scalar;              // periodic: p (= sum_j A_j^T 1)
+  float reg_beta;               // regularised SGP: weight of beta/2 ||f||^2 (0: none)
   float bs[kMaxViews];          // constant backgrounds (used when b == nullptr)
   size_t P;
   float* f[2];                  // iterate ping-pong

@@ -37,7 +37,7 @@ class Params(C.Structure):
                 ("warmup_iters", C.c_int), ("adaptive_L", C.c_int), ("max_backtracks", C.c_int),
                 ("L1", C.c_double), ("L2", C.c_double), ("sigma_R", C.c_double), ("constraint", C.c_int),
                 ("flux_c", C.c_double), ("reduce_fp64", C.c_int), ("trace_cap", C.c_int),
-                ("band_tol", C.c_double)]
+                ("band_tol", C.c_double), ("reg_beta", C.c_double)]
 
 
 class StopRule(C.Structure):
@@ -52,7 +52,7 @@ class Info(C.Structure):
     _fields_ = [("k", C.c_int), ("status", C.c_int), ("stopped", C.c_int), ("trace_n", C.c_int),
                 ("J", C.c_double), ("D", C.c_double), ("L1", C.c_double), ("L2", C.c_double),
                 ("alpha", C.c_double), ("tau", C.c_double), ("lambda_", C.c_double), ("rho", C.c_double),
-                ("nS", C.c_double), ("flux_c", C.c_double), ("band_cols", C.c_int)]
+                ("nS", C.c_double), ("flux_c", C.c_double), ("band_cols", C.c_int), ("reg", C.c_double)]
 
 
 class Mosaic(C.Structure):
