@@ -255,7 +255,10 @@ struct sgp_ctx {
 namespace {
 
 // ---- launch helpers -----------------------------------------------------------------------------
-long long* g_launch_counter = nullptr;   // set while a context is being driven
+// launch counter of the context this host thread is driving: set by enter(), cleared by leave()
+// and by sgp_destroy() of that context, so it never outlives the context; the entry points that
+// drive no context launch with it cleared
+thread_local long long* g_launch_counter = nullptr;
 
 sgp_status launch(const void* fn, int grid, int block, size_t smem, cudaStream_t s, void** args) {
   if (grid <= 0) return SGP_OK;
@@ -414,6 +417,7 @@ sgp_status enter(sgp_ctx* c) {
   return SGP_OK;
 }
 sgp_status leave(sgp_ctx* c) {
+  g_launch_counter = nullptr;
   CU(cudaEventRecord(c->ev_out, c->s));
   CU(cudaStreamWaitEvent(c->user, c->ev_out, 0));
   return SGP_OK;
@@ -476,6 +480,7 @@ sgp_status osem_col(sgp_ctx* c, int variant, int job_off, int j) {
 // PSF band of every problem (after the PSF spectra): cb = 1 + the last spectrum column whose
 // entries exceed tol max|K_hat| in some view, rounded up to the column tile; then the column lists
 // of the iteration's passes (image < 0) over the band, and the descriptors with cb.
+sgp_status apply_band(sgp_ctx* c, const std::vector<int>& raw);
 sgp_status set_band(sgp_ctx* c, double tol) {
   Layout& L = c->L;
   std::vector<float> cm;
@@ -504,10 +509,63 @@ sgp_status set_band(sgp_ctx* c, double tol) {
     }
     raw[i] = cb;
   }
-  // a uniform context of the side with a narrow column variant uses it when every problem's band
-  // keeps half the columns or fewer (more, narrower column tiles)
-  c->col_narrow = !c->mixed && c->H == kNarrowSide;
-  for (int i = 0; i < c->n; ++i) c->col_narrow = c->col_narrow && raw[i] * 2 <= L.d[i].W / 2;
+  // a uniform context of the side with two column plans (16 or 8 values per thread) times both on
+  // its own band and keeps the faster (the choice is remembered per size and band for the process)
+  if (c->mixed || c->H != kNarrowSide) {
+    c->col_narrow = false;
+    return apply_band(c, raw);
+  }
+  static std::map<std::tuple<int, int, int, int>, bool> cache;
+  static std::mutex mu;
+  const auto key = std::make_tuple(c->H, c->W, c->p, *std::max_element(raw.begin(), raw.end()));
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    const auto it = cache.find(key);
+    if (it != cache.end()) {
+      c->col_narrow = it->second;
+      return apply_band(c, raw);
+    }
+  }
+  // the iteration's two column passes on zeroed planes (the controllers read "running")
+  CU(cudaMemsetAsync(L.ctrl, 0, sizeof(CtrlState) * c->n, c->s));
+  for (int i = 0; i < c->n; ++i)
+    CU(cudaMemsetAsync(L.d[i].spec, 0, sizeof(float) * L.d[i].P * (L.d[i].p + 1), c->s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  sgp_status st = SGP_OK;
+  float ms[2] = {1e30f, 1e30f};
+  for (int narrow = 0; narrow < 2 && st == SGP_OK; ++narrow) {
+    c->col_narrow = narrow != 0;
+    if ((st = apply_band(c, raw))) break;
+    for (int round = 0; round < 4 && st == SGP_OK; ++round) {   // round 0 warms up
+      cudaEventRecord(e0, c->s);
+      for (int r = 0; r < 3 && st == SGP_OK; ++r) {
+        st = col_pass(c, COL_1TOP, JOB_A * c->n);
+        if (st == SGP_OK) st = adjoint_cols(c, JOB_AT * c->n);
+      }
+      cudaEventRecord(e1, c->s);
+      float t = 0.0f;
+      if (st == SGP_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+        st = fail(SGP_ERR_CUDA, "column-plan timing failed");
+      if (round > 0) ms[narrow] = std::min(ms[narrow], t);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  c->col_narrow = ms[1] < ms[0];
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    cache.emplace(key, c->col_narrow);
+  }
+  return apply_band(c, raw);
+}
+
+// The PSF band rounded to whole column tiles of the chosen plan, the column item lists over it
+// and the descriptors with cb.
+sgp_status apply_band(sgp_ctx* c, const std::vector<int>& raw) {
+  Layout& L = c->L;
   const int cpi_n = g_reg.col_narrow_cols;
   auto tile_of = [&](const ImgDesc& d) { return c->col_narrow ? cpi_n : cols_per_item(d.H); };
   for (int i = 0; i < c->n; ++i) {   // the band rounded up to whole column tiles
@@ -1661,6 +1719,7 @@ sgp_status sgp_sum_terms(int kind, int reduce_fp64, const float* a, const float*
   if (blocks > size_t(1) << 30) return fail(SGP_ERR_SIZE_UNSUPPORTED, "too many terms");
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || ws_bytes < sgp_sum_terms_workspace_bytes(n))
     return fail(SGP_ERR_WORKSPACE, "workspace missing, misaligned or smaller than sgp_sum_terms_workspace_bytes(n)");
+  g_launch_counter = nullptr;   // no context is driven by this call
   int dev = 0;
   CU(cudaGetDevice(&dev));
   sgp_status st = ensure_device_ready(dev);
@@ -1685,6 +1744,7 @@ sgp_status sgp_sum_terms(int kind, int reduce_fp64, const float* a, const float*
 
 sgp_status sgp_destroy(sgp_ctx* c) {
   if (!c) return SGP_OK;
+  if (g_launch_counter == &c->launches) g_launch_counter = nullptr;
   if (c->s) cudaStreamSynchronize(c->s);
   if (c->g_sgp) cudaGraphExecDestroy(c->g_sgp);
   if (c->g_rl) cudaGraphExecDestroy(c->g_rl);
@@ -1735,6 +1795,7 @@ extern "C" sgp_status sgp_convolve_noalloc(const float* psf, const float* f, flo
   CU(cudaStreamIsCapturing(s, &cap));
   if (cap != cudaStreamCaptureStatusNone)
     return fail(SGP_ERR_STATE, "sgp_convolve_noalloc must not be called while its stream is being captured");
+  g_launch_counter = nullptr;   // no context is driven by this call
   int dev = 0;
   CU(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNoAllocDevices) return fail(SGP_ERR_ARG, "device ordinal beyond the library's table (64)");
