@@ -372,9 +372,12 @@ __device__ __forceinline__ float2 b_pair(const ImgDesc& d, int j, size_t i) {
 // Scaling of the SGP step: D = w clip(f, L1, L2), Eq. (Dk)/(Dkbound) (w = 1/p, or M_R/alpha with a
 // boundary); with the Tikhonov term beta/2 ||f||^2 the split-gradient scaling D = w c / (1 + beta w c),
 // c = clip(f, L1, L2) (the split grad = V - U with V = sum_j A_j^T 1 + beta f, D = c / V(c)).
+// (the regularised form divides with the fast reciprocal, error <= 2 ulp: D only has to be one
+// consistent positive scaling, and a correctly rounded division on this path would be evaluated
+// for every pixel of the unregularised passes too)
 __device__ __forceinline__ float scale_of(float f, float w, float L1, float L2, float beta) {
   const float c = w * clipf(f, L1, L2);
-  return beta > 0.0f ? c / fmaf(beta, c, 1.0f) : c;
+  return beta > 0.0f ? __fdividef(c, fmaf(beta, c, 1.0f)) : c;
 }
 // y = P(f - alpha D grad): non-negativity (mu = 0) or flux (mu from the search)
 __device__ __forceinline__ float proj_step(float f, float gr, float w, float alpha, float mu, float L1, float L2,
