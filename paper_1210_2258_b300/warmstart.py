@@ -327,7 +327,7 @@ def evaluate(net: WarmStartNet, scs, max_iter: int = 2000, batch: int = 50, n_si
     import torch
     out = {"flat_iters": [], "warm_iters": [], "flat_kl": [], "warm_kl": [], "flat_ms": 0.0, "warm_ms": 0.0,
            "net_ms": 0.0, "fallbacks": 0, "single_flat_ms": [], "single_warm_ms": [], "single_net_ms": [],
-           "single_flat32_ms": [], "single_kl_rel_warm_flat32": []}
+           "single_flat32_ms": [], "single_kl_rel_warm_flat32": [], "single_failed": {}, "net_errors": 0}
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     for a in range(0, len(scs), batch):
         part = scs[a:a + batch]
@@ -346,6 +346,7 @@ def evaluate(net: WarmStartNet, scs, max_iter: int = 2000, batch: int = 50, n_si
                 ev[2].record()
                 for i in range(len(part)):
                     probs.set_start(i, lib.START_USER, f0[i])
+                out["net_errors"] += device_error()
             it = probs.solve_until(lib.STOP_LANDED, max_iter=max_iter, eta=1.0, tol=LAND_TOL, raise_on_error=False)
             ev[1].record()
             torch.cuda.synchronize()
@@ -395,13 +396,28 @@ def evaluate(net: WarmStartNet, scs, max_iter: int = 2000, batch: int = 50, n_si
             torch.cuda.synchronize()
             inf = pr.info(0)
             times[mode] = ev[0].elapsed_time(ev[1]) if inf.status == 0 and inf.stopped else None
-            kls[mode] = pr.get_f(0).clone()
+            if inf.status != 0:   # record the failure (status code per arm); the image is left out
+                key = f"{mode}:{lib.STATUS_NAMES[inf.status]}"
+                out["single_failed"][key] = out["single_failed"].get(key, 0) + 1
+            kls[mode] = pr.get_f(0).clone() if inf.status == 0 else None
             if mode == "warm":
                 times["net"] = ev[0].elapsed_time(ev[2])
+                out["net_errors"] += device_error()
         # final KL of the warm (mixed) and plain-FP32 results, both evaluated with FP64 accumulation
         for mode in ("warm", "flat32"):
-            prob.set_start(0, lib.START_USER, kls[mode])
-            kls[mode] = prob.kl_value(0)
+            if kls[mode] is None:
+                continue
+            try:
+                prob.set_start(0, lib.START_USER, kls[mode])
+                kls[mode] = prob.kl_value(0)
+            except lib.SGPError as e:
+                key = f"{mode}:kl_eval:{lib.STATUS_NAMES[e.status]}"
+                out["single_failed"][key] = out["single_failed"].get(key, 0) + 1
+                kls[mode] = None
+        if kls["warm"] is None or kls["flat32"] is None:
+            prob.close()
+            prob32.close()
+            continue
         if times["flat"] is not None and times["warm"] is not None:
             out["single_flat_ms"].append(times["flat"])
             out["single_warm_ms"].append(times["warm"])
@@ -511,7 +527,8 @@ def main(argv=None) -> int:
         "final_kl_rel_diff_median": float(np.median(kl_rel[done])), "final_kl_rel_diff_max": float(np.max(kl_rel[done])),
         "flat_not_stopped": int((res["flat_iters"] >= 2000).sum()),
         "warm_not_stopped": int((res["warm_iters"] >= 2000).sum()),
-        "eval_s": t4 - t3, "fallbacks_to_flat": res["fallbacks"], **single,
+        "eval_s": t4 - t3, "fallbacks_to_flat": res["fallbacks"], "single_failed": res["single_failed"],
+        "net_device_errors": res["net_errors"], **single,
     }
     log(json.dumps(summary))
     if a.save:
