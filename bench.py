@@ -741,7 +741,13 @@ def run_other_workload(args):
                      "sgp": res["sgp"], "rl": res["rl"],
                      "config": {"N": N, "tiles": [2, 2], "sub": 160, "ext": 256, "psf": "Gaussian sigma 2", "b": b}})
     else:
-        scs = scenes.boundary_batch(seed=args.seed, count=64)
+        # the batch shards by problem over the ranks (largest first to the least-loaded rank); the
+        # timing summary is the only communication (replicas.aggregate)
+        from paper_1210_2258_b300 import replicas
+        ws_n, rank, _ = dist_setup(args)
+        all_scs = scenes.boundary_batch(seed=args.seed, count=64)
+        mine = replicas.shard([int(np.prod(s.g.shape[-2:])) for s in all_scs], rank, ws_n)
+        scs = [all_scs[i] for i in mine]
         pr = lib.Problems([dev(s.psfs) for s in scs], [list(map(float, s.b)) for s in scs],
                           [dev(s.mask) for s in scs])
         for i, s in enumerate(scs):
@@ -753,14 +759,25 @@ def run_other_workload(args):
             return pr.solve_until(lib.STOP_CONVERGENCE, max_iter=3000, tol=1e-5, raise_on_error=False)
         for _ in range(args.warmup):
             solve()
+        if ws_n > 1:
+            torch.distributed.barrier()
         ms, its = _timed(torch, solve, args.steps)
-        px = sum(int(np.prod(s.g.shape[-2:])) for s in scs)
-        pix_it = sum(int(np.prod(s.g.shape[-2:])) * k for s, k in zip(scs, its))
+        px_local = sum(int(np.prod(s.g.shape[-2:])) for s in scs)
+        pix_it_local = sum(int(np.prod(s.g.shape[-2:])) * k for s, k in zip(scs, its))
+        stopped_local = sum(int(pr.info(i).stopped) for i in range(len(scs)))
+        ms, pix_it = replicas.aggregate(ms, pix_it_local, device="cuda")
+        _, px = replicas.aggregate(0.0, px_local, device="cuda")
+        _, stopped = replicas.aggregate(0.0, stopped_local, device="cuda")
+        if rank != 0:
+            return 0
+        line["n_gpus"] = ws_n
+        line["scaling"] = "strong"
         line.update({"metric": "batch of 64 boundary problems (sides 128..1024 padded), convergence stop (tol 1e-5)",
                      "unit": "Mpixel-iterations/s", "value": pix_it / (ms / 1e3) / 1e6,
                      "time_to_all_stopped_ms": ms, "iterations_min_max_mean": [int(min(its)), int(max(its)),
                                                                               float(np.mean(its))],
-                     "padded_pixels": px, "not_stopped": int(sum(1 - pr.info(i).stopped for i in range(len(scs)))),
+                     "padded_pixels": px, "not_stopped": len(all_scs) - stopped,
+                     "problems_per_rank": len(scs),
                      "config": {"count": 64, "sides": [128, 256, 384, 512, 768, 1024], "psf": "Gaussian sigma U[1,4]",
                                 "b": "U[5,50]", "mask": "0/1 M_S, extended domain"}})
     print(json.dumps(line))

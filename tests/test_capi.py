@@ -44,3 +44,40 @@ def test_create_rejects_bad_arguments_without_gpu_work():
                         None, C.c_void_p(256), 1 << 30, None)
     assert st == S.ERR_ARG
     assert lib.rl_iterate(None, 1) == S.ERR_ARG
+
+
+def test_regularisation_weight_is_validated_before_gpu_work():
+    lib = S.load()
+    ctx = C.c_void_p()
+    sh = S.Shape(256, 256, 1, 0, 0)
+    for bad in (-1e-3, float("nan"), float("inf")):
+        p = S.default_params(reg_beta=bad)
+        st = lib.sgp_create(C.byref(ctx), C.byref(sh), C.c_void_p(256), None, (C.c_float * 1)(1.0), None,
+                            C.byref(p), C.c_void_p(256), 1 << 30, None)
+        assert st == S.ERR_ARG and b"reg_beta" in lib.sgp_last_error(), bad
+    assert S.default_params().reg_beta == 0.0
+
+
+def test_sum_terms_rejects_bad_arguments_without_gpu_work():
+    """sgp_sum_terms checks its arguments and workspace before any CUDA call (pointers here are
+    never dereferenced)."""
+    lib = S.load()
+    n = 1 << 20
+    need = lib.sgp_sum_terms_workspace_bytes(n)
+    assert need >= 2048 and lib.sgp_sum_terms_workspace_bytes(4 * n) > need
+    assert lib.sgp_sum_terms_workspace_bytes(1) >= 2048
+    a, b, c, w = C.c_void_p(256), C.c_void_p(512), C.c_void_p(768), C.c_void_p(1 << 20)
+    out = C.c_double()
+    call = lambda kind, a, b, c, n, outp, ws, wsb: lib.sgp_sum_terms(kind, 1, a, b, c, n, 1.0, None, outp, ws,
+                                                                     wsb, None)
+    assert call(S.SUM_VALUES, a, None, None, n, None, w, need) == S.ERR_ARG
+    assert call(S.SUM_VALUES, None, None, None, n, C.byref(out), w, need) == S.ERR_ARG
+    assert call(S.SUM_VALUES, a, None, None, 0, C.byref(out), w, need) == S.ERR_ARG
+    assert call(99, a, b, c, n, C.byref(out), w, need) == S.ERR_ARG
+    assert call(-1, a, b, c, n, C.byref(out), w, need) == S.ERR_ARG
+    assert call(S.SUM_KL, a, None, None, n, C.byref(out), w, need) == S.ERR_ARG
+    assert call(S.SUM_ARMIJO, a, b, None, n, C.byref(out), w, need) == S.ERR_ARG
+    assert call(S.SUM_BB0 + 3, a, b, None, n, C.byref(out), w, need) == S.ERR_ARG
+    assert call(S.SUM_VALUES, a, None, None, n, C.byref(out), None, need) == S.ERR_WORKSPACE
+    assert call(S.SUM_VALUES, a, None, None, n, C.byref(out), w, need - 1) == S.ERR_WORKSPACE
+    assert call(S.SUM_VALUES, a, None, None, n, C.byref(out), C.c_void_p((1 << 20) + 64), need) == S.ERR_WORKSPACE
