@@ -245,8 +245,7 @@ __device__ void ctrl_sgp_lambda(const ImgDesc& d) {
   __shared__ CtrlState s;
   const CtrlCopy cp(d.ctrl);
   double g[1], arm[kArmMain], rg[2] = {0.0, 0.0};
-  ctrl_sum<1, FP64>(d, SLOT_GTD, g, false);
-  ctrl_sum<kArmMain, FP64>(d, SLOT_ARM, arm, true);
+  ctrl_sums<1, kArmMain, FP64>(d, SLOT_GTD, false, g, SLOT_ARM, true, arm);
   if (d.reg_beta > 0.0f) ctrl_sum<2, FP64>(d, SLOT_REG, rg, false);   // f'd, d'd of this direction
   cp.to_shared(s);
   if (threadIdx.x == 0) {
@@ -322,8 +321,7 @@ __device__ void ctrl_rl(const ImgDesc& d) {
   __shared__ CtrlState s;
   const CtrlCopy cp(d.ctrl);
   double kl[1], rr[1];
-  ctrl_sum<1, FP64>(d, SLOT_KL, kl, true);
-  ctrl_sum<1, FP64>(d, SLOT_RHO, rr, false);
+  ctrl_sums<1, 1, FP64>(d, SLOT_KL, true, kl, SLOT_RHO, false, rr);
   cp.to_shared(s);
   if (threadIdx.x == 0) rl_decide<FP64>(d, &s, kl[0], rr[0]);
   CtrlCopy::write_back(s, d.ctrl);

@@ -4,7 +4,7 @@
 // Eq. projection / backprojection) are evaluated as
 //      row R2C  ->  column FFT . (PSF spectrum) . column IFFT  ->  row C2R
 // with every pass reading and writing HBM once.  This header provides the pieces:
-//   * in-register DFTs of radix 2, 3, 4, 6, 8, 12, 16, 24;
+//   * in-register DFTs of radix 2, 3, 4, 6, 8, 12, 16, 24, 32;
 //   * one autosorting Stockham stage over data held in shared memory (radix R, sub-transform
 //     length NS):  read x[j + m L/R], twiddle by w_{NS R}^{m (j mod NS)}, DFT_R, write to
 //     (j - j mod NS) R + j mod NS + m NS.  The output is in natural order after the last stage,
@@ -54,16 +54,47 @@ __constant__ float2 c_w48[48] = {
     {9.23879532511e-1f, -3.82683432365e-1f}, {9.65925826289e-1f, -2.58819045103e-1f}, {9.91444861374e-1f, -1.3052619222e-1f},
 };
 
+// cos / sin (2 pi t / 64), t = 0..63: the radix-32 DFT and the 32 x 32 four-step transform.
+__constant__ float2 c_w64[64] = {
+    {1.0f, 0.0f}, {9.951847266722e-01f, 9.801714032956e-02f}, {9.807852804032e-01f, 1.950903220161e-01f}, {9.569403357322e-01f, 2.902846772545e-01f},
+    {9.238795325113e-01f, 3.826834323651e-01f}, {8.819212643484e-01f, 4.713967368260e-01f}, {8.314696123025e-01f, 5.555702330196e-01f}, {7.730104533627e-01f, 6.343932841636e-01f},
+    {7.071067811865e-01f, 7.071067811865e-01f}, {6.343932841636e-01f, 7.730104533627e-01f}, {5.555702330196e-01f, 8.314696123025e-01f}, {4.713967368260e-01f, 8.819212643484e-01f},
+    {3.826834323651e-01f, 9.238795325113e-01f}, {2.902846772545e-01f, 9.569403357322e-01f}, {1.950903220161e-01f, 9.807852804032e-01f}, {9.801714032956e-02f, 9.951847266722e-01f},
+    {0.0f, 1.0f}, {-9.801714032956e-02f, 9.951847266722e-01f}, {-1.950903220161e-01f, 9.807852804032e-01f}, {-2.902846772545e-01f, 9.569403357322e-01f},
+    {-3.826834323651e-01f, 9.238795325113e-01f}, {-4.713967368260e-01f, 8.819212643484e-01f}, {-5.555702330196e-01f, 8.314696123025e-01f}, {-6.343932841636e-01f, 7.730104533627e-01f},
+    {-7.071067811865e-01f, 7.071067811865e-01f}, {-7.730104533627e-01f, 6.343932841636e-01f}, {-8.314696123025e-01f, 5.555702330196e-01f}, {-8.819212643484e-01f, 4.713967368260e-01f},
+    {-9.238795325113e-01f, 3.826834323651e-01f}, {-9.569403357322e-01f, 2.902846772545e-01f}, {-9.807852804032e-01f, 1.950903220161e-01f}, {-9.951847266722e-01f, 9.801714032956e-02f},
+    {-1.0f, 0.0f}, {-9.951847266722e-01f, -9.801714032956e-02f}, {-9.807852804032e-01f, -1.950903220161e-01f}, {-9.569403357322e-01f, -2.902846772545e-01f},
+    {-9.238795325113e-01f, -3.826834323651e-01f}, {-8.819212643484e-01f, -4.713967368260e-01f}, {-8.314696123025e-01f, -5.555702330196e-01f}, {-7.730104533627e-01f, -6.343932841636e-01f},
+    {-7.071067811865e-01f, -7.071067811865e-01f}, {-6.343932841636e-01f, -7.730104533627e-01f}, {-5.555702330196e-01f, -8.314696123025e-01f}, {-4.713967368260e-01f, -8.819212643484e-01f},
+    {-3.826834323651e-01f, -9.238795325113e-01f}, {-2.902846772545e-01f, -9.569403357322e-01f}, {-1.950903220161e-01f, -9.807852804032e-01f}, {-9.801714032956e-02f, -9.951847266722e-01f},
+    {0.0f, -1.0f}, {9.801714032956e-02f, -9.951847266722e-01f}, {1.950903220161e-01f, -9.807852804032e-01f}, {2.902846772545e-01f, -9.569403357322e-01f},
+    {3.826834323651e-01f, -9.238795325113e-01f}, {4.713967368260e-01f, -8.819212643484e-01f}, {5.555702330196e-01f, -8.314696123025e-01f}, {6.343932841636e-01f, -7.730104533627e-01f},
+    {7.071067811865e-01f, -7.071067811865e-01f}, {7.730104533627e-01f, -6.343932841636e-01f}, {8.314696123025e-01f, -5.555702330196e-01f}, {8.819212643484e-01f, -4.713967368260e-01f},
+    {9.238795325113e-01f, -3.826834323651e-01f}, {9.569403357322e-01f, -2.902846772545e-01f}, {9.807852804032e-01f, -1.950903220161e-01f}, {9.951847266722e-01f, -9.801714032956e-02f},
+};
+
 // v * w_R^e, w_R = exp(-/+ 2 pi i / R) (forward / inverse); e is a compile-time constant after unrolling
 template <int R, bool INV>
 __device__ __forceinline__ float2 twr(float2 v, int e) {
-  const int t = ((e % R) * (48 / R)) % 48;
-  if (t == 0) return v;
-  if (t == 24) return make_float2(-v.x, -v.y);
-  if (t == 12) return mul_mi<INV>(v);
-  if (t == 36) return mul_mi<!INV>(v);
-  const float2 w = c_w48[t];
-  return INV ? cmul(v, w) : cmulc(v, w);
+  if constexpr (48 % R == 0) {
+    const int t = ((e % R) * (48 / R)) % 48;
+    if (t == 0) return v;
+    if (t == 24) return make_float2(-v.x, -v.y);
+    if (t == 12) return mul_mi<INV>(v);
+    if (t == 36) return mul_mi<!INV>(v);
+    const float2 w = c_w48[t];
+    return INV ? cmul(v, w) : cmulc(v, w);
+  } else {
+    static_assert(64 % R == 0, "in-register radix must divide 48 or 64");
+    const int t = ((e % R) * (64 / R)) % 64;
+    if (t == 0) return v;
+    if (t == 32) return make_float2(-v.x, -v.y);
+    if (t == 16) return mul_mi<INV>(v);
+    if (t == 48) return mul_mi<!INV>(v);
+    const float2 w = c_w64[t];
+    return INV ? cmul(v, w) : cmulc(v, w);
+  }
 }
 
 // supported transform lengths and the offsets of their tables exp(-2 pi i q / L), q < L
@@ -155,6 +186,7 @@ template <bool INV> struct DFT<8, INV> : DFTComp<2, 4, INV> {};
 template <bool INV> struct DFT<12, INV> : DFTComp<4, 3, INV> {};
 template <bool INV> struct DFT<16, INV> : DFTComp<4, 4, INV> {};
 template <bool INV> struct DFT<24, INV> : DFTComp<8, 3, INV> {};
+template <bool INV> struct DFT<32, INV> : DFTComp<4, 8, INV> {};
 
 // ------------------------------------------------------------------------------ plans
 template <int... Rs> struct RL {};
@@ -297,6 +329,29 @@ template <int L, bool INV, class Lay, class P = Plan<L>>
 __device__ __forceinline__ void fft_inplace(const Lay& x, int t, bool act) {
   if (INV) run_stages<L, P::T, true, 1>(x, t, act, typename P::Inv{});
   else     run_stages<L, P::T, false, 1>(x, t, act, typename P::Fwd{});
+}
+
+// ------------------------------------------------------------------------------ warp four-step
+// A length-1024 transform held by one warp, 32 values per lane: index n = n1 + 32 n2 on input
+// (lane n1 holds n2 = 0..31), k = k1 + 32 k2 on output (lane k1 holds k2 = 0..31), as
+//   X[k1 + 32 k2] = sum_n1 w_1024^(n1 k1) w_32^(n1 k2) sum_n2 x[n1 + 32 n2] w_32^(n2 k1)
+// (w = exp(-/+ 2 pi i / L)): a radix-32 DFT in registers, the twiddles w_1024^(n1 k1), one 32 x 32
+// transpose through the warp's shared buffer T (32 rows of 33 values, so that both the row
+// writes and the column reads are free of bank conflicts), and a second radix-32 DFT.  No block
+// barrier: the warp's rows are independent of the other warps.  T must hold 1056 float2; the
+// caller orders T's previous use before the call (the function starts with __syncwarp).
+template <bool INV>
+__device__ __forceinline__ void warp_fft1024(float2 (&v)[32], float2* T, int lane) {
+  DFT<32, INV>::run(v);
+#pragma unroll
+  for (int q = 1; q < 32; ++q) v[q] = cmul(v[q], twl<1024, INV>(lane * q));
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 32; ++q) T[q * 33 + lane] = v[q];
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = T[lane * 33 + q];
+  DFT<32, INV>::run(v);
 }
 
 }  // namespace sgp

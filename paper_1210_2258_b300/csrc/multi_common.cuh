@@ -27,7 +27,7 @@ constexpr size_t max_col_smem() {
 
 #define SGP_MULTI_ROW(NAME, BODY)                                                                          \
   template <bool FP64>                                                                                    \
-  __global__ void __launch_bounds__(kRowBlock) NAME(const ImgDesc* __restrict__ imgs, const int2* __restrict__ items, \
+  __global__ void __launch_bounds__(kRowBlock, 2) NAME(const ImgDesc* __restrict__ imgs, const int2* __restrict__ items, \
                                                     int n_items, int extra) {                              \
     const int it = blockIdx.x;                                                                            \
     if (it >= n_items) return;                                                                            \
@@ -38,7 +38,7 @@ constexpr size_t max_col_smem() {
 
 // the same with the reduction precision fixed (a plain kernel, for units that build one variant)
 #define SGP_MULTI_ROW_FIXED(NAME, BODY, FP64V)                                                            \
-  __global__ void __launch_bounds__(kRowBlock) NAME(const ImgDesc* __restrict__ imgs, const int2* __restrict__ items, \
+  __global__ void __launch_bounds__(kRowBlock, 2) NAME(const ImgDesc* __restrict__ imgs, const int2* __restrict__ items, \
                                                     int n_items, int extra) {                              \
     constexpr bool FP64 = FP64V;                                                                          \
     const int it = blockIdx.x;                                                                            \

@@ -103,43 +103,72 @@ __device__ __forceinline__ void block_sum_store(const Acc<FP64> (&loc)[NS], doub
   __syncthreads();
 }
 
-// Sum NS slots over this problem's items (row list or row-view list) in a fixed order; the
-// result is on every thread of the block.
-template <int NS, bool FP64>
-__device__ void ctrl_sum(const ImgDesc& d, int slot, double (&res)[NS], bool view_list) {
-  __shared__ FF red[NS][kCtrlBlock / 32];
+// Sum NA slots (from slotA) over list A and NB slots (from slotB) over list B of this problem's
+// items (row list or row-view list) in one pass, in a fixed order: per thread, a shuffle tree per
+// warp, a shuffle tree over the warps (at most 8); the results are on every thread of the block.
+// Pair arithmetic (or plain FP32 sums) throughout: each result is converted to double once, by
+// one lane, since every FP64 instruction of a full warp costs many issue cycles on this part.
+template <int NA, int NB, bool FP64>
+__device__ void ctrl_sums(const ImgDesc& d, int slotA, bool viewA, double* resA, int slotB, bool viewB,
+                          double* resB) {
+  constexpr int NS = NA + NB;
+  static_assert(NS >= 1 && NS <= 32, "at most 32 sums per call");
+  static_assert(kCtrlBlock <= 256 && kRowBlock <= 256, "the tree over the warps takes at most 8 warps");
+  __shared__ FF red[NS][8];
+  __shared__ double fin[NS];
+  const int nA = viewA ? d.n_rv_items : d.n_row_items;
+  const int nB = viewB ? d.n_rv_items : d.n_row_items;
+  const double* bA = (viewA ? d.partv : d.part) + slotA;
+  const double* bB = (viewB ? d.partv : d.part) + slotB;
+  const int n = NB > 0 ? max(nA, nB) : nA;
   FF loc[NS];
 #pragma unroll
-  for (int s = 0; s < NS; ++s) loc[s] = FF{0.0f, 0.0f};
-  const int n = view_list ? d.n_rv_items : d.n_row_items;
-  const double* base = view_list ? d.partv : d.part;
-#pragma unroll 4
+  for (int k = 0; k < NS; ++k) loc[k] = FF{0.0f, 0.0f};
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double* p = base + size_t(i) * kPartStride + slot;
+    FF v[NS];                                       // every load of the item before any use
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const FF v = slot_load(p + s);
-      if (FP64) loc[s] = ff_add(loc[s], v);
-      else loc[s].hi += v.hi;
+    for (int k = 0; k < NA; ++k) v[k] = i < nA ? slot_load(bA + size_t(i) * kPartStride + k) : FF{0.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < NB; ++k) v[NA + k] = i < nB ? slot_load(bB + size_t(i) * kPartStride + k) : FF{0.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      if (FP64) loc[k] = ff_add(loc[k], v[k]);
+      else loc[k].hi += v[k].hi;
     }
   }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = int(blockDim.x >> 5);
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    const FF v = FP64 ? ff_warp_sum(loc[s]) : FF{warp_sum(loc[s].hi), 0.0f};
-    if (lane == 0) red[s][wid] = v;
+  for (int k = 0; k < NS; ++k) {
+    const FF v = FP64 ? ff_warp_sum(loc[k]) : FF{warp_sum(loc[k].hi), 0.0f};
+    if (lane == 0) red[k][wid] = v;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      FF v = lane < nw ? red[k][lane] : FF{0.0f, 0.0f};
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {          // lanes >= 8 hold zeros and never reach lanes < 8
+        const FF w = ff_shfl_xor(v, o);
+        if (FP64) v = ff_add(v, w);
+        else v.hi += w.hi;
+      }
+      if (lane == 0) red[k][0] = v;
+    }
+    __syncwarp();
+    if (lane < NS) fin[lane] = FP64 ? ff_value(red[lane][0]) : double(red[lane][0].hi);
   }
   __syncthreads();
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    FF v = red[s][0];
-    for (int w = 1; w < int(blockDim.x >> 5); ++w) {   // fixed order: deterministic
-      if (FP64) v = ff_add(v, red[s][w]);
-      else v.hi += red[s][w].hi;
-    }
-    res[s] = FP64 ? ff_value(v) : double(v.hi);
-  }
+  for (int k = 0; k < NA; ++k) resA[k] = fin[k];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) resB[k] = fin[NA + k];
   __syncthreads();
+}
+// Sum NS slots over this problem's items (row list or row-view list); see ctrl_sums.
+template <int NS, bool FP64>
+__device__ void ctrl_sum(const ImgDesc& d, int slot, double (&res)[NS], bool view_list) {
+  ctrl_sums<NS, 0, FP64>(d, slot, view_list, res, 0, false, nullptr);
 }
 
 // min over SLOT_MIN and max over SLOT_MAX (plain doubles) of this problem's row items

@@ -21,13 +21,22 @@
 
 namespace sgp {
 
+// Row tiling of width W: T threads per row holding E complex values each, ROWS rows per block of
+// kRowBlock threads.  Rows of 2048 reals run one warp per row (WARP: the four-step transform of
+// warp_fft1024, no block barrier inside the transform, 32 values per lane); the other widths run
+// the block Stockham transform of their Plan.  The launch bounds ask for BLOCKS_HOT (the passes
+// whose registers are held to 64 for the block transform) or BLOCKS_MIN (the others) resident
+// blocks per SM: 2 for the warp rows, i.e. at most 128 registers per thread.
 template <int W> struct RowGeo {
   static constexpr int M = W / 2;
   using P = Plan<M>;
-  static constexpr int T = P::T, E = P::E;
+  static constexpr bool WARP = (M == 1024);
+  static constexpr int T = WARP ? 32 : P::T, E = WARP ? 32 : P::E;
   static constexpr int ROWS = kRowBlock / T;
   static constexpr int PITCH = RowLayout<M>::pitch;
   static constexpr size_t SMEM = size_t(ROWS) * PITCH * sizeof(float2);
+  static constexpr int BLOCKS_HOT = WARP ? 2 : 4;
+  static constexpr int BLOCKS_MIN = WARP ? 2 : 1;
 };
 
 // Pixel pairs per thread whose global loads are issued together, before any of them is used and
@@ -258,7 +267,7 @@ __device__ __forceinline__ void r2c_post(const RowLayout<W / 2>& x, int t, bool 
 // e % 4, column e / 4.  s_rows[r] is row r's start in the plane (nullptr for a row beyond H).
 template <int W>
 __device__ __forceinline__ bool rows_grouped(bool il) {
-  return il && (blockDim.x / RowGeo<W>::T) % 4 == 0;
+  return !RowGeo<W>::WARP && il && (blockDim.x / RowGeo<W>::T) % 4 == 0;
 }
 template <int W>
 __device__ __forceinline__ void rows_store_grouped(float2* const* s_rows, int cb) {
@@ -272,39 +281,128 @@ __device__ __forceinline__ void rows_store_grouped(float2* const* s_rows, int cb
       if (p) p[4 * i] = smem[(4 * g + rr) * G::PITCH + i + (i >> 4)];
     }
 }
+// ------------------------------------------------------------------------------ warp rows (W = 2048)
+// One warp per row of 2048 reals (M = 1024 complex values, 32 per lane; warp_fft1024).  Lane t
+// holds the pixel pairs t + 32 q, q = 0..31, the same pairs the pointwise loops visit with T = 32.
+//
+// C2R: the packed half spectrum X of the row (global, band columns < cb) -> x(t + 32 q) = M times
+// the real pixel pair.  The pre-processing of c2r_pre is applied while loading: for k = 1..M-1
+//   Z[k] = (X[k] + conj X[M-k] + i e^{+2 pi i k / W} (X[k] - conj X[M-k])) / 2,
+// (the pair form of c2r_pre for k and M - k is this one expression at both indices) and
+// Z[0] = ((X0 + XM) / 2, (X0 - XM) / 2) from the packed slot 0.  Lane t loads X[k] and X[M - k]
+// for its own k = t + 32 q only (both 0 outside the band), so no exchange precedes the transform.
+__device__ __forceinline__ void warp_c2r_1024(const RowLayout<1024>& x, const float2* __restrict__ src, int t,
+                                              int cb, bool il) {
+  constexpr int M = 1024;
+  const int s = il ? 4 : 1;
+  const float2 wt = twl<2048, true>(t);                     // e^{+2 pi i t / 2048}
+  float2 v[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) {
+    const int k = t + 32 * q, km = M - k;
+    const float2 z2 = make_float2(0.0f, 0.0f);
+    const float2 a = k < cb ? src[k * s] : z2;
+    const float2 b = (q > 0 || t > 0) && km < cb ? src[km * s] : z2;
+    if (q == 0 && t == 0) {
+      v[q] = make_float2(0.5f * (a.x + a.y), 0.5f * (a.x - a.y));
+    } else {
+      const float2 w = cmul(wt, c_w64[q]);                  // e^{+2 pi i (t + 32 q) / 2048}
+      const float2 e1 = make_float2(a.x + b.x, a.y - b.y);  // a + conj b
+      const float2 o1 = make_float2(a.x - b.x, a.y + b.y);  // a - conj b
+      const float2 wo = cmul(w, o1);
+      v[q] = make_float2(0.5f * (e1.x - wo.y), 0.5f * (e1.y + wo.x));
+    }
+  }
+  warp_fft1024<true>(v, x.base, t);
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 32; ++q) x(t + 32 * q) = v[q];
+  __syncwarp();
+}
+// R2C: x(t + 32 q) (the lane's own pixel pairs) -> the packed half spectrum, band columns < cb
+// stored to dst (stride 4 when interleaved).  r2c_post per index k = 1..M-1:
+//   X[k] = (Z[k] + conj Z[M-k] - i e^{-2 pi i k / W} (Z[k] - conj Z[M-k])) / 2,
+// slot 0 = (Re Z0 + Im Z0, Re Z0 - Im Z0) (X[0] and X[M]), with Z[M - k] read from the lane that
+// holds it through the row buffer.
+__device__ __forceinline__ void warp_r2c_1024(const RowLayout<1024>& x, float2* __restrict__ dst, int t, int cb,
+                                              bool il) {
+  constexpr int M = 1024;
+  const int s = il ? 4 : 1;
+  float2 v[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = x(t + 32 * q);
+  warp_fft1024<false>(v, x.base, t);
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 32; ++q) x(t + 32 * q) = v[q];
+  __syncwarp();
+  const float2 wt = twl<2048, false>(t);                    // e^{-2 pi i t / 2048}
+#pragma unroll
+  for (int q = 0; q < 32; ++q) {
+    const int k = t + 32 * q;
+    if (k < cb) {
+      const float2 a = v[q];
+      float2 X;
+      if (q == 0 && t == 0) {
+        X = make_float2(a.x + a.y, a.x - a.y);
+      } else {
+        const float2 b = x(M - k);
+        const float2 w = cmulc(wt, c_w64[q]);               // e^{-2 pi i (t + 32 q) / 2048}
+        const float2 e1 = make_float2(a.x + b.x, a.y - b.y);
+        const float2 o1 = make_float2(a.x - b.x, a.y + b.y);
+        const float2 wo = cmul(w, o1);
+        X = make_float2(0.5f * (e1.x + wo.y), 0.5f * (e1.y - wo.x));
+      }
+      dst[k * s] = X;
+    }
+  }
+  __syncwarp();
+}
+
 // spectrum row (global) -> real values (times M) in shared memory; ends synchronised
+// (warp rows: each warp transforms its own row; the lane reads back only its own pixel pairs, so
+// no block barrier is needed)
 template <int W>
 __device__ __forceinline__ void row_spec_to_real(const RowLayout<W / 2>& x, const float2* src, int t, bool act,
                                                  bool il, int cb = W / 2) {
-  row_load<W>(x, src, t, act, cb, il);   // (a block-cooperative load measured slower: K6 49 -> 72 us)
-  __syncthreads();
-  c2r_pre<W>(x, t, act);
-  __syncthreads();
-  fft_inplace<W / 2, true>(x, t, act);
+  if constexpr (RowGeo<W>::WARP) {
+    if (act) warp_c2r_1024(x, src, t, cb, il);
+  } else {
+    row_load<W>(x, src, t, act, cb, il);   // (a block-cooperative load measured slower: K6 49 -> 72 us)
+    __syncthreads();
+    c2r_pre<W>(x, t, act);
+    __syncthreads();
+    fft_inplace<W / 2, true>(x, t, act);
+  }
 }
 // real values in shared memory -> spectrum row (global); starts with a barrier
 template <int W>
 __device__ __forceinline__ void row_real_to_spec(const RowLayout<W / 2>& x, float2* dst, int t, bool act,
                                                  bool il, int cb = W / 2) {
-  __syncthreads();
-  fft_inplace<W / 2, false>(x, t, act);
-  r2c_post<W>(x, t, act);
-  if (rows_grouped<W>(il)) {
-    __shared__ float2* s_rows[kRowBlock];
-    if (t == 0) s_rows[threadIdx.x / RowGeo<W>::T] = act ? dst : nullptr;
+  if constexpr (RowGeo<W>::WARP) {
+    if (act) warp_r2c_1024(x, dst, t, cb, il);
     __syncthreads();
-    rows_store_grouped<W>(s_rows, cb);
   } else {
     __syncthreads();
-    row_store<W>(x, dst, t, act, cb, il);
+    fft_inplace<W / 2, false>(x, t, act);
+    r2c_post<W>(x, t, act);
+    if (rows_grouped<W>(il)) {
+      __shared__ float2* s_rows[kRowBlock];
+      if (t == 0) s_rows[threadIdx.x / RowGeo<W>::T] = act ? dst : nullptr;
+      __syncthreads();
+      rows_store_grouped<W>(s_rows, cb);
+    } else {
+      __syncthreads();
+      row_store<W>(x, dst, t, act, cb, il);
+    }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // ------------------------------------------------------------------------------ generic passes
 // out[v] = R2C(max(in[v], 0) if clamp else in[v]) for nviews planes of H x W
 template <int W>
-__global__ void __launch_bounds__(kRowBlock) k_row_r2c(const float* __restrict__ in, size_t in_vs,
+__global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_MIN) k_row_r2c(const float* __restrict__ in, size_t in_vs,
                                                       float2* __restrict__ out, size_t out_vs,
                                                       int H, int nviews, int clamp) {
   using G = RowGeo<W>;
@@ -334,7 +432,7 @@ __global__ void __launch_bounds__(kRowBlock) k_row_r2c(const float* __restrict__
 
 // out[v] = scale * C2R(in[v])
 template <int W>
-__global__ void __launch_bounds__(kRowBlock) k_row_c2r(const float2* __restrict__ in, size_t in_vs,
+__global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_MIN) k_row_c2r(const float2* __restrict__ in, size_t in_vs,
                                                       float* __restrict__ out, size_t out_vs,
                                                       int H, int nviews, float scale) {
   using G = RowGeo<W>;
@@ -495,7 +593,7 @@ __device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ i
   if (arrive_last(d.ctrl, d.n_rv_items)) ctrl_sgp_begin<FP64>(d);
 }
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock, 4) k_sgp_update_ratio(const ImgDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_HOT) k_sgp_update_ratio(const ImgDesc* __restrict__ imgs,
                                                                const int2* __restrict__ items, int n_items) {
   b_sgp_update_ratio<W, FP64>(imgs, items, n_items);
 }
@@ -592,7 +690,7 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
   }
 }
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock, 4) k_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_HOT) k_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
                                                           const int2* __restrict__ items, int n_items) {
   b_sgp_grad_bb<W, FP64>(imgs, items, n_items);
 }
@@ -653,7 +751,7 @@ __device__ __forceinline__ void b_sgp_y(const ImgDesc* __restrict__ imgs,
   }
 }
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock) k_sgp_y(const ImgDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_MIN) k_sgp_y(const ImgDesc* __restrict__ imgs,
                                                     const int2* __restrict__ items, int n_items) {
   b_sgp_y<W, FP64>(imgs, items, n_items);
 }
@@ -726,7 +824,7 @@ __device__ __forceinline__ void b_sgp_ad_armijo(const ImgDesc* __restrict__ imgs
   if (arrive_last(d.ctrl, d.n_rv_items)) ctrl_sgp_lambda<FP64>(d);
 }
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock) k_sgp_ad_armijo(const ImgDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_MIN) k_sgp_ad_armijo(const ImgDesc* __restrict__ imgs,
                                                             const int2* __restrict__ items, int n_items) {
   b_sgp_ad_armijo<W, FP64>(imgs, items, n_items);
 }
@@ -784,12 +882,12 @@ __device__ __forceinline__ void b_sgp_lambda_scan(const ImgDesc* __restrict__ im
   }
 }
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock) k_sgp_armijo_extra(const ImgDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_MIN) k_sgp_armijo_extra(const ImgDesc* __restrict__ imgs,
                                                                const int2* __restrict__ items, int n_items) {
   b_sgp_lambda_scan<W, FP64, false>(imgs, items, n_items);
 }
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock) k_sgp_land(const ImgDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_MIN) k_sgp_land(const ImgDesc* __restrict__ imgs,
                                                        const int2* __restrict__ items, int n_items) {
   b_sgp_lambda_scan<W, FP64, true>(imgs, items, n_items);
 }
@@ -853,7 +951,7 @@ __device__ __forceinline__ void b_rl_update(const ImgDesc* __restrict__ imgs,
   }
 }
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock) k_rl_update(const ImgDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_MIN) k_rl_update(const ImgDesc* __restrict__ imgs,
                                                         const int2* __restrict__ items, int n_items, int wview) {
   b_rl_update<W, FP64>(imgs, items, n_items, wview);
 }
@@ -906,7 +1004,7 @@ __device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
   if (!write_u && arrive_last(d.ctrl, d.n_rv_items)) ctrl_rl<FP64>(d);   // RL iteration (not set-up)
 }
 template <int W, bool FP64>
-__global__ void __launch_bounds__(kRowBlock, 4) k_rl_ratio(const ImgDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_HOT) k_rl_ratio(const ImgDesc* __restrict__ imgs,
                                                        const int2* __restrict__ items, int n_items, int write_u) {
   b_rl_ratio<W, FP64>(imgs, items, n_items, write_u);
 }
@@ -946,7 +1044,7 @@ __device__ __forceinline__ void b_rl_step_minmax(const ImgDesc* __restrict__ img
   }
 }
 template <int W>
-__global__ void __launch_bounds__(kRowBlock) k_rl_step_minmax(const ImgDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_MIN) k_rl_step_minmax(const ImgDesc* __restrict__ imgs,
                                                              const int2* __restrict__ items, int n_items) {
   b_rl_step_minmax<W>(imgs, items, n_items);
 }

@@ -143,6 +143,7 @@ struct Layout {
   size_t bytes = 0;
   int n_row = 0, n_rv = 0, n_colv = 0, n_col = 0, n_colk = 0, n_jobs = 0;
   int cap_row = 0, cap_rv = 0;         // capacity of the row lists (smallest tile)
+  int cap_colb = 0, cap_colvb = 0;     // capacity of the band column lists (smallest column tile)
 };
 
 // Count items and carve every array (base == nullptr: only measure).
@@ -156,6 +157,7 @@ void plan_layout(char* base, int n, const sgp_shape* sh, int trace_cap, const bo
   L.mS.assign(n, nullptr);
   L.n_row = L.n_rv = L.n_colv = L.n_col = L.n_colk = 0;
   L.cap_row = L.cap_rv = 0;
+  L.cap_colb = L.cap_colvb = 0;
   for (int i = 0; i < n; ++i) {
     const int H = sh[i].H, W = sh[i].W, p = sh[i].p;
     const size_t P = size_t(H) * W;
@@ -170,6 +172,10 @@ void plan_layout(char* base, int n, const sgp_shape* sh, int trace_cap, const bo
     d.rv_item0 = 0; d.n_rv_items = nr * p;
     L.n_row += nr; L.n_rv += nr * p; L.n_col += nc; L.n_colv += nc * p; L.n_colk += nc * p;
     L.cap_row += ncap; L.cap_rv += ncap * p;
+    // the band lists may use the narrow column tile (set_band): room for its item count
+    const int cpi_b = H == kNarrowSide ? std::min(cpi, g_reg.col_narrow_cols) : cpi;
+    const int ncb = (M + cpi_b - 1) / cpi_b;
+    L.cap_colb += ncb; L.cap_colvb += ncb * p;
     d.f[0] = cv.take<float>(P); d.f[1] = cv.take<float>(P);
     d.grad[0] = cv.take<float>(P); d.grad[1] = cv.take<float>(P);
     d.u = cv.take<float>(P * p);
@@ -195,9 +201,9 @@ void plan_layout(char* base, int n, const sgp_shape* sh, int trace_cap, const bo
   L.d_rv = cv.take<int2>(L.cap_rv);
   L.d_rvo = cv.take<int2>(L.cap_rv);
   L.d_colv = cv.take<int2>(L.n_colv);
-  L.d_colvo = cv.take<int2>(L.n_colv);
-  L.d_colvb = cv.take<int2>(L.n_colv);
-  L.d_colb = cv.take<int2>(L.n_col);
+  L.d_colvo = cv.take<int2>(L.cap_colvb);
+  L.d_colvb = cv.take<int2>(L.cap_colvb);
+  L.d_colb = cv.take<int2>(L.cap_colb);
   L.d_col = cv.take<int2>(L.n_col);
   L.d_colk = cv.take<int2>(L.n_colk);
   int nj = 0;
@@ -586,6 +592,8 @@ sgp_status apply_band(sgp_ctx* c, const std::vector<int>& raw) {
     for (int j = 0; j < c->p; ++j)
       for (int i : c->order)
         for (int x = 0; x < L.d[i].cb; x += tile_of(L.d[i])) c->colvo.push_back(make_int2(i, x | (j << 16)));
+  if (int(vb.size()) > L.cap_colvb || int(b.size()) > L.cap_colb || int(c->colvo.size()) > L.cap_colvb)
+    return fail(SGP_ERR_ARG, "column tile below the planned minimum");
   L.n_colvb = int(vb.size());
   L.n_colb = int(b.size());
   CU(cudaMemcpyAsync(L.d_colvb, vb.data(), sizeof(int2) * vb.size(), cudaMemcpyHostToDevice, c->s));

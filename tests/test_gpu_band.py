@@ -8,7 +8,7 @@ import pytest
 
 from oracle import sgp_oracle as O
 from paper_1210_2258_b300 import scenes
-from tests.gpu_util import gpu_problem, host, oracle_problem, rel_l2
+from tests.gpu_util import dev, gpu_problem, host, oracle_problem, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -75,3 +75,23 @@ def test_full_size_banded_sgp(gpu):
     assert info.band_cols == 258          # |kx| <= 256: 257 columns, rounded up to the 2-column tile
     assert abs(info.J - ref.J) <= 1e-5 * ref.J, (info.J, ref.J)
     assert rel_l2(host(prob.get_f()), ref.f) <= 1e-3
+
+
+def test_operators_after_column_plan_timing_unbanded(gpu):
+    """A 2048^2 context without the band times both column plans on every column (the narrow plan
+    has more column items than the wide one); the operator passes afterwards use the full column
+    list and must still match the FP64 oracle."""
+    N = 2048
+    psf = scenes.airy_psf(N).astype(np.float32)
+    rng = scenes.rng_for(17)
+    f = (rng.random((N, N)) * 100).astype(np.float32)
+    g = rng.poisson(60.0, (N, N)).astype(np.float32)
+    prob = gpu.Problems(dev(psf[None]), [50.0], None, gpu.default_params(band_tol=0.0))
+    prob.set_data(0, dev(g[None]))
+    prob.sgp_iterate(1)                       # first iteration: band and column plan set up
+    assert prob.info().band_cols == N // 2
+    Af = host(prob.apply_A(dev(f)))[0]
+    orc = O.Problem(psf[None].astype(np.float64), g[None].astype(np.float64), [50.0])
+    assert rel_l2(Af, orc.A(0, f.astype(np.float64))) <= 1e-5
+    ATy = host(prob.apply_AT(dev(g[None])))
+    assert rel_l2(ATy, orc.AT(0, g.astype(np.float64))) <= 1e-5
