@@ -57,20 +57,24 @@ __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b
 // phi(t) = t - log1p(t); for |t| < 1/8 the alternating series t^2 sum_{n>=2} (-t)^(n-2)/n
 // (truncated after n = 9: relative error < 1.3e-8, below FP32 rounding) avoids the cancellation
 // of the direct form.
+__device__ __forceinline__ float phi_series(float t) {
+  float p = -1.0f / 9.0f;
+  p = fmaf(t, p, 1.0f / 8.0f);
+  p = fmaf(t, p, -1.0f / 7.0f);
+  p = fmaf(t, p, 1.0f / 6.0f);
+  p = fmaf(t, p, -1.0f / 5.0f);
+  p = fmaf(t, p, 1.0f / 4.0f);
+  p = fmaf(t, p, -1.0f / 3.0f);
+  p = fmaf(t, p, 0.5f);
+  return t * t * p;
+}
 __device__ __forceinline__ float phi_t(float t) {
-  if (fabsf(t) < 0.125f) {
-    float p = -1.0f / 9.0f;
-    p = fmaf(t, p, 1.0f / 8.0f);
-    p = fmaf(t, p, -1.0f / 7.0f);
-    p = fmaf(t, p, 1.0f / 6.0f);
-    p = fmaf(t, p, -1.0f / 5.0f);
-    p = fmaf(t, p, 1.0f / 4.0f);
-    p = fmaf(t, p, -1.0f / 3.0f);
-    p = fmaf(t, p, 0.5f);
-    return t * t * p;
-  }
+  if (fabsf(t) < 0.125f) return phi_series(t);
   return t - log1pf(t);
 }
+// true on every active lane of the warp when p holds on all of them (the warp then takes a
+// branch-free path; the lanes of a row pass share their loop bounds)
+__device__ __forceinline__ bool warp_all(bool p) { return __all_sync(__activemask(), p); }
 __device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
 
 // KL pixel term g ln(g/u0) + u0 - g and the ratio r - 1 = (g - u0)/u0 (r = 0 where g = 0 or
@@ -79,6 +83,21 @@ __device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
 // (u0 - g) z - 2 g z^3 S(z^2), S(w) = sum_k w^k/(2k+3): both parts are O(z^2), no cancellation.
 // For |z| < 1/3 (1/2 < u0/g < 2) S is truncated after w^6 (relative error < 4e-8 of the second
 // part, itself < 8 % of the term); outside, the direct form has no cancellation to speak of.
+// The series branch of kl_ratio at a pixel with g > 0, u0 > 0: z = (u0 - g)/(u0 + g) from the caller,
+// which checked |z| < 1/3 (the same operations as kl_ratio takes there)
+__device__ __forceinline__ float kl_series(float g, float u0, float z, float& rm1) {
+  const float dlt = u0 - g;
+  rm1 = -dlt / u0;
+  const float w = z * z;
+  float S = 1.0f / 15.0f;
+  S = fmaf(w, S, 1.0f / 13.0f);
+  S = fmaf(w, S, 1.0f / 11.0f);
+  S = fmaf(w, S, 1.0f / 9.0f);
+  S = fmaf(w, S, 1.0f / 7.0f);
+  S = fmaf(w, S, 1.0f / 5.0f);
+  S = fmaf(w, S, 1.0f / 3.0f);
+  return fmaf(dlt, z, -2.0f * g * z * w * S);
+}
 __device__ __forceinline__ float kl_ratio(float g, float u0, float& rm1) {
   if (g < 0.0f) { rm1 = 0.0f; return 0.0f; }
   if (g == 0.0f) { rm1 = -1.0f; return u0; }
@@ -129,6 +148,17 @@ __device__ __forceinline__ void armijo_add(A (&acc)[N], const float (&lam)[N], f
   const float qb = fdiv(ad, u0), gm = u0 - g;
 #pragma unroll
   for (int l = 0; l < N; ++l) acc[l].add(armijo_term(lam[l], qb, gm, g));
+}
+// Armijo terms at a pixel with g > 0, u0 > 0 and |qb| < 1/8, qb = fdiv(A d, u0): every
+// |lam qb| < 1/8 as well (lam <= 1), so the terms are the series branch of armijo_term
+template <int N, class A>
+__device__ __forceinline__ void armijo_series(A (&acc)[N], const float (&lam)[N], float g, float u0, float qb) {
+  const float gm = u0 - g;
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    const float q = lam[l] * qb;
+    acc[l].add(fmaf(gm, q, g * phi_series(q)));
+  }
 }
 // the same for the step lengths lam0 th^l (GEOM) or lam0 + l th (arithmetic), l = 0..N-1, as
 // running products or sums (few registers)
@@ -577,11 +607,35 @@ __device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ i
           u[b].y = fmaf(lam, a[b].y, u[b].y);
           st2(uj, i, u[b]);
         }
-        if (done == 0) {
-          float2 rm;
-          acc[0].add(kl_ratio(g[b].x, u[b].x + bk[b].x, rm.x));
-          acc[0].add(kl_ratio(g[b].y, u[b].y + bk[b].y, rm.y));
-          x(t + (q0 + b) * G::T) = rm;
+      }
+      if (done == 0) {
+        // batches whose pixels all take the series branch of kl_ratio (g > 0, u0 > 0,
+        // |(u0 - g)/(u0 + g)| < 1/3 on the whole warp) run it without the per-pixel branches
+        float2 u0[B], z[B];
+        bool series = true;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          u0[b] = make_float2(u[b].x + bk[b].x, u[b].y + bk[b].y);
+          z[b] = make_float2(fdiv(u0[b].x - g[b].x, u0[b].x + g[b].x), fdiv(u0[b].y - g[b].y, u0[b].y + g[b].y));
+          series = series && g[b].x > 0.0f && u0[b].x > 0.0f && fabsf(z[b].x) < 1.0f / 3.0f &&
+                   g[b].y > 0.0f && u0[b].y > 0.0f && fabsf(z[b].y) < 1.0f / 3.0f;
+        }
+        if (warp_all(series)) {
+#pragma unroll
+          for (int b = 0; b < B; ++b) {
+            float2 rm;
+            acc[0].add(kl_series(g[b].x, u0[b].x, z[b].x, rm.x));
+            acc[0].add(kl_series(g[b].y, u0[b].y, z[b].y, rm.y));
+            x(t + (q0 + b) * G::T) = rm;
+          }
+        } else {
+#pragma unroll
+          for (int b = 0; b < B; ++b) {
+            float2 rm;
+            acc[0].add(kl_ratio(g[b].x, u0[b].x, rm.x));
+            acc[0].add(kl_ratio(g[b].y, u0[b].y, rm.y));
+            x(t + (q0 + b) * G::T) = rm;
+          }
         }
       }
     }
@@ -774,12 +828,31 @@ __device__ __forceinline__ void sgp_armijo_rows(const RowLayout<W / 2>& x, A (&a
       const size_t i = off + t + (q0 + b) * G::T;
       u[b] = ld2(uj, i); g[b] = ld2(gj, i); bk[b] = b_pair(d, j, i);
     }
+    // batches whose pixels all take the series branch (g > 0, u0 > 0, |A d / u0| < 1/8 on the
+    // whole warp: the usual case) run it without the per-pixel branches; identical terms
+    float2 ad[B], u0[B], qb[B];
+    bool series = true;
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-      const float2 ad = x(t + (q0 + b) * G::T);
-      st2(adj, off + t + (q0 + b) * G::T, ad);
-      armijo_add<N>(accN, lamN, g[b].x, u[b].x + bk[b].x, ad.x);
-      armijo_add<N>(accN, lamN, g[b].y, u[b].y + bk[b].y, ad.y);
+      ad[b] = x(t + (q0 + b) * G::T);
+      st2(adj, off + t + (q0 + b) * G::T, ad[b]);
+      u0[b] = make_float2(u[b].x + bk[b].x, u[b].y + bk[b].y);
+      qb[b] = make_float2(fdiv(ad[b].x, u0[b].x), fdiv(ad[b].y, u0[b].y));
+      series = series && g[b].x > 0.0f && u0[b].x > 0.0f && fabsf(qb[b].x) < 0.125f &&
+               g[b].y > 0.0f && u0[b].y > 0.0f && fabsf(qb[b].y) < 0.125f;
+    }
+    if (warp_all(series)) {
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        armijo_series<N>(accN, lamN, g[b].x, u0[b].x, qb[b].x);
+        armijo_series<N>(accN, lamN, g[b].y, u0[b].y, qb[b].y);
+      }
+    } else {
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        armijo_add<N>(accN, lamN, g[b].x, u0[b].x, ad[b].x);
+        armijo_add<N>(accN, lamN, g[b].y, u0[b].y, ad[b].y);
+      }
     }
   }
 }
