@@ -32,11 +32,11 @@ __device__ inline void trace_push(const ImgDesc& d, CtrlState* c, double k, doub
 template <class V>
 __device__ inline double bb_alpha(CtrlState* c, V n1, V d1, V n2, V d2, int k) {
   const V amin = V(c->alpha_min), amax = V(c->alpha_max), aprev = V(c->alpha);
-  V a1, a2;
-  if (d1 <= V(0)) a1 = fmin(V(10) * aprev, amax);
-  else a1 = fmin(amax, fmax(amin, n1 / d1));
-  if (n2 <= V(0)) a2 = fmin(V(10) * aprev, amax);
-  else a2 = fmin(amax, fmax(amin, n2 / d2));
+  // both quotients before either is used, so that the two (long-latency) divisions overlap; a
+  // quotient whose guard fails is not used
+  const V q1 = n1 / d1, q2 = n2 / d2;
+  const V a1 = d1 <= V(0) ? fmin(V(10) * aprev, amax) : fmin(amax, fmax(amin, q1));
+  const V a2 = n2 <= V(0) ? fmin(V(10) * aprev, amax) : fmin(amax, fmax(amin, q2));
   // window of the last M_alpha values of alpha^(2), Eq. (alphadef)
   if (c->hist_n < c->M_alpha) c->hist[c->hist_n++] = double(a2);
   else {
@@ -47,7 +47,7 @@ __device__ inline double bb_alpha(CtrlState* c, V n1, V d1, V n2, V d2, int k) {
   for (int i = 1; i < c->hist_n; ++i) wmin = fmin(wmin, V(c->hist[i]));
   V alpha;
   if (k <= c->warmup) { alpha = wmin; c->branch = 2; }
-  else if (a2 / a1 <= V(c->tau)) { alpha = wmin; c->tau *= 0.9; c->branch = 2; }
+  else if (a2 <= V(c->tau) * a1) { alpha = wmin; c->tau *= 0.9; c->branch = 2; }   // a2 / a1 <= tau, a1 > 0
   else { alpha = a1; c->tau *= 1.1; c->branch = 1; }
   return double(alpha);
 }

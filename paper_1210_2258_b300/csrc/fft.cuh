@@ -97,8 +97,12 @@ __device__ __forceinline__ float2 twr(float2 v, int e) {
   }
 }
 
-// supported transform lengths and the offsets of their tables exp(-2 pi i q / L), q < L
-constexpr int kTwiddleTotal = 7148;
+// supported transform lengths and the offsets of their tables exp(-2 pi i q / L), q < L, followed
+// by the twiddles of the warp four-step transform (warp_fft1024) stored lane-fastest:
+// entry kTw4Offset + 32 q + lane = exp(-2 pi i lane q / 1024), so that the 32 lanes of a warp read
+// 256 contiguous bytes per q instead of 32 scattered entries
+constexpr int kTw4Offset = 7148;
+constexpr int kTwiddleTotal = kTw4Offset + 1024;
 __host__ __device__ constexpr int tw_offset(int L) {
   return L == 8 ? 0 : L == 12 ? 8 : L == 16 ? 20 : L == 24 ? 36 : L == 32 ? 60 : L == 48 ? 92 :
          L == 64 ? 140 : L == 96 ? 204 : L == 128 ? 300 : L == 192 ? 428 : L == 256 ? 620 :
@@ -115,6 +119,12 @@ __device__ float2 g_twiddle[kTwiddleTotal];
     return cudaMemcpyToSymbol(::sgp::g_twiddle, host_table, sizeof(float2) * ::sgp::kTwiddleTotal);  \
   }
 
+template <bool INV>
+__device__ __forceinline__ float2 tw4(int lane, int q) {  // exp(-/+ 2 pi i lane q / 1024), q < 32
+  asm volatile("" : "+r"(lane));
+  const float2 w = __ldg(&g_twiddle[kTw4Offset + 32 * q + lane]);
+  return INV ? cconj(w) : w;
+}
 template <int L, bool INV>
 __device__ __forceinline__ float2 twl(int q) {  // exp(-/+ 2 pi i q / L), 0 <= q < L
   // the empty asm keeps the load after the preceding barrier: read-only loads may otherwise be
@@ -344,7 +354,7 @@ template <bool INV>
 __device__ __forceinline__ void warp_fft1024(float2 (&v)[32], float2* T, int lane) {
   DFT<32, INV>::run(v);
 #pragma unroll
-  for (int q = 1; q < 32; ++q) v[q] = cmul(v[q], twl<1024, INV>(lane * q));
+  for (int q = 1; q < 32; ++q) v[q] = cmul(v[q], tw4<INV>(lane, q));
   __syncwarp();
 #pragma unroll
   for (int q = 0; q < 32; ++q) T[q * 33 + lane] = v[q];

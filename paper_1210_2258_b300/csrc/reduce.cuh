@@ -104,66 +104,103 @@ __device__ __forceinline__ void block_sum_store(const Acc<FP64> (&loc)[NS], doub
 }
 
 // Sum NA slots (from slotA) over list A and NB slots (from slotB) over list B of this problem's
-// items (row list or row-view list) in one pass, in a fixed order: per thread, a shuffle tree per
-// warp, a shuffle tree over the warps (at most 8); the results are on every thread of the block.
+// items (row list or row-view list) in a fixed order; the results are on every thread of the block.
 // Pair arithmetic (or plain FP32 sums) throughout: each result is converted to double once, by
-// one lane, since every FP64 instruction of a full warp costs many issue cycles on this part.
+// one lane (an FP64 operation has a latency of about 60 cycles on this part, an FP32 one 4).
+// This runs in the one block that finishes a pass last, while the rest of the GPU waits for it,
+// so its latency is what counts.  Up to 8 sums: warp w sums slot w over all items, each lane 8
+// items per load round (all loads in flight together), then one shuffle tree; a single global
+// round trip and no block-level tree.  More sums: every thread loads all sums of one item, a
+// shuffle tree per warp, a tree over the warps (at most 8).
 template <int NA, int NB, bool FP64>
 __device__ void ctrl_sums(const ImgDesc& d, int slotA, bool viewA, double* resA, int slotB, bool viewB,
                           double* resB) {
   constexpr int NS = NA + NB;
   static_assert(NS >= 1 && NS <= 32, "at most 32 sums per call");
-  static_assert(kCtrlBlock <= 256 && kRowBlock <= 256, "the tree over the warps takes at most 8 warps");
-  __shared__ FF red[NS][8];
-  __shared__ double fin[NS];
-  const int nA = viewA ? d.n_rv_items : d.n_row_items;
-  const int nB = viewB ? d.n_rv_items : d.n_row_items;
-  const double* bA = (viewA ? d.partv : d.part) + slotA;
-  const double* bB = (viewB ? d.partv : d.part) + slotB;
-  const int n = NB > 0 ? max(nA, nB) : nA;
-  FF loc[NS];
+  if constexpr (NS <= 8) {
+    __shared__ double fin8[NS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = int(blockDim.x >> 5);
+    for (int k = wid; k < NS; k += nw) {
+      const bool isA = k < NA;
+      const bool view = isA ? viewA : viewB;
+      const int n = view ? d.n_rv_items : d.n_row_items;
+      const double* b = (view ? d.partv : d.part) + (isA ? slotA + k : slotB + (k - NA));
+      FF acc{0.0f, 0.0f};
+      for (int i0 = 0; i0 < n; i0 += 256) {
+        FF v[8];                                    // every load of the round before any use
 #pragma unroll
-  for (int k = 0; k < NS; ++k) loc[k] = FF{0.0f, 0.0f};
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    FF v[NS];                                       // every load of the item before any use
+        for (int q = 0; q < 8; ++q) {
+          const int i = i0 + lane + 32 * q;
+          v[q] = i < n ? slot_load(b + size_t(i) * kPartStride) : FF{0.0f, 0.0f};
+        }
 #pragma unroll
-    for (int k = 0; k < NA; ++k) v[k] = i < nA ? slot_load(bA + size_t(i) * kPartStride + k) : FF{0.0f, 0.0f};
-#pragma unroll
-    for (int k = 0; k < NB; ++k) v[NA + k] = i < nB ? slot_load(bB + size_t(i) * kPartStride + k) : FF{0.0f, 0.0f};
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      if (FP64) loc[k] = ff_add(loc[k], v[k]);
-      else loc[k].hi += v[k].hi;
-    }
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = int(blockDim.x >> 5);
-#pragma unroll
-  for (int k = 0; k < NS; ++k) {
-    const FF v = FP64 ? ff_warp_sum(loc[k]) : FF{warp_sum(loc[k].hi), 0.0f};
-    if (lane == 0) red[k][wid] = v;
-  }
-  __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      FF v = lane < nw ? red[k][lane] : FF{0.0f, 0.0f};
-#pragma unroll
-      for (int o = 4; o > 0; o >>= 1) {          // lanes >= 8 hold zeros and never reach lanes < 8
-        const FF w = ff_shfl_xor(v, o);
-        if (FP64) v = ff_add(v, w);
-        else v.hi += w.hi;
+        for (int q = 0; q < 8; ++q) {
+          if (FP64) acc = ff_add(acc, v[q]);
+          else acc.hi += v[q].hi;
+        }
       }
-      if (lane == 0) red[k][0] = v;
+      acc = FP64 ? ff_warp_sum(acc) : FF{warp_sum(acc.hi), 0.0f};
+      if (lane == 0) fin8[k] = FP64 ? ff_value(acc) : double(acc.hi);
     }
-    __syncwarp();
-    if (lane < NS) fin[lane] = FP64 ? ff_value(red[lane][0]) : double(red[lane][0].hi);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NA; ++k) resA[k] = fin8[k];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) resB[k] = fin8[NA + k];
+    __syncthreads();
+  } else {
+    static_assert(kCtrlBlock <= 256 && kRowBlock <= 256, "the tree over the warps takes at most 8 warps");
+    __shared__ FF red[NS][8];
+    __shared__ double fin[NS];
+    const int nA = viewA ? d.n_rv_items : d.n_row_items;
+    const int nB = viewB ? d.n_rv_items : d.n_row_items;
+    const double* bA = (viewA ? d.partv : d.part) + slotA;
+    const double* bB = (viewB ? d.partv : d.part) + slotB;
+    const int n = NB > 0 ? max(nA, nB) : nA;
+    FF loc[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) loc[k] = FF{0.0f, 0.0f};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      FF v[NS];                                       // every load of the item before any use
+#pragma unroll
+      for (int k = 0; k < NA; ++k) v[k] = i < nA ? slot_load(bA + size_t(i) * kPartStride + k) : FF{0.0f, 0.0f};
+#pragma unroll
+      for (int k = 0; k < NB; ++k) v[NA + k] = i < nB ? slot_load(bB + size_t(i) * kPartStride + k) : FF{0.0f, 0.0f};
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        if (FP64) loc[k] = ff_add(loc[k], v[k]);
+        else loc[k].hi += v[k].hi;
+      }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = int(blockDim.x >> 5);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const FF v = FP64 ? ff_warp_sum(loc[k]) : FF{warp_sum(loc[k].hi), 0.0f};
+      if (lane == 0) red[k][wid] = v;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        FF v = lane < nw ? red[k][lane] : FF{0.0f, 0.0f};
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {          // lanes >= 8 hold zeros and never reach lanes < 8
+          const FF w = ff_shfl_xor(v, o);
+          if (FP64) v = ff_add(v, w);
+          else v.hi += w.hi;
+        }
+        if (lane == 0) red[k][0] = v;
+      }
+      __syncwarp();
+      if (lane < NS) fin[lane] = FP64 ? ff_value(red[lane][0]) : double(red[lane][0].hi);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NA; ++k) resA[k] = fin[k];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) resB[k] = fin[NA + k];
+    __syncthreads();
   }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NA; ++k) resA[k] = fin[k];
-#pragma unroll
-  for (int k = 0; k < NB; ++k) resB[k] = fin[NA + k];
-  __syncthreads();
 }
 // Sum NS slots over this problem's items (row list or row-view list); see ctrl_sums.
 template <int NS, bool FP64>

@@ -75,6 +75,11 @@ sgp_status ensure_device_ready(int dev) {
       tab[off + q] = make_float2(float(cos(a)), float(sin(a)));
     }
   }
+  for (int q = 0; q < 32; ++q)   // the four-step table, lane-fastest
+    for (int lane = 0; lane < 32; ++lane) {
+      const double a = -2.0 * M_PI * double(lane * q) / 1024.0;
+      tab[kTw4Offset + 32 * q + lane] = make_float2(float(cos(a)), float(sin(a)));
+    }
   for (int i = 0; i < kTwiddleUnits; ++i)
     if (g_reg.twiddle_init[i]) CU(g_reg.twiddle_init[i](tab.data()));
   for (int op = 0; op < ROP_COUNT; ++op)
