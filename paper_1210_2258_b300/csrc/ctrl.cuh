@@ -354,11 +354,13 @@ __global__ void k_make_w(const float* __restrict__ alpha, int p, size_t P, float
 }
 
 // Condition of the device-side solve loop (a WHILE node of a CUDA graph, see run_until): keep
-// iterating while some problem has not stopped (done == 0) and fewer than `cap` iterations have
+// iterating while some problem has not stopped (done == 0) and fewer than `cap` bodies have
 // run since the launch (counter, zeroed by the host before the launch).  One block; it is the last
-// node of the loop body, so it sees the controllers' decisions of this iteration.
+// node of the loop body, so it sees the controllers' decisions of this iteration.  Launched as a
+// programmatic dependent of the body's last pass: it waits for that pass before reading.
 __global__ void k_loop_cond(const ImgDesc* __restrict__ imgs, int n, cudaGraphConditionalHandle h,
                             int* __restrict__ counter, int cap) {
+  pdl_enter();
   __shared__ int running;
   if (threadIdx.x == 0) running = 0;
   __syncthreads();

@@ -321,18 +321,20 @@ __device__ __forceinline__ void rows_store_grouped(float2* const* s_rows, int cb
 // (the pair form of c2r_pre for k and M - k is this one expression at both indices) and
 // Z[0] = ((X0 + XM) / 2, (X0 - XM) / 2) from the packed slot 0.  Lane t loads X[k] and X[M - k]
 // for its own k = t + 32 q only (both 0 outside the band), so no exchange precedes the transform.
-__device__ __forceinline__ void warp_c2r_1024(const RowLayout<1024>& x, const float2* __restrict__ src, int t,
-                                              int cb, bool il) {
+// The result stays in v (lane t: pixel pairs t + 32 q); tb is the warp's transpose buffer.  Loads
+// whose whole warp lies outside the band are skipped by a warp-uniform test.
+__device__ __forceinline__ void warp_c2r_1024_v(float2 (&v)[32], const float2* __restrict__ src, int t, int cb,
+                                                bool il, float2* tb) {
   constexpr int M = 1024;
   const int s = il ? 4 : 1;
   const float2 wt = twl<2048, true>(t);                     // e^{+2 pi i t / 2048}
-  float2 v[32];
 #pragma unroll
   for (int q = 0; q < 32; ++q) {
     const int k = t + 32 * q, km = M - k;
     const float2 z2 = make_float2(0.0f, 0.0f);
-    const float2 a = k < cb ? src[k * s] : z2;
-    const float2 b = (q > 0 || t > 0) && km < cb ? src[km * s] : z2;
+    float2 a = z2, b = z2;
+    if (32 * q < cb) a = k < cb ? src[k * s] : z2;                               // some lane: k < cb
+    if (M - 32 * q - 31 < cb) b = (q > 0 || t > 0) && km < cb ? src[km * s] : z2; // some lane: M - k < cb
     if (q == 0 && t == 0) {
       v[q] = make_float2(0.5f * (a.x + a.y), 0.5f * (a.x - a.y));
     } else {
@@ -343,7 +345,12 @@ __device__ __forceinline__ void warp_c2r_1024(const RowLayout<1024>& x, const fl
       v[q] = make_float2(0.5f * (e1.x - wo.y), 0.5f * (e1.y + wo.x));
     }
   }
-  warp_fft1024<true>(v, x.base, t);
+  warp_fft1024<true>(v, tb, t);
+}
+__device__ __forceinline__ void warp_c2r_1024(const RowLayout<1024>& x, const float2* __restrict__ src, int t,
+                                              int cb, bool il) {
+  float2 v[32];
+  warp_c2r_1024_v(v, src, t, cb, il, x.base);
   __syncwarp();
 #pragma unroll
   for (int q = 0; q < 32; ++q) x(t + 32 * q) = v[q];

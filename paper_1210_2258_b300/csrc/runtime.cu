@@ -677,11 +677,14 @@ sgp_status build_graph(sgp_ctx* c, bool sgp, cudaGraphExec_t* out) {
 }
 
 // Fresh controller state for every problem, with the current iterate moved to f[0].
-// The solve loop of run_until as one graph: a WHILE node whose body is one iteration (the same
-// passes as a unit of build_graph) followed by k_loop_cond, which ends the loop when every
-// problem has stopped or after `cap` iterations.  The iteration count stays on the device, so a
-// solve needs no host round trip and runs no idle iterations after the stop.
+// The solve loop of run_until as one graph: a WHILE node whose body is kLoopUnroll iterations
+// (the same passes as a unit of build_graph) followed by k_loop_cond, which ends the loop when
+// every problem has stopped or after `cap` bodies.  The iteration count stays on the device, so a
+// solve needs no host round trip.  Every pass of an iteration returns at once for a problem that
+// has stopped, so an iteration of the body after the stop costs only its launches; two iterations
+// per body halve the loop's own cost (the condition kernel and the relaunch of the body).
 constexpr int kLoopCounter = 4;   // index of the loop counter in L.d_flag
+constexpr int kLoopUnroll = 2;    // iterations per body of the solve loop
 sgp_status build_loop_graph(sgp_ctx* c, bool sgp, bool land, int cap, cudaGraphExec_t* out,
                             cudaGraphConditionalHandle* hout) {
   if (*out) return SGP_OK;
@@ -706,13 +709,14 @@ sgp_status build_loop_graph(sgp_ctx* c, bool sgp, bool land, int cap, cudaGraphE
   }
   long long* saved = g_launch_counter;
   g_launch_counter = nullptr;
-  sgp_status st = sgp ? seq_sgp_unit(c, land) : seq_rl_unit(c);
+  sgp_status st = SGP_OK;
+  for (int u = 0; u < kLoopUnroll && st == SGP_OK; ++u) st = sgp ? seq_sgp_unit(c, land) : seq_rl_unit(c);
   if (st == SGP_OK) {
     const ImgDesc* imgs = c->L.d_imgs;
-    int n = c->n, cp = cap;
+    int n = c->n, cp = (cap + kLoopUnroll - 1) / kLoopUnroll;
     int* counter = c->L.d_flag + kLoopCounter;
     void* a[] = {(void*)&imgs, (void*)&n, (void*)&h, (void*)&counter, (void*)&cp};
-    st = launch((const void*)&k_loop_cond, 1, 128, 0, c->s, a);
+    st = launch_pdl((const void*)&k_loop_cond, 1, 128, 0, c->s, a);
   }
   cudaGraph_t body = nullptr;
   e = cudaStreamEndCapture(c->s, &body);
@@ -919,7 +923,7 @@ sgp_status run_until(sgp_ctx* c, bool sgp, const sgp_stop_rule* rule, int* iters
     for (int i = 0; i < c->n; ++i)
       if (!c->truth[i]) return fail(SGP_ERR_ARG, "minimum-error stop needs sgp_set_truth");
   // one graph launch: a device-side loop of iterations until every problem has stopped (or
-  // max_iter + 2 iterations, past the controllers' own cap)
+  // at least max_iter + 2 iterations, past the controllers' own cap)
   const int cap = rule->max_iter + 2;
   cudaGraphExec_t* gp = land ? &c->gl_land : (sgp ? &c->gl_sgp : &c->gl_rl);
   cudaGraphConditionalHandle* hp = land ? &c->hl_land : (sgp ? &c->hl_sgp : &c->hl_rl);
@@ -932,16 +936,17 @@ sgp_status run_until(sgp_ctx* c, bool sgp, const sgp_stop_rule* rule, int* iters
   if ((st = build_loop_graph(c, sgp, land, cap, gp, hp))) return st;
   if ((st = arm(c, rule->kind, rule->max_iter, tol, rule->eta))) return st;
   const int vs = (c->p > 1 && !c->mixed) ? 1 : 0;      // view-sum launch of the adjoint
-  const int per_iter = (sgp ? (c->prm.constraint == 1 ? kSgpLaunches + kFluxLaunches : kSgpLaunches) +
-                                  (land ? kLandPasses : 0) + vs
-                            : kRlLaunches + vs) + 1;   // + the loop condition
+  const int per_iter = sgp ? (c->prm.constraint == 1 ? kSgpLaunches + kFluxLaunches : kSgpLaunches) +
+                                 (land ? kLandPasses : 0) + vs
+                           : kRlLaunches + vs;
+  const int per_body = kLoopUnroll * per_iter + 1;   // + the loop condition
   CU(cudaMemsetAsync(c->L.d_flag + kLoopCounter, 0, sizeof(int), c->s));
   CU(cudaGraphLaunch(*gp, c->s));
   if (sgp && (st = seq_sgp_finalize(c))) return st;
   int bodies = 0;
   CU(cudaMemcpyAsync(&bodies, c->L.d_flag + kLoopCounter, sizeof(int), cudaMemcpyDeviceToHost, c->s));
   if ((st = read_ctrl(c, c->h_ctrl))) return st;
-  c->launches += (long long)bodies * per_iter;
+  c->launches += (long long)bodies * per_body;
   sgp_status res = SGP_OK;
   for (int i = 0; i < c->n; ++i) {
     const CtrlState& h = c->h_ctrl[i];
