@@ -18,10 +18,10 @@
 
 namespace sgp {
 
-__device__ inline void trace_push(const ImgDesc& d, CtrlState* c, double k, double J, double alpha,
+__device__ inline void trace_push(double* trace, CtrlState* c, double k, double J, double alpha,
                                   double lam, int bt, int branch, double gTd) {
   if (c->trace_n < c->trace_cap) {
-    double* r = d.trace + size_t(c->trace_n) * kTraceStride;
+    double* r = trace + size_t(c->trace_n) * kTraceStride;
     r[0] = k; r[1] = J; r[2] = 2.0 * J * c->inv_pS; r[3] = alpha; r[4] = lam;
     r[5] = bt; r[6] = branch; r[7] = gTd;
   }
@@ -152,7 +152,7 @@ __device__ __forceinline__ double reg_delta(const CtrlState* c, double lam) {
   return c->reg_beta > 0.0 ? c->reg_beta * (lam * c->reg_fd + 0.5 * lam * lam * c->reg_dd) : 0.0;
 }
 
-__device__ inline void sgp_accept(const ImgDesc& d, CtrlState* c, int nb, double lam, double dJ) {
+__device__ inline void sgp_accept(double* trace, CtrlState* c, int nb, double lam, double dJ) {
   c->lambda = lam;
   c->backtracks = nb;
   c->dJ = dJ;
@@ -162,7 +162,7 @@ __device__ inline void sgp_accept(const ImgDesc& d, CtrlState* c, int nb, double
   c->need_more = 0;
   c->arm_nl = nb == 0 ? 1 : (nb == 1 ? 2 : kArmMain);
   const int kn = c->k + 1;
-  trace_push(d, c, kn, c->J_pred, c->alpha, lam, nb, c->branch, c->gTd);
+  trace_push(trace, c, kn, c->J_pred, c->alpha, lam, nb, c->branch, c->gTd);
   bool rule = false;                  // the stop rule itself fired (not only the iteration cap)
   // Eq. (convergence) on the objective J_0 + R (R = 0 without regularisation)
   if (c->stop_kind == STOP_CONVERGENCE &&
@@ -189,7 +189,7 @@ __device__ inline void sgp_accept(const ImgDesc& d, CtrlState* c, int nb, double
 // candidate with J <= Jt closes the new bracket.  After the last pass lambda interpolates J
 // linearly between the bracket ends; by convexity the chord lies above J, so the stored J_pred
 // (= Jt) bounds the true value from above and the discrepancy ends at most eta (1 - tol/2).
-__device__ inline void sgp_land_decide(const ImgDesc& d, CtrlState* c, const double (&dj)[kLandCand]) {
+__device__ inline void sgp_land_decide(double* trace, CtrlState* c, const double (&dj)[kLandCand]) {
   const double lo = c->land_lo, hi = c->land_hi, h = (hi - lo) / double(kLandCand + 1);
   double nlo = lo, nhi = hi, Jlo = c->land_Jlo, Jhi = c->land_Jhi;
   for (int i = 0; i < kLandCand; ++i) {
@@ -210,23 +210,24 @@ __device__ inline void sgp_land_decide(const ImgDesc& d, CtrlState* c, const dou
   c->land_pass = 0;
   c->done = 1;
   if (c->trace_n >= 1 && c->trace_n <= c->trace_cap) {   // the record sgp_accept wrote
-    double* r = d.trace + size_t(c->trace_n - 1) * kTraceStride;
+    double* r = trace + size_t(c->trace_n - 1) * kTraceStride;
     r[1] = Jp; r[2] = 2.0 * Jp * c->inv_pS; r[4] = lam;
   }
 }
 template <bool FP64>
 __device__ void ctrl_sgp_land(const ImgDesc& d) {
   __shared__ CtrlState s;
+  double* const trace = d.trace;                  // loaded while the partial sums are read
   const CtrlCopy cp(d.ctrl);
   double dj[kLandCand];
   ctrl_sum<kLandCand, FP64>(d, SLOT_ARMX, dj, false);
   cp.to_shared(s);
-  if (threadIdx.x == 0) sgp_land_decide(d, &s, dj);
+  if (threadIdx.x == 0) sgp_land_decide(trace, &s, dj);
   CtrlCopy::write_back(s, d.ctrl);
 }
 
 template <bool FP64>
-__device__ void sgp_lambda_decide(const ImgDesc& d, CtrlState* c, double gTd, const double (&arm)[kArmMain]) {
+__device__ void sgp_lambda_decide(double* trace, CtrlState* c, double gTd, const double (&arm)[kArmMain]) {
   c->gTd = gTd;
   if (!isfinite(gTd)) { c->status = 8; c->done = 2; return; }
   double lam = 1.0;
@@ -235,7 +236,7 @@ __device__ void sgp_lambda_decide(const ImgDesc& d, CtrlState* c, double gTd, co
     const double dobj = arm[i] + reg_delta(c, lam);   // change of J_0 + R
     const bool ok = FP64 ? (dobj <= c->beta * lam * gTd)
                          : (float(dobj) <= float(c->beta) * float(lam) * float(gTd));
-    if (ok) { sgp_accept(d, c, i, lam, arm[i]); return; }
+    if (ok) { sgp_accept(trace, c, i, lam, arm[i]); return; }
     lam *= c->theta;
   }
   c->need_more = 1;
@@ -243,21 +244,23 @@ __device__ void sgp_lambda_decide(const ImgDesc& d, CtrlState* c, double gTd, co
 template <bool FP64>
 __device__ void ctrl_sgp_lambda(const ImgDesc& d) {
   __shared__ CtrlState s;
+  double* const trace = d.trace;                  // both loaded while the partial sums are read
+  const bool reg = d.reg_beta > 0.0f;
   const CtrlCopy cp(d.ctrl);
   double g[1], arm[kArmMain], rg[2] = {0.0, 0.0};
   ctrl_sums<1, kArmMain, FP64>(d, SLOT_GTD, false, g, SLOT_ARM, true, arm);
-  if (d.reg_beta > 0.0f) ctrl_sum<2, FP64>(d, SLOT_REG, rg, false);   // f'd, d'd of this direction
+  if (reg) ctrl_sum<2, FP64>(d, SLOT_REG, rg, false);   // f'd, d'd of this direction
   cp.to_shared(s);
   if (threadIdx.x == 0) {
     s.reg_fd = rg[0];
     s.reg_dd = rg[1];
-    sgp_lambda_decide<FP64>(d, &s, g[0], arm);
+    sgp_lambda_decide<FP64>(trace, &s, g[0], arm);
   }
   CtrlCopy::write_back(s, d.ctrl);
 }
 
 template <bool FP64>
-__device__ void sgp_lambda_extra_decide(const ImgDesc& d, CtrlState* c, const double (&arm)[kArmExtra]) {
+__device__ void sgp_lambda_extra_decide(double* trace, CtrlState* c, const double (&arm)[kArmExtra]) {
   const int nl = arm_count(c);
   double lam = 1.0;
   for (int i = 0; i < nl; ++i) lam *= c->theta;
@@ -266,7 +269,7 @@ __device__ void sgp_lambda_extra_decide(const ImgDesc& d, CtrlState* c, const do
     const double dobj = arm[i] + reg_delta(c, lam);
     const bool ok = FP64 ? (dobj <= c->beta * lam * gTd)
                          : (float(dobj) <= float(c->beta) * float(lam) * float(gTd));
-    if (ok) { sgp_accept(d, c, nl + i, lam, arm[i]); return; }
+    if (ok) { sgp_accept(trace, c, nl + i, lam, arm[i]); return; }
     lam *= c->theta;
   }
   c->need_more = 0;
@@ -276,16 +279,17 @@ __device__ void sgp_lambda_extra_decide(const ImgDesc& d, CtrlState* c, const do
 template <bool FP64>
 __device__ void ctrl_sgp_lambda_extra(const ImgDesc& d) {
   __shared__ CtrlState s;
+  double* const trace = d.trace;                  // loaded while the partial sums are read
   const CtrlCopy cp(d.ctrl);
   double arm[kArmExtra];
   ctrl_sum<kArmExtra, FP64>(d, SLOT_ARMX, arm, false);
   cp.to_shared(s);
-  if (threadIdx.x == 0) sgp_lambda_extra_decide<FP64>(d, &s, arm);
+  if (threadIdx.x == 0) sgp_lambda_extra_decide<FP64>(trace, &s, arm);
   CtrlCopy::write_back(s, d.ctrl);
 }
 
 template <bool FP64>
-__device__ void rl_decide(const ImgDesc& d, CtrlState* c, double kl, double rr) {
+__device__ void rl_decide(double* trace, CtrlState* c, double kl, double rr) {
   const bool updated = c->have_v;
   if (updated) c->k += 1;
   c->have_v = 1;
@@ -293,7 +297,7 @@ __device__ void rl_decide(const ImgDesc& d, CtrlState* c, double kl, double rr) 
   if (!isfinite(kl)) { c->status = 8; c->done = 2; c->have_v = 0; return; }
   c->J_prev = c->J;
   c->J = kl;
-  if (updated) trace_push(d, c, c->k, c->J, 0.0, 1.0, 0, 0, 0.0);
+  if (updated) trace_push(trace, c, c->k, c->J, 0.0, 1.0, 0, 0, 0.0);
   if (c->stop_kind == STOP_MIN_ERROR && c->ftrue_norm2 > 0.0) {
     const double rho = sqrt(rr / c->ftrue_norm2);
     c->rho = rho;
@@ -319,11 +323,12 @@ __device__ inline void osem_tick(CtrlState* c, int have_v_after) {
 template <bool FP64>
 __device__ void ctrl_rl(const ImgDesc& d) {
   __shared__ CtrlState s;
+  double* const trace = d.trace;                  // loaded while the partial sums are read
   const CtrlCopy cp(d.ctrl);
   double kl[1], rr[1];
   ctrl_sums<1, 1, FP64>(d, SLOT_KL, true, kl, SLOT_RHO, false, rr);
   cp.to_shared(s);
-  if (threadIdx.x == 0) rl_decide<FP64>(d, &s, kl[0], rr[0]);
+  if (threadIdx.x == 0) rl_decide<FP64>(trace, &s, kl[0], rr[0]);
   CtrlCopy::write_back(s, d.ctrl);
 }
 
