@@ -25,6 +25,10 @@
 namespace sgp {
 
 
+// columns of 2048 (the iteration's column passes at the largest supported side, one block per SM
+// over the PSF band: latency-bound) form their twiddles from fewer table entries (stage_twiddles)
+template <int H> constexpr bool kColPowTwiddles = H == 2048;
+
 template <int H, bool NARROW = false> struct ColGeo {
   using P = typename std::conditional<NARROW, ColPlanNarrow<H>, ColPlan<H>>::type;
   static constexpr int T = P::T, E = P::E;
@@ -92,7 +96,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
     if (MODE == COL_KHAT) {
       col_load<CP, C>(x, jb.in + (IL ? 4 : 1) * col, M, t, act);
       __syncthreads();
-      fft_inplace<H, false, ColLayout<C>, CP>(x, t, act);
+      fft_inplace<H, false, ColLayout<C>, CP, kColPowTwiddles<H>>(x, t, act);
       if (act) {
         float2 outv[E], qv[E];
         const float s = jb.scale;
@@ -135,7 +139,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
         col_load<CP, C>(x, jb.in + (MODE == COL_PTOV ? size_t(j) * jb.plane_stride : size_t(0)) + (IL ? 4 : 1) * col,
                         M, t, act);
         __syncthreads();
-        fft_inplace<H, false, ColLayout<C>, CP>(x, t, act);
+        fft_inplace<H, false, ColLayout<C>, CP, kColPowTwiddles<H>>(x, t, act);
         float2 v[E];
         if (act) {
           const float2* kh = jb.khat + size_t(j) * jb.plane_stride;
@@ -152,7 +156,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
           for (int q = 0; q < E; ++q) x(t + q * T) = v[q];
         }
         __syncthreads();
-        fft_inplace<H, true, ColLayout<C>, CP>(x, t, act);
+        fft_inplace<H, true, ColLayout<C>, CP, kColPowTwiddles<H>>(x, t, act);
         if (act) {
           float2* dst = jb.out + size_t(MODE == COL_PTOV ? j + 1 : j) * jb.plane_stride + (IL ? 4 : 1) * col;
 #pragma unroll
@@ -166,7 +170,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
     } else if (NV == 1) {  // COL_PTO1, one view: the product goes straight back to x
       col_load<CP, C>(x, jb.in + (IL ? 4 : 1) * col, M, t, act);
       __syncthreads();
-      fft_inplace<H, false, ColLayout<C>, CP>(x, t, act);
+      fft_inplace<H, false, ColLayout<C>, CP, kColPowTwiddles<H>>(x, t, act);
       float2 v[E];
       if (act) {
 #pragma unroll
@@ -181,7 +185,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
         for (int q = 0; q < E; ++q) x(t + q * T) = v[q];
       }
       __syncthreads();
-      fft_inplace<H, true, ColLayout<C>, CP>(x, t, act);
+      fft_inplace<H, true, ColLayout<C>, CP, kColPowTwiddles<H>>(x, t, act);
       if (act) {
         float2* dst = jb.out + (IL ? 4 : 1) * col;
 #pragma unroll
@@ -199,7 +203,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
       for (int j = 0; j < nin; ++j) {
         col_load<CP, C>(x, jb.in + size_t(j) * jb.plane_stride + (IL ? 4 : 1) * col, M, t, act);
         __syncthreads();
-        fft_inplace<H, false, ColLayout<C>, CP>(x, t, act);
+        fft_inplace<H, false, ColLayout<C>, CP, kColPowTwiddles<H>>(x, t, act);
         if (act) {
           const float2* kh = jb.khat + size_t(j) * jb.plane_stride;
           const float2* kq = jb.khatq + size_t(j) * H;
@@ -221,7 +225,7 @@ __device__ __forceinline__ void b_col(const ColJob* __restrict__ jobs, const int
         }
       }
       __syncthreads();
-      fft_inplace<H, true, ColLayout<C>, CP>(x, t, act);
+      fft_inplace<H, true, ColLayout<C>, CP, kColPowTwiddles<H>>(x, t, act);
       if (act) {
         float2* dst = jb.out + (IL ? 4 : 1) * col;
 #pragma unroll

@@ -287,7 +287,30 @@ template <int L> __host__ __device__ constexpr int col_rows_padded() { return L 
 // ------------------------------------------------------------------------------ Stockham stage
 // One radix-R stage of a length-L transform run by T threads (t in [0, T)).  Every thread of the
 // block calls it (it synchronises); threads with act == false only synchronise.
-template <int L, int R, int NS, int T, bool INV, class Lay>
+// The twiddles w^(m e), m = 1..R-1, of one butterfly (w = exp(-/+ 2 pi i / L)).  Read from the table
+// entry by entry, or (POW, radices 4 and 8) from the entries e, 2e and 4e and their products (at
+// most two further roundings): the lanes of a warp hold few distinct e, and each distinct entry of
+// a stage is a separate access (scattered table lines), so fewer entries per butterfly means less
+// load traffic and latency per stage.
+template <int L, int R, bool INV, bool POW>
+__device__ __forceinline__ void stage_twiddles(int e, float2 (&w)[R]) {
+  if constexpr (POW && (R == 4 || R == 8)) {
+    w[1] = twl<L, INV>(e);
+    w[2] = twl<L, INV>(2 * e);
+    w[3] = cmul(w[2], w[1]);
+    if constexpr (R == 8) {
+      w[4] = twl<L, INV>(4 * e);
+      w[5] = cmul(w[4], w[1]);
+      w[6] = cmul(w[4], w[2]);
+      w[7] = cmul(w[4], w[3]);
+    }
+  } else {
+#pragma unroll
+    for (int m = 1; m < R; ++m) w[m] = twl<L, INV>(m * e);
+  }
+}
+
+template <int L, int R, int NS, int T, bool INV, class Lay, bool POW = false>
 __device__ __forceinline__ void stockham_stage(const Lay& x0, int t, bool act) {
   // Opaque copies of the thread index and base pointer: without them the compiler hoists the
   // shared-memory addresses of every stage (and of every loop iteration around the transform)
@@ -314,8 +337,10 @@ __device__ __forceinline__ void stockham_stage(const Lay& x0, int t, bool act) {
       const int j = t + b * T;
       const int k = j % NS;
       if (NS > 1) {
+        float2 w[R];
+        stage_twiddles<L, R, INV, POW>(k * (L / (NS * R)), w);
 #pragma unroll
-        for (int m = 1; m < R; ++m) v[b][m] = cmul(v[b][m], twl<L, INV>(m * k * (L / (NS * R))));
+        for (int m = 1; m < R; ++m) v[b][m] = cmul(v[b][m], w[m]);
       }
       DFT<R, INV>::run(v[b]);
       const int base = (j - k) * R + k;
@@ -326,19 +351,20 @@ __device__ __forceinline__ void stockham_stage(const Lay& x0, int t, bool act) {
   __syncthreads();
 }
 
-template <int L, int T, bool INV, int NS, class Lay>
+template <int L, int T, bool INV, int NS, bool POW, class Lay>
 __device__ __forceinline__ void run_stages(const Lay&, int, bool, RL<>) {}
-template <int L, int T, bool INV, int NS, class Lay, int R, int... Rest>
+template <int L, int T, bool INV, int NS, bool POW, class Lay, int R, int... Rest>
 __device__ __forceinline__ void run_stages(const Lay& x, int t, bool act, RL<R, Rest...>) {
-  stockham_stage<L, R, NS, T, INV>(x, t, act);
-  run_stages<L, T, INV, NS * R>(x, t, act, RL<Rest...>{});
+  stockham_stage<L, R, NS, T, INV, Lay, POW>(x, t, act);
+  run_stages<L, T, INV, NS * R, POW>(x, t, act, RL<Rest...>{});
 }
 
-// In-place complex FFT of length L (unnormalised), natural order in and out, by the plan P.
-template <int L, bool INV, class Lay, class P = Plan<L>>
+// In-place complex FFT of length L (unnormalised), natural order in and out, by the plan P;
+// POW: twiddles from products of fewer table entries (stage_twiddles).
+template <int L, bool INV, class Lay, class P = Plan<L>, bool POW = false>
 __device__ __forceinline__ void fft_inplace(const Lay& x, int t, bool act) {
-  if (INV) run_stages<L, P::T, true, 1>(x, t, act, typename P::Inv{});
-  else     run_stages<L, P::T, false, 1>(x, t, act, typename P::Fwd{});
+  if (INV) run_stages<L, P::T, true, 1, POW>(x, t, act, typename P::Inv{});
+  else     run_stages<L, P::T, false, 1, POW>(x, t, act, typename P::Fwd{});
 }
 
 // ------------------------------------------------------------------------------ warp four-step
@@ -353,8 +379,19 @@ __device__ __forceinline__ void fft_inplace(const Lay& x, int t, bool act) {
 template <bool INV>
 __device__ __forceinline__ void warp_fft1024(float2 (&v)[32], float2* T, int lane) {
   DFT<32, INV>::run(v);
+  // twiddles w^(lane q), q = 1..31: entries q = 1..7 and 8, 16, 24 of the lane's table, the
+  // others as w^(lane 8a) w^(lane b) (one further rounding; 10 table reads instead of 31)
+  float2 wb[8], wa[4];
 #pragma unroll
-  for (int q = 1; q < 32; ++q) v[q] = cmul(v[q], tw4<INV>(lane, q));
+  for (int q = 1; q < 8; ++q) wb[q] = tw4<INV>(lane, q);
+#pragma unroll
+  for (int a = 1; a < 4; ++a) wa[a] = tw4<INV>(lane, 8 * a);
+#pragma unroll
+  for (int q = 1; q < 32; ++q) {
+    const int a = q >> 3, b = q & 7;
+    const float2 w = a == 0 ? wb[b] : (b == 0 ? wa[a] : cmul(wa[a], wb[b]));
+    v[q] = cmul(v[q], w);
+  }
   __syncwarp();
 #pragma unroll
   for (int q = 0; q < 32; ++q) T[q * 33 + lane] = v[q];
