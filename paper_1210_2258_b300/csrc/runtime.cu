@@ -1600,13 +1600,16 @@ sgp_status sgp_time_passes(sgp_ctx* c, int iters, double* ms_out, int n_out) {
   if (st) return st;
   if (c->mode != 1 && (st = prepare(c, 1))) return st;
   if ((st = arm(c, STOP_FIXED, 1 << 30, 0.0, 1.0))) return st;
-  std::vector<cudaEvent_t> ev(kSgpLaunches + 1);
+  // every iteration's passes are queued before the host waits once, so the GPU does not idle
+  // between iterations (an event pair around each pass; a pass's time includes its launch)
+  std::vector<cudaEvent_t> ev(size_t(iters) * (kSgpLaunches + 1));
   for (auto& e : ev) CU(cudaEventCreate(&e));
   std::vector<double> acc(kSgpLaunches, 0.0);
   for (int it = 0; it < iters && st == SGP_OK; ++it) {
+    cudaEvent_t* e = ev.data() + size_t(it) * (kSgpLaunches + 1);
     int q = 0;
-    CU(cudaEventRecord(ev[q++], c->s));
-    auto step = [&](sgp_status s2) { if (!st) st = s2; cudaEventRecord(ev[q++], c->s); };
+    CU(cudaEventRecord(e[q++], c->s));
+    auto step = [&](sgp_status s2) { if (!st) st = s2; cudaEventRecord(e[q++], c->s); };
     step(row_pass(c, ROP_SGP_UPDATE, true));
     step(adjoint_cols(c, JOB_AT * c->n));
     step(row_pass(c, ROP_SGP_GRAD, false));
@@ -1614,10 +1617,13 @@ sgp_status sgp_time_passes(sgp_ctx* c, int iters, double* ms_out, int n_out) {
     step(col_pass(c, COL_1TOP, JOB_A * c->n));
     step(row_pass(c, ROP_SGP_AD, true));
     step(row_pass(c, ROP_SGP_ARMX, false));
-    CU(cudaEventSynchronize(ev[kSgpLaunches]));
+  }
+  if (st == SGP_OK && cudaEventSynchronize(ev.back()) != cudaSuccess) st = fail(SGP_ERR_CUDA, "pass timing failed");
+  for (int it = 0; it < iters && st == SGP_OK; ++it) {
+    cudaEvent_t* e = ev.data() + size_t(it) * (kSgpLaunches + 1);
     for (int k = 0; k < kSgpLaunches; ++k) {
       float ms = 0.0f;
-      CU(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+      if (cudaEventElapsedTime(&ms, e[k], e[k + 1]) != cudaSuccess) st = fail(SGP_ERR_CUDA, "pass timing failed");
       acc[k] += ms;
     }
   }
