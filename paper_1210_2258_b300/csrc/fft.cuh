@@ -285,8 +285,6 @@ template <int C> struct ColLayout {
 template <int L> __host__ __device__ constexpr int col_rows_padded() { return L + (L >> 4); }
 
 // ------------------------------------------------------------------------------ Stockham stage
-// One radix-R stage of a length-L transform run by T threads (t in [0, T)).  Every thread of the
-// block calls it (it synchronises); threads with act == false only synchronise.
 // The twiddles w^(m e), m = 1..R-1, of one butterfly (w = exp(-/+ 2 pi i / L)).  Read from the table
 // entry by entry, or (POW, radices 4 and 8) from the entries e, 2e and 4e and their products (at
 // most two further roundings): the lanes of a warp hold few distinct e, and each distinct entry of
@@ -310,6 +308,8 @@ __device__ __forceinline__ void stage_twiddles(int e, float2 (&w)[R]) {
   }
 }
 
+// One radix-R stage of a length-L transform run by T threads (t in [0, T)).  Every thread of the
+// block calls it (it synchronises); threads with act == false only synchronise.
 template <int L, int R, int NS, int T, bool INV, class Lay, bool POW = false>
 __device__ __forceinline__ void stockham_stage(const Lay& x0, int t, bool act) {
   // Opaque copies of the thread index and base pointer: without them the compiler hoists the

@@ -356,6 +356,27 @@ __device__ __forceinline__ void store32(bf16* p, const float (&v)[32]) {
         int(pack2(__float2bfloat16(v[8 * q + 6]), __float2bfloat16(v[8 * q + 7]))));
 }
 dim3 pix_grid(int B, int H, int W) { return dim3((W + 127) / 128, H, B); }
+// Block-wide store of 32 channels per pixel for the 128 consecutive pixels x0 .. x0 + 127 of one
+// row (one per thread; pixels at or beyond W are skipped), staged in shared memory so that every
+// warp store writes 512 contiguous bytes: stored directly, a thread's 64 bytes go out as four
+// 16-byte pieces 64 bytes apart, half-sector writes.  Called by every thread of the block.
+__device__ __forceinline__ void store32_block(bf16* row, int x0, int W, const float (&v)[32]) {
+  __shared__ int4 tile[128 * 5];                   // 5 int4 per pixel: conflict-free both ways
+  const int p = int(threadIdx.x);
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    tile[p * 5 + q] = make_int4(int(pack2(__float2bfloat16(v[8 * q]), __float2bfloat16(v[8 * q + 1]))),
+                                int(pack2(__float2bfloat16(v[8 * q + 2]), __float2bfloat16(v[8 * q + 3]))),
+                                int(pack2(__float2bfloat16(v[8 * q + 4]), __float2bfloat16(v[8 * q + 5]))),
+                                int(pack2(__float2bfloat16(v[8 * q + 6]), __float2bfloat16(v[8 * q + 7]))));
+  __syncthreads();
+  int4* dst = reinterpret_cast<int4*>(row + size_t(x0) * 32);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = p + 128 * j;                      // 16-byte piece c: pixel c / 4, part c % 4
+    if (x0 + c / 4 < W) dst[c] = tile[(c >> 2) * 5 + (c & 3)];
+  }
+}
 
 // input layer 1 -> 32: Y[p][co] = relu(sum_tap X[p + off] W[co][tap] + b[co]), X fp32 single channel
 __global__ void __launch_bounds__(128) k_conv_in(const float* __restrict__ x, const float* __restrict__ w,
@@ -364,12 +385,12 @@ __global__ void __launch_bounds__(128) k_conv_in(const float* __restrict__ x, co
   for (int i = threadIdx.x; i < 32 * 9 + 32; i += blockDim.x) sw[i] = i < 288 ? w[i] : bias[i - 288];
   __syncthreads();
   int b, yy, xx;
-  if (!pix_of(W, b, yy, xx)) return;
+  const bool in = pix_of(W, b, yy, xx);            // (no early return: the store is block-wide)
   float xv[9];
 #pragma unroll
   for (int tap = 0; tap < 9; ++tap) {
     const int u = yy + tap / 3 - 1, v = xx + tap % 3 - 1;
-    xv[tap] = (u >= 0 && u < H && v >= 0 && v < W) ? x[(size_t(b) * H + u) * W + v] : 0.0f;
+    xv[tap] = (in && u >= 0 && u < H && v >= 0 && v < W) ? x[(size_t(b) * H + u) * W + v] : 0.0f;
   }
   float o[32];
 #pragma unroll
@@ -379,7 +400,7 @@ __global__ void __launch_bounds__(128) k_conv_in(const float* __restrict__ x, co
     for (int tap = 0; tap < 9; ++tap) s = fmaf(xv[tap], sw[co * 9 + tap], s);
     o[co] = fmaxf(s, 0.0f);
   }
-  store32(y + ((size_t(b) * H + yy) * W + xx) * 32, o);
+  store32_block(y + (size_t(b) * H + yy) * W * 32, int(blockIdx.x) * 128, W, o);
 }
 
 // output layer 32 -> 1: Z[p] = sum_{tap, ci} X[p + off][ci] W[tap][ci] + b (FP32 out), written as
