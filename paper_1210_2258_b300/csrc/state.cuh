@@ -17,9 +17,9 @@ constexpr int kCtrlBlock = 256;     // threads of the controller blocks
 // Programmatic dependent launch: the hot passes are launched so that a pass's launch is processed
 // while the previous pass drains; every such kernel waits (in hardware, griddepcontrol.wait) until
 // the previous grid has completed and its memory is visible before it reads anything.  (Letting
-// the successor's blocks become resident early, at the start of a pass or before the controller
-// tail, measured slower: 3690 and 3130-3960 SGP iterations/s against 3980 at 2048^2.)  Without
-// the launch attribute the wait returns at once.
+// the successor's blocks become resident early measured slower at the start of a pass, 5.54 ms
+// against 4.66 ms for the 2048^2 solve, and no faster before the controller tail, 4.68 ms.)
+// Without the launch attribute the wait returns at once.
 __device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // partial-sum slots (per row item)
