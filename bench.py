@@ -51,8 +51,8 @@ PASS_PLANES = [a + b for a, b in zip(PASS_PIX, PASS_SPEC)]   # without a band: 2
 # the kernels of this tree, PSF band of the Airy PSF in use (258 of 1024 spectrum columns).  A pass's
 # writes are mostly still in L2 when its launch ends, so the figures are mostly its reads; they
 # equal the algorithmic reads (no tile is read twice).
-TRAFFIC_2048 = {"update_ratio": 50.47e6, "col_AT": 8.58e6, "grad_bb": 37.95e6, "proj_y": 33.65e6,
-                "col_A": 8.58e6, "ad_armijo": 37.99e6, "armijo_extra": 0.07e6}
+TRAFFIC_2048 = {"update_ratio": 50.46e6, "col_AT": 8.58e6, "grad_bb": 37.93e6, "proj_y": 33.64e6,
+                "col_A": 8.58e6, "ad_armijo": 37.98e6, "armijo_extra": 0.07e6}
 
 
 def parse():
