@@ -20,7 +20,7 @@ namespace sgp {
 
 __device__ inline void trace_push(double* trace, CtrlState* c, double k, double J, double alpha,
                                   double lam, int bt, int branch, double gTd) {
-  if (c->trace_n < c->trace_cap) {
+  if (trace && c->trace_n < c->trace_cap) {
     double* r = trace + size_t(c->trace_n) * kTraceStride;
     r[0] = k; r[1] = J; r[2] = 2.0 * J * c->inv_pS; r[3] = alpha; r[4] = lam;
     r[5] = bt; r[6] = branch; r[7] = gTd;
@@ -110,15 +110,23 @@ __device__ void sgp_begin_decide(CtrlState* c, const double (&kl)[2]) {
   }
 }
 // (with done == 1 the KL partials were not written by this pass: the sums are not used)
+// The three per-iteration controllers are called by every block of their pass: for real by the
+// block that arrives last, as a dry run (nothing written to global memory, no trace record) by the
+// others.  A controller's instructions run once per pass, in one block, after ~20 us in which the
+// pass has streamed tens of MB through L2: fetched cold, they cost that block 1-2 us of the
+// ~40 000-cycle pass.  The dry runs of the blocks that arrive earlier (which have nothing else to
+// do) bring the code into L2 and into the instruction caches of their SMs first.  One copy of the
+// code serves both (noinline), so the dry runs warm the code that the real run executes.
 template <bool FP64>
-__device__ void ctrl_sgp_begin(const ImgDesc& d) {
+__device__ __noinline__ void ctrl_sgp_begin(const ImgDesc& d, bool dry) {
   __shared__ CtrlState s;
   const CtrlCopy cp(d.ctrl);
   double kl[2];
   ctrl_sum<2, FP64>(d, SLOT_KL, kl, true);
   cp.to_shared(s);
   if (threadIdx.x == 0) sgp_begin_decide<FP64>(&s, kl);
-  CtrlCopy::write_back(s, d.ctrl);
+  if (!dry) CtrlCopy::write_back(s, d.ctrl);
+  else __syncthreads();
 }
 
 template <bool FP64>
@@ -136,14 +144,15 @@ __device__ void sgp_alpha_decide(CtrlState* c, const double (&bb)[4]) {
   c->f_pending = 0;   // K3 has stored f^(k)
 }
 template <bool FP64>
-__device__ void ctrl_sgp_alpha(const ImgDesc& d) {
+__device__ __noinline__ void ctrl_sgp_alpha(const ImgDesc& d, bool dry) {
   __shared__ CtrlState s;
   const CtrlCopy cp(d.ctrl);
   double bb[4];
   ctrl_sum<4, FP64>(d, SLOT_BB, bb, false);
   cp.to_shared(s);
   if (threadIdx.x == 0) sgp_alpha_decide<FP64>(&s, bb);
-  CtrlCopy::write_back(s, d.ctrl);
+  if (!dry) CtrlCopy::write_back(s, d.ctrl);
+  else __syncthreads();
 }
 
 // Change of the Tikhonov term beta/2 ||f||^2 along the step: R(f + lam d) - R(f) =
@@ -242,9 +251,9 @@ __device__ void sgp_lambda_decide(double* trace, CtrlState* c, double gTd, const
   c->need_more = 1;
 }
 template <bool FP64>
-__device__ void ctrl_sgp_lambda(const ImgDesc& d) {
+__device__ __noinline__ void ctrl_sgp_lambda(const ImgDesc& d, bool dry) {
   __shared__ CtrlState s;
-  double* const trace = d.trace;                  // both loaded while the partial sums are read
+  double* const trace = dry ? nullptr : d.trace;  // both loaded while the partial sums are read
   const bool reg = d.reg_beta > 0.0f;
   const CtrlCopy cp(d.ctrl);
   double g[1], arm[kArmMain], rg[2] = {0.0, 0.0};
@@ -256,7 +265,8 @@ __device__ void ctrl_sgp_lambda(const ImgDesc& d) {
     s.reg_dd = rg[1];
     sgp_lambda_decide<FP64>(trace, &s, g[0], arm);
   }
-  CtrlCopy::write_back(s, d.ctrl);
+  if (!dry) CtrlCopy::write_back(s, d.ctrl);
+  else __syncthreads();
 }
 
 template <bool FP64>

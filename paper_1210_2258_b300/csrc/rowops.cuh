@@ -651,7 +651,7 @@ __device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ i
     row_real_to_spec<W>(x, spec_plane(d, j + 1) + spec_row_off(row, G::M, spec_interleaved(d.H)), t, act, spec_interleaved(d.H), d.cb);
     block_sum_store<2, FP64>(acc, partv_of(d, it) + SLOT_KL);
   }
-  if (arrive_last(d.ctrl, d.n_rv_items)) ctrl_sgp_begin<FP64>(d);
+  ctrl_sgp_begin<FP64>(d, !arrive_last(d.ctrl, d.n_rv_items));   // real in the last block, dry in the others
 }
 template <int W, bool FP64>
 __global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_HOT) k_sgp_update_ratio(const ImgDesc* __restrict__ imgs,
@@ -747,7 +747,7 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
       }
     }
     block_sum_store<4, FP64>(acc, part_of(d, it) + SLOT_BB);
-    if (arrive_last(d.ctrl, d.n_row_items)) ctrl_sgp_alpha<FP64>(d);
+    ctrl_sgp_alpha<FP64>(d, !arrive_last(d.ctrl, d.n_row_items));
   }
 }
 template <int W, bool FP64>
@@ -912,7 +912,7 @@ __device__ __forceinline__ void b_sgp_ad_armijo(const ImgDesc* __restrict__ imgs
     else sgp_armijo_rows<W, 1>(x, acc, lam, uj, adj, gj, d, j, off, t);
   }
   block_sum_store<kArmMain, FP64>(acc, partv_of(d, it) + SLOT_ARM);
-  if (arrive_last(d.ctrl, d.n_rv_items)) ctrl_sgp_lambda<FP64>(d);
+  ctrl_sgp_lambda<FP64>(d, !arrive_last(d.ctrl, d.n_rv_items));
 }
 template <int W, bool FP64>
 __global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_MIN) k_sgp_ad_armijo(const ImgDesc* __restrict__ imgs,
