@@ -109,14 +109,15 @@ __device__ void sgp_begin_decide(CtrlState* c, const double (&kl)[2]) {
     c->rho_prev = rho;
   }
 }
+// The per-iteration controllers (the three of SGP here, ctrl_rl below) are called by every block
+// of their pass: for real by the block that arrives last, as a dry run (nothing written to global
+// memory, no trace record) by the others.  A controller's instructions run once per pass, in one
+// block, after ~20 us in which the pass has streamed tens of MB through L2: fetched cold, they cost
+// that block 1-2 us of the ~40 000-cycle pass.  The dry runs of the blocks that arrive earlier
+// (which have nothing else to do) bring the code into L2 and into the instruction caches of their
+// SMs first.  One copy of the code serves both (noinline), so the dry runs warm the code that the
+// real run executes.
 // (with done == 1 the KL partials were not written by this pass: the sums are not used)
-// The three per-iteration controllers are called by every block of their pass: for real by the
-// block that arrives last, as a dry run (nothing written to global memory, no trace record) by the
-// others.  A controller's instructions run once per pass, in one block, after ~20 us in which the
-// pass has streamed tens of MB through L2: fetched cold, they cost that block 1-2 us of the
-// ~40 000-cycle pass.  The dry runs of the blocks that arrive earlier (which have nothing else to
-// do) bring the code into L2 and into the instruction caches of their SMs first.  One copy of the
-// code serves both (noinline), so the dry runs warm the code that the real run executes.
 template <bool FP64>
 __device__ __noinline__ void ctrl_sgp_begin(const ImgDesc& d, bool dry) {
   __shared__ CtrlState s;
@@ -330,16 +331,18 @@ __device__ inline void osem_tick(CtrlState* c, int have_v_after) {
   }
 }
 
+// real in the last block of the RL ratio pass, dry in the others (as the SGP controllers above)
 template <bool FP64>
-__device__ void ctrl_rl(const ImgDesc& d) {
+__device__ __noinline__ void ctrl_rl(const ImgDesc& d, bool dry) {
   __shared__ CtrlState s;
-  double* const trace = d.trace;                  // loaded while the partial sums are read
+  double* const trace = dry ? nullptr : d.trace;  // loaded while the partial sums are read
   const CtrlCopy cp(d.ctrl);
   double kl[1], rr[1];
   ctrl_sums<1, 1, FP64>(d, SLOT_KL, true, kl, SLOT_RHO, false, rr);
   cp.to_shared(s);
   if (threadIdx.x == 0) rl_decide<FP64>(trace, &s, kl[0], rr[0]);
-  CtrlCopy::write_back(s, d.ctrl);
+  if (!dry) CtrlCopy::write_back(s, d.ctrl);
+  else __syncthreads();
 }
 
 }  // namespace sgp

@@ -1092,7 +1092,7 @@ __device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
     return;
   }
   block_sum_store<1, FP64>(acc, partv_of(d, it) + SLOT_KL);
-  if (!write_u && arrive_last(d.ctrl, d.n_rv_items)) ctrl_rl<FP64>(d);   // RL iteration (not set-up)
+  if (!write_u) ctrl_rl<FP64>(d, !arrive_last(d.ctrl, d.n_rv_items));   // RL iteration (not set-up)
 }
 template <int W, bool FP64>
 __global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_HOT) k_rl_ratio(const ImgDesc* __restrict__ imgs,
