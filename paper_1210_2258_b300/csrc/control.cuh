@@ -109,17 +109,21 @@ __device__ void sgp_begin_decide(CtrlState* c, const double (&kl)[2]) {
     c->rho_prev = rho;
   }
 }
-// The per-iteration controllers (the three of SGP here, ctrl_rl below) are called by every block
-// of their pass: for real by the block that arrives last, as a dry run (nothing written to global
-// memory, no trace record) by the others.  A controller's instructions run once per pass, in one
-// block, after ~20 us in which the pass has streamed tens of MB through L2: fetched cold, they cost
-// that block 1-2 us of the ~40 000-cycle pass.  The dry runs of the blocks that arrive earlier
-// (which have nothing else to do) bring the code into L2 and into the instruction caches of their
-// SMs first.  One copy of the code serves both (noinline), so the dry runs warm the code that the
-// real run executes.
+// The per-iteration controllers (the three of SGP here, ctrl_rl below) run for real in the block
+// that arrives last; with `dry` they write nothing to global memory and no trace record.  A
+// controller's instructions run once per pass, in one block, after ~20 us in which the pass has
+// streamed tens of MB through L2: fetched cold, they cost that block 1-2 us of the ~40 000-cycle
+// pass.  So in the one-wave passes over rows of 2048 the blocks that arrive before the last one
+// (which have nothing else to do) run the controller dry first, which brings its code into L2 and
+// into the instruction caches of their SMs.  They call the one non-inlined copy (the *_nl ones) that
+// the last block calls, so the dry runs warm the code that the real run executes.  Elsewhere the
+// controller runs in the last block only: inlined at the other widths (64 registers per thread,
+// where a call's saved registers would spill), and without dry runs in passes of several waves (a
+// dry run would hold a slot that a waiting block needs) or of fewer blocks than SMs (the arrivals
+// do not spread enough for the dry runs to end first); ImgDesc::dry_row / dry_rv say which.
 // (with done == 1 the KL partials were not written by this pass: the sums are not used)
 template <bool FP64>
-__device__ __noinline__ void ctrl_sgp_begin(const ImgDesc& d, bool dry) {
+__device__ __forceinline__ void ctrl_sgp_begin(const ImgDesc& d, bool dry) {
   __shared__ CtrlState s;
   const CtrlCopy cp(d.ctrl);
   double kl[2];
@@ -129,6 +133,8 @@ __device__ __noinline__ void ctrl_sgp_begin(const ImgDesc& d, bool dry) {
   if (!dry) CtrlCopy::write_back(s, d.ctrl);
   else __syncthreads();
 }
+template <bool FP64>
+__device__ __noinline__ void ctrl_sgp_begin_nl(const ImgDesc& d, bool dry) { ctrl_sgp_begin<FP64>(d, dry); }
 
 template <bool FP64>
 __device__ void sgp_alpha_decide(CtrlState* c, const double (&bb)[4]) {
@@ -145,7 +151,7 @@ __device__ void sgp_alpha_decide(CtrlState* c, const double (&bb)[4]) {
   c->f_pending = 0;   // K3 has stored f^(k)
 }
 template <bool FP64>
-__device__ __noinline__ void ctrl_sgp_alpha(const ImgDesc& d, bool dry) {
+__device__ __forceinline__ void ctrl_sgp_alpha(const ImgDesc& d, bool dry) {
   __shared__ CtrlState s;
   const CtrlCopy cp(d.ctrl);
   double bb[4];
@@ -155,6 +161,8 @@ __device__ __noinline__ void ctrl_sgp_alpha(const ImgDesc& d, bool dry) {
   if (!dry) CtrlCopy::write_back(s, d.ctrl);
   else __syncthreads();
 }
+template <bool FP64>
+__device__ __noinline__ void ctrl_sgp_alpha_nl(const ImgDesc& d, bool dry) { ctrl_sgp_alpha<FP64>(d, dry); }
 
 // Change of the Tikhonov term beta/2 ||f||^2 along the step: R(f + lam d) - R(f) =
 // beta (lam f'd + lam^2/2 d'd), exact in lam (0 without regularisation)
@@ -252,7 +260,7 @@ __device__ void sgp_lambda_decide(double* trace, CtrlState* c, double gTd, const
   c->need_more = 1;
 }
 template <bool FP64>
-__device__ __noinline__ void ctrl_sgp_lambda(const ImgDesc& d, bool dry) {
+__device__ __forceinline__ void ctrl_sgp_lambda(const ImgDesc& d, bool dry) {
   __shared__ CtrlState s;
   double* const trace = dry ? nullptr : d.trace;  // both loaded while the partial sums are read
   const bool reg = d.reg_beta > 0.0f;
@@ -269,6 +277,8 @@ __device__ __noinline__ void ctrl_sgp_lambda(const ImgDesc& d, bool dry) {
   if (!dry) CtrlCopy::write_back(s, d.ctrl);
   else __syncthreads();
 }
+template <bool FP64>
+__device__ __noinline__ void ctrl_sgp_lambda_nl(const ImgDesc& d, bool dry) { ctrl_sgp_lambda<FP64>(d, dry); }
 
 template <bool FP64>
 __device__ void sgp_lambda_extra_decide(double* trace, CtrlState* c, const double (&arm)[kArmExtra]) {
@@ -333,7 +343,7 @@ __device__ inline void osem_tick(CtrlState* c, int have_v_after) {
 
 // real in the last block of the RL ratio pass, dry in the others (as the SGP controllers above)
 template <bool FP64>
-__device__ __noinline__ void ctrl_rl(const ImgDesc& d, bool dry) {
+__device__ __forceinline__ void ctrl_rl(const ImgDesc& d, bool dry) {
   __shared__ CtrlState s;
   double* const trace = dry ? nullptr : d.trace;  // loaded while the partial sums are read
   const CtrlCopy cp(d.ctrl);
@@ -344,5 +354,7 @@ __device__ __noinline__ void ctrl_rl(const ImgDesc& d, bool dry) {
   if (!dry) CtrlCopy::write_back(s, d.ctrl);
   else __syncthreads();
 }
+template <bool FP64>
+__device__ __noinline__ void ctrl_rl_nl(const ImgDesc& d, bool dry) { ctrl_rl<FP64>(d, dry); }
 
 }  // namespace sgp

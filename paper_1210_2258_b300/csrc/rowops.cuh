@@ -651,7 +651,14 @@ __device__ __forceinline__ void b_sgp_update_ratio(const ImgDesc* __restrict__ i
     row_real_to_spec<W>(x, spec_plane(d, j + 1) + spec_row_off(row, G::M, spec_interleaved(d.H)), t, act, spec_interleaved(d.H), d.cb);
     block_sum_store<2, FP64>(acc, partv_of(d, it) + SLOT_KL);
   }
-  ctrl_sgp_begin<FP64>(d, !arrive_last(d.ctrl, d.n_rv_items));   // real in the last block, dry in the others
+  {  // the controller: real in the last block, dry in the others when d.dry_rv (control.cuh)
+    const bool last = arrive_last(d.ctrl, d.n_rv_items);
+    if constexpr (RowGeo<W>::WARP) {
+      if (last || d.dry_rv) ctrl_sgp_begin_nl<FP64>(d, !last);
+    } else if (last) {
+      ctrl_sgp_begin<FP64>(d, false);
+    }
+  }
 }
 template <int W, bool FP64>
 __global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_HOT) k_sgp_update_ratio(const ImgDesc* __restrict__ imgs,
@@ -747,7 +754,12 @@ __device__ __forceinline__ void b_sgp_grad_bb(const ImgDesc* __restrict__ imgs,
       }
     }
     block_sum_store<4, FP64>(acc, part_of(d, it) + SLOT_BB);
-    ctrl_sgp_alpha<FP64>(d, !arrive_last(d.ctrl, d.n_row_items));
+    const bool last = arrive_last(d.ctrl, d.n_row_items);
+    if constexpr (RowGeo<W>::WARP) {
+      if (last || d.dry_row) ctrl_sgp_alpha_nl<FP64>(d, !last);
+    } else if (last) {
+      ctrl_sgp_alpha<FP64>(d, false);
+    }
   }
 }
 template <int W, bool FP64>
@@ -912,7 +924,12 @@ __device__ __forceinline__ void b_sgp_ad_armijo(const ImgDesc* __restrict__ imgs
     else sgp_armijo_rows<W, 1>(x, acc, lam, uj, adj, gj, d, j, off, t);
   }
   block_sum_store<kArmMain, FP64>(acc, partv_of(d, it) + SLOT_ARM);
-  ctrl_sgp_lambda<FP64>(d, !arrive_last(d.ctrl, d.n_rv_items));
+  const bool last = arrive_last(d.ctrl, d.n_rv_items);
+  if constexpr (RowGeo<W>::WARP) {
+    if (last || d.dry_rv) ctrl_sgp_lambda_nl<FP64>(d, !last);
+  } else if (last) {
+    ctrl_sgp_lambda<FP64>(d, false);
+  }
 }
 template <int W, bool FP64>
 __global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_MIN) k_sgp_ad_armijo(const ImgDesc* __restrict__ imgs,
@@ -1092,7 +1109,14 @@ __device__ __forceinline__ void b_rl_ratio(const ImgDesc* __restrict__ imgs,
     return;
   }
   block_sum_store<1, FP64>(acc, partv_of(d, it) + SLOT_KL);
-  if (!write_u) ctrl_rl<FP64>(d, !arrive_last(d.ctrl, d.n_rv_items));   // RL iteration (not set-up)
+  if (!write_u) {   // RL iteration (not set-up)
+    const bool last = arrive_last(d.ctrl, d.n_rv_items);
+    if constexpr (RowGeo<W>::WARP) {
+      if (last || d.dry_rv) ctrl_rl_nl<FP64>(d, !last);
+    } else if (last) {
+      ctrl_rl<FP64>(d, false);
+    }
+  }
 }
 template <int W, bool FP64>
 __global__ void __launch_bounds__(kRowBlock, RowGeo<W>::BLOCKS_HOT) k_rl_ratio(const ImgDesc* __restrict__ imgs,

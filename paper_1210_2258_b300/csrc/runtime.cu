@@ -345,6 +345,29 @@ sgp_status fill_row_items(sgp_ctx* c, int R) {
     c->row_threads = R * (kRowBlock / rm);
     c->row_smem_hot = g_reg.row_smem[si] / size_t(rm) * size_t(R);
   }
+  // Dry controller runs pay when a pass is one wave of at least one block per SM: every block is
+  // resident from the start (a dry run delays no waiting block) and the arrivals spread over
+  // microseconds (the early dry runs end before the last block's real one).
+  {
+    int dev = 0, nsm = 0, occ = 1 << 30;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const RowOp ops[] = {ROP_SGP_UPDATE, ROP_SGP_GRAD, ROP_SGP_AD, ROP_RL_RATIO};
+    for (RowOp op : ops)
+      for (int f = 0; f < 2; ++f) {
+        const void* fn = c->mixed ? g_reg.row_multi[op][f] : g_reg.row[op][f][side_index(c->W)];
+        if (!fn) continue;
+        int o = 0;
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, c->mixed ? kRowBlock : c->row_threads,
+                                                         c->mixed ? g_reg.row_multi_smem : c->row_smem_hot));
+        occ = std::min(occ, o);
+      }
+    const int slots = occ == (1 << 30) ? 0 : occ * nsm;
+    for (int i = 0; i < c->n; ++i) {
+      L.d[i].dry_row = r0 >= nsm && r0 <= slots;
+      L.d[i].dry_rv = rv0 >= nsm && rv0 <= slots;
+    }
+  }
   CU(cudaMemcpyAsync(L.d_imgs, L.d.data(), sizeof(ImgDesc) * c->n, cudaMemcpyHostToDevice, c->s));
   CU(cudaMemcpyAsync(L.d_row, c->row.data(), sizeof(int2) * c->row.size(), cudaMemcpyHostToDevice, c->s));
   CU(cudaMemcpyAsync(L.d_rv, c->rv.data(), sizeof(int2) * c->rv.size(), cudaMemcpyHostToDevice, c->s));

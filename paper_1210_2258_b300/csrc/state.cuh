@@ -109,6 +109,8 @@ struct ImgDesc {
   int rpi;                      // image rows per row item
   int cb;                       // spectrum columns in the PSF band (<= W/2): the hot row passes store
                                 // and load only columns < cb, the others are zero (band-limited PSF)
+  int dry_row, dry_rv;          // 1: the passes over the row (row-view) list run their controller dry
+                                // in the blocks that arrive before the last one (control.cuh)
   float w_scalar;               // periodic: 1/p (RL factor, SGP scaling factor)
   float a1_scalar;              // periodic: p (= sum_j A_j^T 1)
   float reg_beta;               // regularised SGP: weight of beta/2 ||f||^2 (0: none)
