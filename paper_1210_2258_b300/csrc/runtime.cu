@@ -228,6 +228,7 @@ struct sgp_ctx {
   cudaStream_t s = nullptr;        // internal stream (graphs are captured on it)
   cudaStream_t user = nullptr;     // caller's stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_hctrl = nullptr;  // recorded after each upload from h_ctrl (reset_ctrl)
   sgp_params prm;
   std::vector<sgp_shape> sh;
   Layout L;
@@ -249,6 +250,7 @@ struct sgp_ctx {
   std::vector<double> nS;          // |S| per problem
   std::vector<int> has_data;
   std::vector<const float*> truth;
+  std::vector<double> ftrue_n2;    // ||f_true||^2 per problem (0 without one), as set_truth computed it
   std::vector<int> start_in_f0;    // 1: a new start was written to f[0] since the last set-up
   int mode = 0;                    // 0 not prepared, 1 SGP, 2 RL, 3 OSEM
   cudaGraphExec_t g_sgp = nullptr, g_rl = nullptr;   // graph_units iterations (fixed counts)
@@ -755,10 +757,18 @@ sgp_status build_loop_graph(sgp_ctx* c, bool sgp, bool land, int cap, cudaGraphE
   return SGP_OK;
 }
 
+// Fresh controller states for a new run.  The device state is read back only when some problem
+// continues from its last iterate (which of f[0], f[1] holds it); with a new start everywhere (the
+// usual solve) the host fills the states and uploads them without waiting for the GPU.
 sgp_status reset_ctrl(sgp_ctx* c) {
   CtrlState* h = c->h_ctrl;
-  CU(cudaMemcpyAsync(h, c->L.ctrl, sizeof(CtrlState) * c->n, cudaMemcpyDeviceToHost, c->s));
-  CU(cudaStreamSynchronize(c->s));
+  CU(cudaEventSynchronize(c->ev_hctrl));   // the previous upload has read h
+  bool all_new = true;
+  for (int i = 0; i < c->n; ++i) all_new = all_new && c->start_in_f0[i];
+  if (!all_new) {
+    CU(cudaMemcpyAsync(h, c->L.ctrl, sizeof(CtrlState) * c->n, cudaMemcpyDeviceToHost, c->s));
+    CU(cudaStreamSynchronize(c->s));
+  }
   for (int i = 0; i < c->n; ++i) {
     const int cur = c->start_in_f0[i] ? 0 : ((h[i].k - h[i].result_prev) & 1);
     c->start_in_f0[i] = 0;
@@ -780,12 +790,12 @@ sgp_status reset_ctrl(sgp_ctx* c) {
     z.alpha_min = P.alpha_min; z.alpha_max = P.alpha_max;
     z.tol = 0; z.eta = 1.0;
     z.inv_pS = c->nS[i] > 0 ? 1.0 / (double(c->L.d[i].p) * c->nS[i]) : 0.0;
-    z.ftrue_norm2 = h[i].ftrue_norm2;
+    z.ftrue_norm2 = c->ftrue_n2[i];
     z.rho_prev = INFINITY;
     h[i] = z;
   }
   CU(cudaMemcpyAsync(c->L.ctrl, h, sizeof(CtrlState) * c->n, cudaMemcpyHostToDevice, c->s));
-  CU(cudaStreamSynchronize(c->s));
+  CU(cudaEventRecord(c->ev_hctrl, c->s));
   return SGP_OK;
 }
 
@@ -846,7 +856,9 @@ sgp_status autotune_rows(sgp_ctx* c) {
   return fill_row_items(c, best_r);
 }
 
-sgp_status prepare(sgp_ctx* c, int mode) {
+// report = false (the solve loops): the set-up's status is not read back here; a problem whose
+// set-up failed is stopped with its status, which the caller reads after the loop.
+sgp_status prepare(sgp_ctx* c, int mode, bool report = true) {
   for (int i = 0; i < c->n; ++i)
     if (!c->has_data[i]) return fail(SGP_ERR_STATE, "sgp_set_data was not called for every problem");
   sgp_status st;
@@ -892,6 +904,10 @@ sgp_status prepare(sgp_ctx* c, int mode) {
       CU(cudaMemcpyAsync(&c->L.ctrl[i].have_v, &one, sizeof(int), cudaMemcpyHostToDevice, c->s));
       CU(cudaStreamSynchronize(c->s));
     }
+  }
+  if (!report) {
+    c->mode = mode;
+    return SGP_OK;
   }
   CU(read_ctrl(c, c->h_ctrl) == SGP_OK ? cudaSuccess : cudaErrorUnknown);
   // a problem whose set-up failed stays stopped with its status; the others proceed
@@ -941,7 +957,7 @@ sgp_status run_until(sgp_ctx* c, bool sgp, const sgp_stop_rule* rule, int* iters
   if (land && !(rule->tol < 0.5)) return fail(SGP_ERR_ARG, "landed stop: tol must be below 0.5");
   const double tol = land && rule->tol <= 0.0 ? 1e-5 : rule->tol;
   sgp_status st;
-  if (c->mode != (sgp ? 1 : 2) && (st = prepare(c, sgp ? 1 : 2))) return st;
+  if (c->mode != (sgp ? 1 : 2) && (st = prepare(c, sgp ? 1 : 2, false))) return st;
   if (rule->kind == STOP_MIN_ERROR)
     for (int i = 0; i < c->n; ++i)
       if (!c->truth[i]) return fail(SGP_ERR_ARG, "minimum-error stop needs sgp_set_truth");
@@ -974,7 +990,10 @@ sgp_status run_until(sgp_ctx* c, bool sgp, const sgp_stop_rule* rule, int* iters
   for (int i = 0; i < c->n; ++i) {
     const CtrlState& h = c->h_ctrl[i];
     if (iters) iters[i] = h.k - h.result_prev;
-    if (h.status && res == SGP_OK) res = fail(sgp_status(h.status), "problem " + std::to_string(i) + " stopped with an error");
+    if (h.status && res == SGP_OK)
+      res = fail(sgp_status(h.status), h.k == 0 ? "set-up failed for problem " + std::to_string(i) +
+                                                      " (no positive pixel after one RL step, or non-finite J)"
+                                                : "problem " + std::to_string(i) + " stopped with an error");
     if (res == SGP_OK && (h.done < 1 || (rule->kind != STOP_FIXED && h.capped)))
       res = fail(SGP_ERR_TIMEOUT, "problem " + std::to_string(i) + ": stop rule not reached within max_iter");
   }
@@ -1129,7 +1148,8 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
   auto bail = [&](sgp_status s) { sgp_destroy(c); return s; };
   if (cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_hctrl, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(SGP_ERR_CUDA, "stream/event creation failed"));
   if (cudaMallocHost(&c->h_ctrl, sizeof(CtrlState) * n) != cudaSuccess)
     return bail(fail(SGP_ERR_CUDA, "pinned host buffer allocation failed"));
@@ -1210,6 +1230,7 @@ sgp_status sgp_create_batch(sgp_ctx** out, int n, const sgp_shape* shapes, const
   c->nS.assign(n, 0.0);
   c->has_data.assign(n, 0);
   c->truth.assign(n, nullptr);
+  c->ftrue_n2.assign(n, 0.0);
   c->start_in_f0.assign(n, 1);
 
   // PSF statistics and normalisation scale (Sect. 1 / 2.4: unit volume over the domain)
@@ -1426,6 +1447,7 @@ sgp_status sgp_set_truth(sgp_ctx* c, int image, const float* f_true) {
   }
   CU(cudaMemcpyAsync(&c->L.ctrl[image].ftrue_norm2, &nrm, sizeof(double), cudaMemcpyHostToDevice, c->s));
   CU(cudaStreamSynchronize(c->s));
+  c->ftrue_n2[image] = nrm;
   return leave(c);
 }
 
@@ -1801,6 +1823,7 @@ sgp_status sgp_destroy(sgp_ctx* c) {
   if (c->gl_land) cudaGraphExecDestroy(c->gl_land);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->ev_hctrl) cudaEventDestroy(c->ev_hctrl);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
   if (c->s) cudaStreamDestroy(c->s);
   delete c;
