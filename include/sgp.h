@@ -27,9 +27,9 @@
  *   - The workspace (device memory of sgp_workspace_bytes bytes, 256-byte aligned) is owned by
  *     the caller and must outlive the context; the library never allocates device memory.
  *   - `stream` is a cudaStream_t (passed as void*; NULL = legacy default stream).  Calls are
- *     ordered with that stream.  sgp_create, sgp_set_data, sgp_set_start, kl_value, sgp_get_*,
- *     sgp_solve_until and rl_solve_until synchronise; rl_iterate, sgp_iterate, sgp_apply_A and
- *     sgp_apply_AT are asynchronous.
+ *     ordered with that stream.  sgp_create, sgp_set_data, kl_value, sgp_get_*, sgp_solve_until
+ *     and rl_solve_until synchronise; sgp_set_start, rl_iterate, sgp_iterate, sgp_apply_A and
+ *     sgp_apply_AT are asynchronous (a user start f0 is read in stream order).
  *   - Every call returns an sgp_status; sgp_last_error() gives a message for the calling thread.
  *   - A context is not thread safe; use one context per host thread.
  */

@@ -1425,8 +1425,7 @@ sgp_status sgp_set_start(sgp_ctx* c, int image, int mode, const float* f0) {
   if ((st = launch((const void*)&k_fill_start, grid_for(P), 256, 0, c->s, a))) return st;
   c->start_in_f0[image] = 1;
   c->mode = 0;
-  CU(cudaStreamSynchronize(c->s));
-  return leave(c);
+  return leave(c);   // stream-ordered: the next call (or the caller's stream) sees f[0]
 }
 
 sgp_status sgp_set_truth(sgp_ctx* c, int image, const float* f_true) {
