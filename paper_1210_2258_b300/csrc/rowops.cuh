@@ -840,7 +840,7 @@ __device__ __forceinline__ void sgp_armijo_rows(const RowLayout<W / 2>& x, A (&a
   const float (&lamN)[N] = reinterpret_cast<const float (&)[N]>(lam);
   constexpr int B = batch_of<G::E, 4>();
   // software pipeline: the loads of the next batch are issued before this batch is used (the pass
-  // holds no transform data in registers here; K1 and K4 measured slower with the same change)
+  // holds no transform data in registers here; K1, K3 and K4 measured slower with the same change)
   float2 un[B], gn[B];
   auto load = [&](int q0) {
 #pragma unroll
