@@ -215,6 +215,10 @@ class Problems:
     def set_start(self, image: int, mode: int, f0=None) -> None:
         f0c = f0.contiguous() if f0 is not None else None
         _check(load().sgp_set_start(self.ctx, image, mode, _ptr(f0c)))
+        # the call is stream-ordered: a contiguous copy made here stays alive until the next start
+        # of this image, so that its memory is not reused before the library has read it
+        self._starts = getattr(self, "_starts", {})
+        self._starts[image] = f0c
 
     def set_truth(self, image: int, f_true) -> None:
         self._truth = getattr(self, "_truth", {})
