@@ -259,16 +259,40 @@ __global__ void __launch_bounds__(256) k_stats_partial(const float* __restrict__
   // max / min / counts (exact: a thread sees fewer than 2^24 pixels); FP64 from the block level up
   Acc<true> k0, k1;
   float m1 = mode ? 0.0f : -INFINITY, m2 = mode ? 0.0f : INFINITY, n2 = 0.0f, n3 = 0.0f;
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < P; i += size_t(gridDim.x) * blockDim.x) {
-    const float v = a[i];
+  auto add = [&](float v, size_t i) {
     if (mode == 0) {
-      if (!isfinite(v)) { n3 += 1.0f; continue; }
+      if (!isfinite(v)) { n3 += 1.0f; return; }
       k0.add(v); m1 = fmaxf(m1, v); m2 = fminf(m2, v);
     } else {
-      if (v < 0.0f) continue;
+      if (v < 0.0f) return;
       k0.add(v); k1.add(bj ? bj[i] : bc); n2 += 1.0f;
     }
+  };
+  const size_t stride = size_t(gridDim.x) * blockDim.x;
+  // 16-byte loads of four samples, four of them in flight per thread, when the plane allows
+  const bool vec = P % 4 == 0 && (reinterpret_cast<uintptr_t>(a) & 15) == 0;
+  size_t i0 = 0;
+  if (vec) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const size_t P4 = P / 4;
+    size_t j = blockIdx.x * size_t(blockDim.x) + threadIdx.x;
+    for (; j + 3 * stride < P4; j += 4 * stride) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = a4[j + u * stride];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const size_t e = 4 * (j + u * stride);
+        add(v[u].x, e); add(v[u].y, e + 1); add(v[u].z, e + 2); add(v[u].w, e + 3);
+      }
+    }
+    for (; j < P4; j += stride) {
+      const float4 v = a4[j];
+      add(v.x, 4 * j); add(v.y, 4 * j + 1); add(v.z, 4 * j + 2); add(v.w, 4 * j + 3);
+    }
+    i0 = P;   // nothing left for the scalar loop
   }
+  for (size_t i = i0 + blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < P; i += stride) add(a[i], i);
   const double s0 = double(k0.hi) + double(k0.lo), s3 = n3;
   const double s1 = mode ? double(k1.hi) + double(k1.lo) : double(m1), s2 = mode ? double(n2) : double(m2);
   __shared__ double r[4][256];
