@@ -72,3 +72,27 @@ def test_nonfinite_status_from_an_overflowing_start(gpu, stars64):
     # a fresh context on the same device still solves
     ok = gpu_problem(gpu, sc)
     assert ok.solve_until(gpu.STOP_DISCREPANCY, max_iter=500, eta=1.5)[0] > 0
+
+
+def test_user_start_from_a_temporary_view_is_read_in_stream_order(gpu, stars64):
+    """sgp_set_start is asynchronous (stream-ordered): a start given as a non-contiguous view is
+    copied by the binding, and the solve sees that start even when the view is dropped and its
+    memory is reused right after the call."""
+    import torch
+    sc = stars64
+    start = np.random.default_rng(5).uniform(1.0, 2.0, sc.shape).astype(np.float32)
+    ref = gpu_problem(gpu, sc)
+    ref.set_start(0, gpu.START_USER, dev(start))
+    it_ref = ref.solve_until(gpu.STOP_DISCREPANCY, max_iter=30, eta=1.5, raise_on_error=False)
+    f_ref = host(ref.get_f())
+
+    prob = gpu_problem(gpu, sc)
+    view = dev(np.ascontiguousarray(start.T)).t()          # the same values, not contiguous
+    assert not view.is_contiguous()
+    prob.set_start(0, gpu.START_USER, view)
+    del view
+    junk = [torch.full(sc.shape, 7.0, device="cuda") for _ in range(8)]   # reuse of freed memory
+    it = prob.solve_until(gpu.STOP_DISCREPANCY, max_iter=30, eta=1.5, raise_on_error=False)
+    del junk
+    assert it == it_ref and it[0] > 0 and prob.last_status == ref.last_status
+    assert np.array_equal(host(prob.get_f()), f_ref)
