@@ -96,3 +96,24 @@ def test_user_start_from_a_temporary_view_is_read_in_stream_order(gpu, stars64):
     del junk
     assert it == it_ref and it[0] > 0 and prob.last_status == ref.last_status
     assert np.array_equal(host(prob.get_f()), f_ref)
+
+
+def test_setup_failure_of_one_problem_in_a_batch(gpu, stars64):
+    """The solve loop starts without reading the set-up status back: a problem whose set-up fails
+    (the overflowing start above) stops with its status at iteration 0 while the other problem of
+    the same context solves exactly as it does alone."""
+    sc = stars64
+    psf = dev(np.asarray(sc.psfs, np.float32))
+    b = list(np.asarray(sc.b, np.float32))
+    g = dev(np.asarray(sc.g, np.float32))
+    alone = gpu_problem(gpu, sc)
+    it_alone = alone.solve_until(gpu.STOP_DISCREPANCY, max_iter=500, eta=1.5)
+    pair = gpu.Problems([psf, psf], [b, b])
+    pair.set_data(0, g)
+    pair.set_data(1, g)
+    pair.set_start(0, gpu.START_USER, dev(np.full(sc.shape, 1e36, np.float32)))
+    it = pair.solve_until(gpu.STOP_DISCREPANCY, max_iter=500, eta=1.5, raise_on_error=False)
+    assert pair.last_status == gpu.ERR_NONFINITE
+    assert pair.info(0).status == gpu.ERR_NONFINITE and it[0] == 0
+    assert pair.info(1).status == 0 and it[1] == it_alone[0]
+    assert np.array_equal(host(pair.get_f(1)), host(alone.get_f()))
